@@ -1,0 +1,56 @@
+"""The five synthetic workloads: lattice shapes, couplings, seeds and solver settings.
+
+They stand in for the paper's production ensembles (32^3x64, 48^3x64, 64^3x128
+clover lattices, Sec. V), which are not available: random SU(3) fields of a stated
+width, optionally APE smoothed, with Gaussian or point sources.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from .gauge import ape_smear, random_su3_field
+from .sources import gaussian_source
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    dims: tuple            # (Lx, Ly, Lz, Lt)
+    width: float           # random SU(3) width
+    ape_steps: int
+    kappa: float
+    csw: float
+    domain: tuple          # Schwarz domain shape (bx, by, bz, bt)
+    i_schwarz: int
+    i_domain: int
+    m: int                 # FGMRES-DR basis size
+    k: int                 # deflation vectors
+    gauge_seed: int
+    source_seed: int
+    tol: float = 1e-10
+
+    @property
+    def volume(self) -> int:
+        return int(np.prod(self.dims))
+
+
+WORKLOADS = {
+    "8^4": Workload("8^4", (8, 8, 8, 8), 0.6, 0, 0.1300, 1.0, (4, 4, 4, 4), 16, 4, 16, 0, 11, 21),
+    "32^3x64": Workload("32^3x64", (32, 32, 32, 64), 0.5, 5, 0.1360, 1.5, (8, 4, 4, 4), 16, 5, 16, 6, 12, 22),
+    "24^3x48": Workload("24^3x48", (24, 24, 24, 48), 0.5, 5, 0.1360, 1.5, (4, 4, 4, 4), 16, 5, 16, 6, 14, 24),
+    "16^3x32": Workload("16^3x32", (16, 16, 16, 32), 0.5, 5, 0.1340, 1.5, (4, 4, 4, 4), 16, 5, 16, 6, 151, 25),
+}
+
+
+def make_gauge(w: Workload, device="cpu") -> torch.Tensor:
+    U = random_su3_field(w.dims, w.width, w.gauge_seed, device=device)
+    if w.ape_steps:
+        U = ape_smear(U, 0.5, w.ape_steps)
+    return U
+
+
+def make_sources(w: Workload, n: int = 1) -> list[np.ndarray]:
+    return [gaussian_source(w.dims, w.source_seed + i) for i in range(n)]
