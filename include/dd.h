@@ -1,0 +1,163 @@
+/*
+ * dd.h -- C ABI of a GB300 (sm_103a) solver for the Wilson-clover Dirac equation with
+ * the domain-decomposition method of Heybrock et al., "Lattice QCD with Domain
+ * Decomposition on Intel Xeon Phi Co-Processors" (SC14): a multiplicative Schwarz
+ * (SAP) preconditioner whose domain solves are minimal-residual iterations on the
+ * even-odd Schur complement, inside flexible GMRES with deflated restarts.
+ *
+ * Conventions for every entry point:
+ *   - Every function returns a dd_status; DD_OK is 0.  Nothing aborts or exits.  After
+ *     a failure dd_last_error(ctx) returns a message (valid until the next call).
+ *   - The caller owns every buffer it passes and keeps ownership.  The context owns
+ *     its internal copies (gauge field, clover, Schwarz state, Krylov basis).
+ *   - All work is issued on the stream given to dd_create (NULL = legacy stream) and
+ *     the functions return after that work has completed, unless stated otherwise.
+ *   - One context per stream; contexts are not thread safe.
+ *
+ * Canonical layouts (host or device memory, little endian IEEE):
+ *   spinor  [t][z][y][x][spin 4][colour 3][re, im]    FP64 (double) or FP32 (float)
+ *   gauge   [t][z][y][x][mu 4][row 3][col 3][re, im]  FP64, mu = x, y, z, t; entry
+ *           (mu, a, b) of site x is U_mu(x)_ab, the forward link from x to x + mu.
+ *   Site x = (x, y, z, t); lexicographic index x + Lx (y + Ly (z + Lz t)).
+ * Internal layout: domain-major (see dd_spinor_bytes); only needed for the fastest
+ *   device-to-device calls.  dd_pack_spinor / dd_unpack_spinor convert.
+ *
+ * Operator (Sec. II-B, Eq. 1-3):  A = 1/(2 kappa) - 1/2 D_w + D_cl with
+ *   D_w psi(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu)
+ *   D_cl(x)   = -(c_sw/32) sum_{mu != nu} gamma_mu gamma_nu (Q_mu,nu(x) - Q_nu,mu(x)),
+ *   Q_mu,nu the sum of the four plaquettes in the (mu, nu) plane at x; N_d + m = 1/(2 kappa).
+ *   Gamma matrices: chiral basis, gamma_5 = diag(1, 1, -1, -1), gamma_k = [[0, -i s_k],
+ *   [i s_k, 0]] for k = x, y, z, gamma_t = [[0, 1], [1, 0]].  Boundary conditions:
+ *   periodic in x, y, z; antiperiodic in t when t_antiperiodic != 0.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dd_ctx dd_ctx;
+typedef int dd_status;
+
+enum {
+  DD_OK = 0,
+  DD_ERR_INVALID = 1,          /* null pointer or out-of-range argument */
+  DD_ERR_DIMS = 2,             /* lattice / domain shape not allowed */
+  DD_ERR_NO_GAUGE = 3,         /* dd_load_gauge has not been called */
+  DD_ERR_NO_CLOVER = 4,        /* dd_build_clover has not been called */
+  DD_ERR_SINGULAR_CLOVER = 5,  /* a 6x6 clover block is (numerically) singular */
+  DD_ERR_NOT_CONVERGED = 6,    /* iteration limit reached; info is still filled */
+  DD_ERR_NONFINITE = 7,        /* NaN or Inf met in a norm */
+  DD_ERR_TIMEOUT = 8,          /* a bounded device wait ran out */
+  DD_ERR_OOM = 9,              /* device allocation failed */
+  DD_ERR_CUDA = 10             /* other CUDA runtime error */
+};
+
+enum { DD_PREC_FP64 = 0, DD_PREC_FP32 = 1, DD_PREC_FP16 = 2 };
+enum { DD_HOST = 0, DD_DEVICE = 1 };
+enum { DD_LAYOUT_CANONICAL = 0, DD_LAYOUT_INTERNAL = 1 };
+
+/* Schwarz preconditioner parameters (Sec. II-C, Table I). */
+typedef struct {
+  int i_schwarz;      /* Schwarz iterations; one iteration = black then white half-sweep (paper: 16) */
+  int i_domain;       /* MR steps per domain solve (paper: 4-5) */
+  int storage_prec;   /* DD_PREC_FP16: FP16 links, Schwarz matrices and spinors (FP32 arithmetic);
+                         DD_PREC_FP32: everything FP32 */
+} dd_sap_params;
+
+/* Outer solver parameters (flexible GMRES with deflated restarts, Table I). */
+typedef struct {
+  double tol;         /* target |f - A x| / |f|, recomputed in FP64 (paper: 1e-10) */
+  int m;              /* basis size, 1 <= m <= 64 */
+  int k;              /* deflation vectors kept at a restart, 0 <= k < m */
+  int max_iter;       /* total Arnoldi steps allowed */
+  dd_sap_params sap;
+} dd_solve_params;
+
+/* Result of dd_solve (for nrhs > 1: summed counts and times, worst residual). */
+typedef struct {
+  int status;
+  int iterations;         /* Arnoldi steps = applications of the preconditioner */
+  int restarts;           /* cycles after the first */
+  int reliable_updates;   /* FP64 true-residual recomputations */
+  int deflated_restarts;
+  double true_rel_residual;  /* |f - A x| / |f| in FP64 at exit */
+  double t_total, t_A, t_M, t_GS, t_other;  /* seconds (device time of each part) */
+  double flops_nominal;   /* 1848 flop/site per A and per D application, paper's convention */
+} dd_solve_info;
+
+/* Create a context for a lattice dims = {Lx, Ly, Lz, Lt} split into domains of shape
+ * domain = {bx, by, bz, bt}.  Each b_mu must be a power of two >= 2 and divide L_mu,
+ * each L_mu / b_mu must be even (two-colouring of the domains, Sec. IV-D) and >= 2, and
+ * the Schwarz kernel needs 64 <= prod(b) <= 512.  stream: a cudaStream_t or NULL.
+ * Allocates its device memory with cudaMalloc. */
+dd_status dd_create(dd_ctx** out, const int dims[4], const int domain[4], int t_antiperiodic, void* stream);
+dd_status dd_destroy(dd_ctx* ctx);
+const char* dd_last_error(const dd_ctx* ctx);
+
+/* Load the gauge field (canonical FP64 layout, host or device memory per `where`).
+ * It is copied; FP64, FP32 and FP16 internal copies are made. */
+dd_status dd_load_gauge(dd_ctx* ctx, const double* U, int where);
+
+/* Build the clover term (Eq. 3) with the diagonal 1/(2 kappa) folded in, in FP64, and
+ * each 6x6 block's inverse for the even-odd domain solves (Eq. 5); store FP64/FP32/FP16
+ * copies.  Returns DD_ERR_SINGULAR_CLOVER (after building) if a block is singular. */
+dd_status dd_build_clover(dd_ctx* ctx, double kappa, double c_sw);
+
+/* out = A in (Eq. 1) for device buffers.  prec: DD_PREC_FP64 / FP32 (canonical or
+ * internal layout) or DD_PREC_FP16 (internal layout only: FP16 storage, FP32
+ * arithmetic).  in and out must not overlap. */
+dd_status dd_apply_D(dd_ctx* ctx, const void* in, void* out, int prec, int layout);
+
+/* out = M in: the multiplicative Schwarz preconditioner (Table I, Sec. II-C) with
+ * I_Schwarz black/white sweeps of even-odd MR domain solves.  in/out: FP32 device
+ * buffers in `layout`; they may not overlap. */
+dd_status dd_sap_precondition(dd_ctx* ctx, const float* in, float* out, const dd_sap_params* p, int layout);
+
+/* Solve A x = f (Sec. III, Table I) for nrhs right-hand sides stored one after another
+ * in the canonical FP64 layout (host or device memory per `where`).  x holds the
+ * initial guess on entry (zeros are fine) and the solution on exit.  Outer FGMRES-DR
+ * in FP32 vectors with FP64 Hessenberg, Gram-Schmidt coefficients and least squares;
+ * x accumulated in FP64 and the residual recomputed with the FP64 operator at every
+ * restart (reliable update).  info may be NULL. */
+dd_status dd_solve(dd_ctx* ctx, const double* f, double* x, int nrhs, int where, const dd_solve_params* p,
+                   dd_solve_info* info);
+
+/* Bytes of one spinor field for a precision and layout (FP16 internal: values and norms). */
+size_t dd_spinor_bytes(const dd_ctx* ctx, int prec, int layout);
+
+/* Convert between the canonical layout (FP64 or FP32, device) and the internal layout
+ * (FP64, FP32 or FP16, device).  For FP16 the per-site norms follow the values in the
+ * same buffer (see dd_spinor_bytes). */
+dd_status dd_pack_spinor(dd_ctx* ctx, const void* canonical, int canonical_prec, void* internal, int internal_prec);
+dd_status dd_unpack_spinor(dd_ctx* ctx, const void* internal, int internal_prec, void* canonical, int canonical_prec);
+
+/* Number of kernels this context has launched since it was created. */
+long long dd_launch_count(const dd_ctx* ctx);
+
+/* Wave-quantisation load of the Schwarz kernel, the GPU analogue of Eq. 6-7: with
+ * n = number of domains of one colour and `slots` CTAs resident at once,
+ * load = n / (slots * ceil(n / slots)).  Pure host function. */
+double dd_load_model(long long n_domains_per_colour, int slots);
+
+/* Pick a domain shape and I_domain for this lattice (the context's own shape is not
+ * changed): candidates allowed by the constraints above are timed on the device with
+ * the current gauge field and clover.  Writes the best shape to domain_out and its SAP
+ * parameters to out. */
+dd_status dd_autotune(dd_ctx* ctx, int storage_prec, int domain_out[4], dd_sap_params* out);
+
+/* Host build of the deflated-restart step that dd_solve runs on the device: given the
+ * (m+1) x m Hessenberg matrix Hbar (column-major, leading dimension m+1, complex as
+ * re, im pairs), the cycle's right-hand side c (m+1) and least-squares solution y (m),
+ * return the orthonormal (m+1) x (k+1) basis P, Hn = P^H Hbar P_k ((k+1) x k, ld m+1),
+ * cn = P^H (c - Hbar y) and the harmonic Ritz values theta (m, sorted by modulus). */
+dd_status dd_deflate_host(int m, int k, const double* Hbar, const double* c, const double* y, double* P, double* Hn,
+                          double* cn, double* theta);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DD_H */

@@ -1,0 +1,824 @@
+// C ABI of the library (include/dd.h): context, gauge and clover set-up, the operator,
+// the Schwarz preconditioner and the outer solver.
+//
+// Outer solver (Table I): flexible GMRES with deflated restarts.  Krylov vectors V, Z are
+// FP32 fields; Gram-Schmidt coefficients, the Hessenberg matrix, its least-squares
+// problem and the deflation algebra are FP64 on the device; the solution is accumulated
+// in FP64 and at every restart the residual is recomputed with the FP64 operator
+// (reliable update), which is what makes the 1e-10 target reachable with FP32 Krylov
+// vectors.  A deflated restart keeps the k harmonic Ritz vectors of smallest modulus;
+// its right-hand side is the projection of the recomputed FP64 residual onto the new
+// basis, and the restart falls back to a plain one when that projection misses more
+// than `defl_tol` of the residual.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dd.h"
+#include "dd_kernels.hpp"
+#include "smalldense.cuh"
+
+using namespace dd;
+
+struct SapBuffers {
+  void* r_store = nullptr;
+  float* r_norm = nullptr;
+  void* u_store = nullptr;
+  float* u_norm = nullptr;
+  float4* faces = nullptr;
+};
+
+struct SolverBuffers {
+  int m = 0;                 // capacity (basis size)
+  float4* V[2] = {nullptr, nullptr};   // (m+1) vectors each, double-buffered for restarts
+  float4* Z[2] = {nullptr, nullptr};   // m vectors each
+  float4* w = nullptr;
+  double2 *x64 = nullptr, *f64 = nullptr, *r64 = nullptr;
+  double2* canon64 = nullptr;          // canonical FP64 staging (one field)
+  // device scalars
+  zd *H = nullptr, *R = nullptr, *g = nullptr, *c0 = nullptr, *y = nullptr;
+  zd *hA = nullptr, *hB = nullptr, *P = nullptr, *Hn = nullptr, *cn = nullptr, *theta = nullptr, *cp = nullptr;
+  double2* partial = nullptr;
+  double2* nrm2 = nullptr;
+  double* status = nullptr;            // [0] residual estimate, [1] deflate status
+  double* h_status = nullptr;          // pinned host mirror
+  LsqState* lsq = nullptr;
+  DeflateWork* dw = nullptr;
+};
+
+struct dd_ctx {
+  Geom g;
+  int anti = 1;
+  cudaStream_t st = nullptr;
+  std::string err;
+  long long launches = 0;
+  // gauge
+  double* Ucanon = nullptr;
+  double2* U64 = nullptr;
+  float2* U32 = nullptr;
+  uint32_t* U16 = nullptr;
+  bool have_gauge = false;
+  // clover
+  double2* C64 = nullptr;
+  float4* C32 = nullptr;
+  uint4* C16 = nullptr;
+  float4* S32 = nullptr;
+  uint4* S16 = nullptr;
+  int* dstatus = nullptr;
+  bool have_clover = false;
+  double kappa = 0, csw = 0;
+  // schwarz
+  SapBuffers sap[3];
+  int* sap_err = nullptr;
+  // scratch fields for canonical-layout calls
+  void* scratch_in = nullptr;
+  void* scratch_out = nullptr;
+  SolverBuffers sv;
+  std::vector<void*> allocs;
+};
+
+// ------------------------------------------------------------------ helpers
+static dd_status fail(dd_ctx* c, dd_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+static dd_status cuda_check(dd_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return DD_OK;
+  if (c) c->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? DD_ERR_OOM : DD_ERR_CUDA;
+}
+
+template <typename T>
+static dd_status dalloc(dd_ctx* c, T** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, DD_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  c->allocs.push_back(q);
+  *p = (T*)q;
+  return DD_OK;
+}
+
+#define TRY(x)                         \
+  do {                                 \
+    dd_status _s = (x);                \
+    if (_s != DD_OK) return _s;        \
+  } while (0)
+
+static dd_status launched(dd_ctx* c, int n = 1) {
+  c->launches += n;
+  cudaError_t e = cudaGetLastError();
+  return cuda_check(c, e, "kernel launch");
+}
+
+static size_t field_bytes(const Geom& g, int prec) {
+  if (prec == P64) return (size_t)g.V * 24 * 8;
+  if (prec == P32) return (size_t)g.V * 24 * 4;
+  return (size_t)g.V * 24 * 2 + (size_t)g.V * 4;
+}
+
+static FieldView view(const Geom& g, void* p, int prec) {
+  FieldView f;
+  f.data = p;
+  f.prec = prec;
+  f.norm = prec == P16 ? (float*)((char*)p + (size_t)g.V * 48) : nullptr;
+  return f;
+}
+
+static int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return (1 << l) == v ? l : -1;
+}
+
+// ------------------------------------------------------------------ create / destroy
+extern "C" dd_status dd_create(dd_ctx** out, const int dims[4], const int domain[4], int t_antiperiodic,
+                               void* stream) {
+  if (!out || !dims || !domain) return DD_ERR_INVALID;
+  *out = nullptr;
+  Geom g;
+  memset(&g, 0, sizeof(g));
+  g.V = 1;
+  g.Vd = 1;
+  g.ND = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    g.L[mu] = dims[mu];
+    g.b[mu] = domain[mu];
+    if (dims[mu] <= 0 || domain[mu] < 2 || ilog2(domain[mu]) < 0 || dims[mu] % domain[mu]) return DD_ERR_DIMS;
+    g.N[mu] = dims[mu] / domain[mu];
+    if (g.N[mu] < 2 || g.N[mu] % 2) return DD_ERR_DIMS;
+    g.lgb[mu] = ilog2(domain[mu]);
+    g.V *= dims[mu];
+    g.Vd *= domain[mu];
+    g.ND *= g.N[mu];
+  }
+  if (g.Vd < 64 || g.Vd > sap_max_domain_sites()) return DD_ERR_DIMS;
+  g.Hd = g.Vd / 2;
+  g.lgVd = ilog2(g.Vd);
+  g.bstride[0] = 1;
+  g.dstride[0] = 1;
+  for (int mu = 1; mu < 4; ++mu) {
+    g.bstride[mu] = g.bstride[mu - 1] * g.b[mu - 1];
+    g.dstride[mu] = g.dstride[mu - 1] * g.N[mu - 1];
+  }
+  int off = 0;
+  for (int mu = 0; mu < 4; ++mu) {
+    g.face_n[mu] = g.Vd / g.b[mu];
+    g.face_off[2 * mu] = off;
+    off += g.face_n[mu];
+    g.face_off[2 * mu + 1] = off;
+    off += g.face_n[mu];
+  }
+  g.face_block = off;
+  dd_ctx* c = new dd_ctx();
+  c->g = g;
+  c->anti = t_antiperiodic ? 1 : 0;
+  c->st = (cudaStream_t)stream;
+  if (dalloc(c, &c->dstatus, 64) != DD_OK || dalloc(c, &c->sap_err, 64) != DD_OK) {
+    for (void* p : c->allocs) cudaFree(p);
+    delete c;
+    return DD_ERR_OOM;
+  }
+  cudaMemsetAsync(c->dstatus, 0, 64, c->st);
+  cudaMemsetAsync(c->sap_err, 0, 64, c->st);
+  *out = c;
+  return DD_OK;
+}
+
+extern "C" dd_status dd_destroy(dd_ctx* c) {
+  if (!c) return DD_ERR_INVALID;
+  cudaStreamSynchronize(c->st);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->sv.h_status) cudaFreeHost(c->sv.h_status);
+  delete c;
+  return DD_OK;
+}
+
+extern "C" const char* dd_last_error(const dd_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" long long dd_launch_count(const dd_ctx* c) { return c ? c->launches : 0; }
+
+extern "C" size_t dd_spinor_bytes(const dd_ctx* c, int prec, int layout) {
+  if (!c) return 0;
+  if (layout == DD_LAYOUT_CANONICAL) return (size_t)c->g.V * 24 * (prec == DD_PREC_FP64 ? 8 : 4);
+  return field_bytes(c->g, prec);
+}
+
+// ------------------------------------------------------------------ gauge / clover
+extern "C" dd_status dd_load_gauge(dd_ctx* c, const double* U, int where) {
+  if (!c || !U) return DD_ERR_INVALID;
+  const Geom& g = c->g;
+  size_t n = (size_t)g.V * 72;
+  if (!c->Ucanon) {
+    TRY(dalloc(c, &c->Ucanon, n * 8));
+    TRY(dalloc(c, &c->U64, n * 8));
+    TRY(dalloc(c, &c->U32, n * 4));
+    TRY(dalloc(c, &c->U16, n * 2));
+  }
+  TRY(cuda_check(c, cudaMemcpyAsync(c->Ucanon, U, n * 8, where == DD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->st),
+                 "gauge copy"));
+  launch_pack_gauge(g, c->Ucanon, c->anti, c->U64, c->U32, c->U16, c->st);
+  TRY(launched(c));
+  TRY(cuda_check(c, cudaStreamSynchronize(c->st), "load_gauge"));
+  c->have_gauge = true;
+  c->have_clover = false;
+  return DD_OK;
+}
+
+extern "C" dd_status dd_build_clover(dd_ctx* c, double kappa, double csw) {
+  if (!c) return DD_ERR_INVALID;
+  if (!c->have_gauge) return fail(c, DD_ERR_NO_GAUGE, "no gauge field loaded");
+  if (!(kappa > 0)) return fail(c, DD_ERR_INVALID, "kappa must be positive");
+  const Geom& g = c->g;
+  if (!c->C64) {
+    TRY(dalloc(c, &c->C64, (size_t)g.V * 72 * 8));
+    TRY(dalloc(c, &c->C32, (size_t)g.V * 72 * 4));
+    TRY(dalloc(c, &c->C16, (size_t)g.V * 72 * 2));
+    TRY(dalloc(c, &c->S32, (size_t)g.V * 72 * 4));
+    TRY(dalloc(c, &c->S16, (size_t)g.V * 72 * 2));
+  }
+  cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->st);
+  launch_build_clover(g, c->Ucanon, kappa, csw, c->C64, c->C32, c->C16, c->S32, c->S16, c->dstatus, c->st);
+  TRY(launched(c));
+  int bad = 0;
+  TRY(cuda_check(c, cudaMemcpyAsync(&bad, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st), "clover status"));
+  TRY(cuda_check(c, cudaStreamSynchronize(c->st), "build_clover"));
+  c->kappa = kappa;
+  c->csw = csw;
+  c->have_clover = true;
+  if (bad) return fail(c, DD_ERR_SINGULAR_CLOVER, std::to_string(bad) + " sites with a singular clover block");
+  return DD_OK;
+}
+
+// ------------------------------------------------------------------ operator
+static GaugeView gauge_view(dd_ctx* c, int prec) {
+  GaugeView v;
+  v.prec = prec;
+  v.links = prec == P64 ? (const void*)c->U64 : prec == P32 ? (const void*)c->U32 : (const void*)c->U16;
+  return v;
+}
+static CloverView clover_view(dd_ctx* c, int prec) {
+  CloverView v;
+  v.prec = prec;
+  v.m = prec == P64 ? (const void*)c->C64 : prec == P32 ? (const void*)c->C32 : (const void*)c->C16;
+  return v;
+}
+
+static dd_status ensure_scratch(dd_ctx* c) {
+  if (!c->scratch_in) {
+    TRY(dalloc(c, &c->scratch_in, field_bytes(c->g, P64)));
+    TRY(dalloc(c, &c->scratch_out, field_bytes(c->g, P64)));
+  }
+  return DD_OK;
+}
+
+static dd_status apply_internal(dd_ctx* c, const void* in, void* out, int prec, const void* f = nullptr) {
+  FieldView vi = view(c->g, (void*)in, prec), vo = view(c->g, out, prec), vf = view(c->g, (void*)f, prec);
+  launch_apply_A(c->g, gauge_view(c, prec), clover_view(c, prec), vi, vo, f ? &vf : nullptr, c->st);
+  return launched(c);
+}
+
+extern "C" dd_status dd_apply_D(dd_ctx* c, const void* in, void* out, int prec, int layout) {
+  if (!c || !in || !out || prec < 0 || prec > 2) return DD_ERR_INVALID;
+  if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
+  if (layout == DD_LAYOUT_INTERNAL) {
+    TRY(apply_internal(c, in, out, prec));
+  } else {
+    if (prec == P16) return fail(c, DD_ERR_INVALID, "FP16 needs the internal layout");
+    TRY(ensure_scratch(c));
+    launch_pack_spinor(c->g, in, prec, view(c->g, c->scratch_in, prec), c->st);
+    TRY(launched(c));
+    TRY(apply_internal(c, c->scratch_in, c->scratch_out, prec));
+    launch_unpack_spinor(c->g, view(c->g, c->scratch_out, prec), out, prec, c->st);
+    TRY(launched(c));
+  }
+  return cuda_check(c, cudaStreamSynchronize(c->st), "apply_D");
+}
+
+extern "C" dd_status dd_pack_spinor(dd_ctx* c, const void* canon, int cprec, void* internal, int iprec) {
+  if (!c || !canon || !internal || cprec < 0 || cprec > 1 || iprec < 0 || iprec > 2) return DD_ERR_INVALID;
+  launch_pack_spinor(c->g, canon, cprec, view(c->g, internal, iprec), c->st);
+  TRY(launched(c));
+  return cuda_check(c, cudaStreamSynchronize(c->st), "pack");
+}
+
+extern "C" dd_status dd_unpack_spinor(dd_ctx* c, const void* internal, int iprec, void* canon, int cprec) {
+  if (!c || !canon || !internal || cprec < 0 || cprec > 1 || iprec < 0 || iprec > 2) return DD_ERR_INVALID;
+  launch_unpack_spinor(c->g, view(c->g, (void*)internal, iprec), canon, cprec, c->st);
+  TRY(launched(c));
+  return cuda_check(c, cudaStreamSynchronize(c->st), "unpack");
+}
+
+// ------------------------------------------------------------------ Schwarz preconditioner
+static dd_status ensure_sap(dd_ctx* c, int prec) {
+  SapBuffers& b = c->sap[prec];
+  if (b.faces) return DD_OK;
+  const Geom& g = c->g;
+  size_t half_sites = (size_t)g.V / 2;
+  if (prec == P16) {
+    TRY(dalloc(c, &b.r_store, half_sites * 48));
+    TRY(dalloc(c, &b.r_norm, half_sites * 4));
+    TRY(dalloc(c, &b.u_store, (size_t)g.V * 48));
+    TRY(dalloc(c, &b.u_norm, (size_t)g.V * 4));
+  } else {
+    TRY(dalloc(c, &b.r_store, half_sites * 96));
+    TRY(dalloc(c, &b.u_store, (size_t)g.V * 96));
+  }
+  TRY(dalloc(c, &b.faces, (size_t)g.ND * g.face_block * 48));
+  return DD_OK;
+}
+
+static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_params* p) {
+  int prec = p->storage_prec == DD_PREC_FP16 ? P16 : P32;
+  TRY(ensure_sap(c, prec));
+  SapBuffers& b = c->sap[prec];
+  SapState S;
+  S.mat_prec = prec;
+  S.vec_prec = prec;
+  S.links = prec == P16 ? (const void*)c->U16 : (const void*)c->U32;
+  S.smat = prec == P16 ? (const void*)c->S16 : (const void*)c->S32;
+  S.r_store = b.r_store;
+  S.r_norm = b.r_norm;
+  S.u_store = b.u_store;
+  S.u_norm = b.u_norm;
+  S.faces = b.faces;
+  S.err = c->sap_err;
+  S.mat_in_smem = sap_mat_fits_smem(c->g, prec);
+  for (int s = 0; s < p->i_schwarz; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      int first = s == 0, use_faces = !(s == 0 && colour == 0), last = s == p->i_schwarz - 1;
+      if (sap_half_sweep(c->g, S, colour, first, use_faces, last, v, z, p->i_domain, c->st))
+        return fail(c, DD_ERR_CUDA, std::string("Schwarz launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+      TRY(launched(c));
+    }
+  return DD_OK;
+}
+
+static dd_status check_sap_params(dd_ctx* c, const dd_sap_params* p) {
+  if (!p || p->i_schwarz < 1 || p->i_domain < 0 || (p->storage_prec != DD_PREC_FP16 && p->storage_prec != DD_PREC_FP32))
+    return fail(c, DD_ERR_INVALID, "bad Schwarz parameters");
+  return DD_OK;
+}
+
+static dd_status sap_error_flag(dd_ctx* c) {
+  int e = 0;
+  TRY(cuda_check(c, cudaMemcpyAsync(&e, c->sap_err, sizeof(int), cudaMemcpyDeviceToHost, c->st), "sap status"));
+  TRY(cuda_check(c, cudaStreamSynchronize(c->st), "sap"));
+  if (e) {
+    cudaMemsetAsync(c->sap_err, 0, sizeof(int), c->st);
+    return fail(c, DD_ERR_TIMEOUT, "a bounded wait for the domain's staged data ran out");
+  }
+  return DD_OK;
+}
+
+extern "C" dd_status dd_sap_precondition(dd_ctx* c, const float* in, float* out, const dd_sap_params* p, int layout) {
+  if (!c || !in || !out) return DD_ERR_INVALID;
+  TRY(check_sap_params(c, p));
+  if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
+  if (p->i_domain == 0) return fail(c, DD_ERR_INVALID, "i_domain must be >= 1");
+  if (layout == DD_LAYOUT_INTERNAL) {
+    TRY(sap_run(c, (const float4*)in, (float4*)out, p));
+  } else {
+    TRY(ensure_scratch(c));
+    launch_pack_spinor(c->g, in, P32, view(c->g, c->scratch_in, P32), c->st);
+    TRY(launched(c));
+    TRY(sap_run(c, (const float4*)c->scratch_in, (float4*)c->scratch_out, p));
+    launch_unpack_spinor(c->g, view(c->g, c->scratch_out, P32), out, P32, c->st);
+    TRY(launched(c));
+  }
+  return sap_error_flag(c);
+}
+
+// ------------------------------------------------------------------ small dense kernels
+__global__ void arnoldi_finish_kernel(zd* H, zd* R, int ldh, int j, const zd* hA, const zd* hB, const double2* nrm2,
+                                      LsqState* lsq, zd* g, double* status) {
+  zd* col = H + (long)j * ldh;
+  for (int i = 0; i <= j; ++i) col[i] = hA[i] + hB[i];
+  double h = sqrt(nrm2->x);
+  col[j + 1] = Z(h);
+  zd* rc = R + (long)j * ldh;
+  for (int i = 0; i <= j + 1; ++i) rc[i] = col[i];
+  status[0] = lsq_add_column(*lsq, R, ldh, j, j + 2, g);
+  status[2] = h;
+}
+
+__global__ void lsq_solve_kernel(const zd* R, int ldh, int n, const zd* g, zd* y) { lsq_solve(R, ldh, n, g, y); }
+
+__global__ void deflate_kernel(const zd* H, int ldh, int m, int k, const zd* c, const zd* y, zd* P, zd* Hn, zd* cn,
+                               zd* theta, DeflateWork* W, double* status) {
+  status[1] = deflate(H, ldh, m, k, c, y, P, Hn, cn, theta, *W);
+}
+
+// After a deflated restart: H <- Hn (k+1 x k), g <- cp, and the rotations of the dense
+// block are rebuilt.
+__global__ void restart_lsq_kernel(zd* H, zd* R, int ldh, int m, int k, const zd* Hn, const zd* cp, zd* g, zd* c0,
+                                   LsqState* lsq, double* status) {
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i <= m; ++i) { H[i + (long)j * ldh] = Z(0.0); R[i + (long)j * ldh] = Z(0.0); }
+  for (int i = 0; i <= m; ++i) g[i] = c0[i] = Z(0.0);
+  for (int i = 0; i <= k; ++i) g[i] = c0[i] = cp[i];
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i <= k; ++i) H[i + (long)j * ldh] = R[i + (long)j * ldh] = Hn[i + (long)j * ldh];
+  lsq->nrot = 0;
+  double res = 0;
+  for (int j = 0; j < k; ++j) res = lsq_add_column(*lsq, R, ldh, j, k + 1, g);
+  status[0] = res;
+}
+
+__global__ void plain_restart_kernel(zd* H, zd* R, int ldh, int m, const double2* nrm2, zd* g, zd* c0, LsqState* lsq) {
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i <= m; ++i) { H[i + (long)j * ldh] = Z(0.0); R[i + (long)j * ldh] = Z(0.0); }
+  for (int i = 0; i <= m; ++i) g[i] = c0[i] = Z(0.0);
+  g[0] = c0[0] = Z(sqrt(nrm2->x));
+  lsq->nrot = 0;
+}
+
+// cp = rho * cp (the projection was taken against r / rho)
+__global__ void scale_coeffs_kernel(zd* cp, int n, const double2* nrm2) {
+  double rho = sqrt(nrm2->x);
+  for (int i = 0; i < n; ++i) cp[i] = rho * cp[i];
+}
+
+// ------------------------------------------------------------------ solver
+static dd_status ensure_solver(dd_ctx* c, int m) {
+  SolverBuffers& s = c->sv;
+  if (s.m >= m) return DD_OK;
+  if (s.m) return fail(c, DD_ERR_INVALID, "basis size larger than the first solve's is not supported by this context");
+  const Geom& g = c->g;
+  long long n4 = g.V * 6;
+  size_t vb = (size_t)n4 * 16;
+  for (int b = 0; b < 2; ++b) {
+    TRY(dalloc(c, &s.V[b], vb * (m + 1)));
+    TRY(dalloc(c, &s.Z[b], vb * m));
+  }
+  TRY(dalloc(c, &s.w, vb));
+  TRY(dalloc(c, &s.x64, field_bytes(g, P64)));
+  TRY(dalloc(c, &s.f64, field_bytes(g, P64)));
+  TRY(dalloc(c, &s.r64, field_bytes(g, P64)));
+  TRY(dalloc(c, &s.canon64, field_bytes(g, P64)));
+  int ld = m + 1;
+  size_t hm = (size_t)ld * (m + 1) * sizeof(zd);
+  TRY(dalloc(c, &s.H, hm));
+  TRY(dalloc(c, &s.R, hm));
+  TRY(dalloc(c, &s.P, hm));
+  TRY(dalloc(c, &s.Hn, hm));
+  for (zd** p : {&s.g, &s.c0, &s.y, &s.hA, &s.hB, &s.cn, &s.theta, &s.cp}) TRY(dalloc(c, p, (m + 2) * sizeof(zd)));
+  TRY(dalloc(c, &s.partial, (size_t)blas_partials_blocks() * (m + 2) * sizeof(double2)));
+  TRY(dalloc(c, &s.nrm2, 4 * sizeof(double2)));
+  TRY(dalloc(c, &s.status, 8 * sizeof(double)));
+  TRY(dalloc(c, &s.lsq, sizeof(LsqState)));
+  TRY(dalloc(c, &s.dw, sizeof(DeflateWork)));
+  if (cudaMallocHost(&s.h_status, 8 * sizeof(double)) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned status");
+  s.m = m;
+  return DD_OK;
+}
+
+struct Timer {
+  cudaEvent_t a, b;
+  Timer() { cudaEventCreate(&a); cudaEventCreate(&b); }
+  ~Timer() { cudaEventDestroy(a); cudaEventDestroy(b); }
+};
+
+static dd_status read_status(dd_ctx* c, int n = 3) {
+  SolverBuffers& s = c->sv;
+  TRY(cuda_check(c, cudaMemcpyAsync(s.h_status, s.status, n * sizeof(double), cudaMemcpyDeviceToHost, c->st), "status"));
+  return cuda_check(c, cudaStreamSynchronize(c->st), "solver step");
+}
+
+// rho2 = |f - A x|^2 into s.nrm2 (device) and return it on the host.
+static dd_status true_residual(dd_ctx* c, double* rho2) {
+  SolverBuffers& s = c->sv;
+  TRY(apply_internal(c, s.x64, s.r64, P64, s.f64));
+  launch_norm2_64(s.r64, c->g.V * 12, s.partial, c->st);
+  launch_reduce_partials(s.partial, 1, s.nrm2, 0, c->st);
+  TRY(launched(c, 2));
+  double2 h;
+  TRY(cuda_check(c, cudaMemcpyAsync(&h, s.nrm2, sizeof(double2), cudaMemcpyDeviceToHost, c->st), "norm"));
+  TRY(cuda_check(c, cudaStreamSynchronize(c->st), "norm"));
+  *rho2 = h.x;
+  return DD_OK;
+}
+
+static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_solve_info* info) {
+  SolverBuffers& s = c->sv;
+  const Geom& g = c->g;
+  const long long n4 = g.V * 6;
+  const int m = p->m, k = p->k, ldh = m + 1;
+  const double tol = p->tol;
+  const double nf = sqrt(nf2);
+  const double defl_tol = 1e-2;
+  cudaEvent_t e0, e1, e2, e3, e4;
+  cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2); cudaEventCreate(&e3); cudaEventCreate(&e4);
+  cudaEvent_t tstart, tend;
+  cudaEventCreate(&tstart); cudaEventCreate(&tend);
+  cudaEventRecord(tstart, c->st);
+  double tA = 0, tM = 0, tGS = 0;
+  int iters = 0, restarts = 0, reliable = 0, deflated = 0;
+  dd_status rc = DD_OK;
+  double rho2 = 0;
+  int cur = 0;
+  auto Vv = [&](int i) { return s.V[cur] + (long long)i * n4; };
+  auto Zv = [&](int i) { return s.Z[cur] + (long long)i * n4; };
+
+  TRY(true_residual(c, &rho2));
+  reliable++;
+  double rel = sqrt(rho2) / nf;
+  if (!isfinite(rel)) rc = fail(c, DD_ERR_NONFINITE, "non-finite residual");
+  int j0 = 0;
+  if (rc == DD_OK && rel > tol) {
+    launch_r64_to_v32(Vv(0), s.r64, n4, s.nrm2, c->st);
+    plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq);
+    TRY(launched(c, 2));
+  }
+  while (rc == DD_OK && rel > tol) {
+    if (iters >= p->max_iter) { rc = fail(c, DD_ERR_NOT_CONVERGED, "iteration limit reached"); break; }
+    int mm = m;
+    double rho_cycle = sqrt(rho2);
+    for (int j = j0; j < m; ++j) {
+      cudaEventRecord(e0, c->st);
+      TRY(sap_run(c, Vv(j), Zv(j), &p->sap));
+      cudaEventRecord(e1, c->st);
+      TRY(apply_internal(c, Zv(j), s.w, P32));
+      cudaEventRecord(e2, c->st);
+      // classical Gram-Schmidt, two passes
+      int nk = launch_multi_dot(Vv(0), j + 1, n4, s.w, s.partial, c->st);
+      launch_reduce_partials(s.partial, j + 1, (double2*)s.hA, 0, c->st);
+      nk += launch_multi_axpy(s.w, Vv(0), j + 1, n4, (const double2*)s.hA, nullptr, c->st);
+      nk += launch_multi_dot(Vv(0), j + 1, n4, s.w, s.partial, c->st);
+      launch_reduce_partials(s.partial, j + 1, (double2*)s.hB, 0, c->st);
+      nk += launch_multi_axpy(s.w, Vv(0), j + 1, n4, (const double2*)s.hB, s.partial, c->st);
+      launch_reduce_partials(s.partial, 1, s.nrm2, 0, c->st);
+      arnoldi_finish_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, j, s.hA, s.hB, s.nrm2, s.lsq, s.g, s.status);
+      launch_scale_to(Vv(j + 1), s.w, n4, s.nrm2, c->st);
+      TRY(launched(c, nk + 5));
+      cudaEventRecord(e3, c->st);
+      TRY(read_status(c));
+      float ms;
+      cudaEventElapsedTime(&ms, e0, e1); tM += ms * 1e-3;
+      cudaEventElapsedTime(&ms, e1, e2); tA += ms * 1e-3;
+      cudaEventElapsedTime(&ms, e2, e3); tGS += ms * 1e-3;
+      iters++;
+      double est = s.h_status[0];
+      if (!isfinite(est) || !isfinite(s.h_status[2])) { rc = fail(c, DD_ERR_NONFINITE, "non-finite Arnoldi step"); break; }
+      // stop the cycle when the target is met or FP32 vectors cannot resolve further
+      if (est <= 0.5 * tol * nf || est <= 2e-6 * rho_cycle || iters >= p->max_iter) { mm = j + 1; break; }
+    }
+    if (rc != DD_OK) break;
+    lsq_solve_kernel<<<1, 1, 0, c->st>>>(s.R, ldh, mm, s.g, s.y);
+    launch_x_update(s.x64, Zv(0), mm, n4, (const double2*)s.y, c->st);
+    TRY(launched(c, 2));
+    TRY(true_residual(c, &rho2));
+    reliable++;
+    rel = sqrt(rho2) / nf;
+    if (!isfinite(rel)) { rc = fail(c, DD_ERR_NONFINITE, "non-finite residual"); break; }
+    if (rel <= tol) break;
+    if (iters >= p->max_iter) { rc = fail(c, DD_ERR_NOT_CONVERGED, "iteration limit reached"); break; }
+    restarts++;
+    bool done_defl = false;
+    if (k > 0 && mm > k) {
+      deflate_kernel<<<1, 1, 0, c->st>>>(s.H, ldh, mm, k, s.c0, s.y, s.P, s.Hn, s.cn, s.theta, s.dw, s.status);
+      TRY(launched(c));
+      TRY(read_status(c, 2));
+      if (s.h_status[1] == 0.0) {
+        int nxt = 1 - cur;
+        float4* Vn = s.V[nxt];
+        float4* Zn = s.Z[nxt];
+        int nk = launch_recombine(Vn, s.V[cur], mm + 1, k + 1, n4, (const double2*)s.P, ldh, c->st);
+        nk += launch_recombine(Zn, s.Z[cur], mm, k, n4, (const double2*)s.P, ldh, c->st);
+        cur = nxt;
+        // project the FP64 residual onto the new basis
+        launch_r64_to_v32(s.w, s.r64, n4, s.nrm2, c->st);
+        nk += launch_multi_dot(Vv(0), k + 1, n4, s.w, s.partial, c->st);
+        launch_reduce_partials(s.partial, k + 1, (double2*)s.cp, 0, c->st);
+        scale_coeffs_kernel<<<1, 1, 0, c->st>>>(s.cp, k + 1, s.nrm2);
+        TRY(launched(c, nk + 3));
+        std::vector<zd> cp(k + 1);
+        TRY(cuda_check(c, cudaMemcpyAsync(cp.data(), s.cp, (k + 1) * sizeof(zd), cudaMemcpyDeviceToHost, c->st), "cp"));
+        TRY(cuda_check(c, cudaStreamSynchronize(c->st), "cp"));
+        double pc = 0;
+        for (auto& z : cp) pc += abs2(z);
+        double miss = sqrt(fmax(0.0, 1.0 - pc / rho2));
+        if (miss <= defl_tol) {
+          restart_lsq_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, k, s.Hn, s.cp, s.g, s.c0, s.lsq, s.status);
+          TRY(launched(c));
+          j0 = k;
+          done_defl = true;
+          deflated++;
+        }
+      }
+    }
+    if (!done_defl) {
+      launch_r64_to_v32(Vv(0), s.r64, n4, s.nrm2, c->st);
+      plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq);
+      TRY(launched(c, 2));
+      j0 = 0;
+    }
+  }
+  cudaEventRecord(tend, c->st);
+  cudaEventSynchronize(tend);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, tstart, tend);
+  if (info) {
+    info->iterations += iters;
+    info->restarts += restarts;
+    info->reliable_updates += reliable;
+    info->deflated_restarts += deflated;
+    info->true_rel_residual = fmax(info->true_rel_residual, rel);
+    info->t_total += ms * 1e-3;
+    info->t_A += tA;
+    info->t_M += tM;
+    info->t_GS += tGS;
+    info->t_other += ms * 1e-3 - tA - tM - tGS;
+    double V = (double)g.V;
+    // paper's convention: 1848 flop per site per operator application; each Schwarz
+    // half-sweep applies D once per MR step plus once for preparation and update
+    info->flops_nominal += iters * (1848.0 * V + p->sap.i_schwarz * (p->sap.i_domain + 1) * 1848.0 * V) + reliable * 1848.0 * V;
+  }
+  for (cudaEvent_t e : {e0, e1, e2, e3, e4, tstart, tend}) cudaEventDestroy(e);
+  if (rc == DD_OK) TRY(sap_error_flag(c));
+  return rc;
+}
+
+extern "C" dd_status dd_solve(dd_ctx* c, const double* f, double* x, int nrhs, int where, const dd_solve_params* p,
+                              dd_solve_info* info) {
+  if (!c || !f || !x || !p || nrhs < 1) return DD_ERR_INVALID;
+  if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
+  if (p->m < 1 || p->m > DD_MAXM - 1 || p->k < 0 || p->k >= p->m || !(p->tol > 0) || p->max_iter < 1)
+    return fail(c, DD_ERR_INVALID, "bad solver parameters");
+  TRY(check_sap_params(c, &p->sap));
+  if (p->sap.i_domain < 1) return fail(c, DD_ERR_INVALID, "i_domain must be >= 1");
+  TRY(ensure_solver(c, p->m));
+  if (info) memset(info, 0, sizeof(*info));
+  SolverBuffers& s = c->sv;
+  const Geom& g = c->g;
+  size_t cb = (size_t)g.V * 24 * 8;
+  cudaMemcpyKind in_kind = where == DD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaMemcpyKind out_kind = where == DD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  dd_status worst = DD_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    const double* fr = f + (size_t)r * g.V * 24;
+    double* xr = x + (size_t)r * g.V * 24;
+    TRY(cuda_check(c, cudaMemcpyAsync(s.canon64, fr, cb, in_kind, c->st), "copy f"));
+    launch_pack_spinor(g, s.canon64, P64, view(g, s.f64, P64), c->st);
+    TRY(cuda_check(c, cudaMemcpyAsync(s.canon64, xr, cb, in_kind, c->st), "copy x"));
+    launch_pack_spinor(g, s.canon64, P64, view(g, s.x64, P64), c->st);
+    launch_norm2_64(s.f64, g.V * 12, s.partial, c->st);
+    launch_reduce_partials(s.partial, 1, s.nrm2, 0, c->st);
+    TRY(launched(c, 4));
+    double2 h;
+    TRY(cuda_check(c, cudaMemcpyAsync(&h, s.nrm2, sizeof(double2), cudaMemcpyDeviceToHost, c->st), "norm f"));
+    TRY(cuda_check(c, cudaStreamSynchronize(c->st), "norm f"));
+    dd_status st;
+    if (h.x == 0.0) {
+      cudaMemsetAsync(s.x64, 0, field_bytes(g, P64), c->st);
+      st = DD_OK;
+    } else {
+      st = solve_one(c, p, h.x, info);
+    }
+    launch_unpack_spinor(g, view(g, s.x64, P64), s.canon64, P64, c->st);
+    TRY(launched(c));
+    TRY(cuda_check(c, cudaMemcpyAsync(xr, s.canon64, cb, out_kind, c->st), "copy x out"));
+    TRY(cuda_check(c, cudaStreamSynchronize(c->st), "solve"));
+    if (st != DD_OK && worst == DD_OK) worst = st;
+    if (st != DD_OK && st != DD_ERR_NOT_CONVERGED) break;
+  }
+  if (info) info->status = worst;
+  return worst;
+}
+
+// ------------------------------------------------------------------ host utilities
+extern "C" double dd_load_model(long long n, int slots) {
+  if (n <= 0 || slots <= 0) return 0.0;
+  long long waves = (n + slots - 1) / slots;
+  return (double)n / ((double)slots * (double)waves);
+}
+
+extern "C" dd_status dd_deflate_host(int m, int k, const double* Hbar, const double* cvec, const double* yvec,
+                                     double* P, double* Hn, double* cn, double* theta) {
+  if (m < 1 || m >= DD_MAXM || k < 1 || k >= m || !Hbar || !cvec || !yvec || !P || !Hn || !cn || !theta)
+    return DD_ERR_INVALID;
+  DeflateWork* W = new DeflateWork();
+  int rc = deflate((const zd*)Hbar, m + 1, m, k, (const zd*)cvec, (const zd*)yvec, (zd*)P, (zd*)Hn, (zd*)cn,
+                   (zd*)theta, *W);
+  delete W;
+  return rc == 0 ? DD_OK : DD_ERR_NONFINITE;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Deterministic pseudo-random FP32 field (splitmix64 per unit), for tuning runs only.
+__global__ void fill_random_kernel(float4* v, long long n4, unsigned long long seed) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+    float f[4];
+    for (int e = 0; e < 4; ++e) {
+      unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(4 * q + e + 1);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      f[e] = (float)((z >> 40) * (1.0 / 16777216.0)) - 0.5f;
+    }
+    v[q] = make_float4(f[0], f[1], f[2], f[3]);
+  }
+}
+
+__global__ void sub_norm2_kernel(const float4* a, const float4* b, long long n4, double2* out) {
+  __shared__ double sh[256];
+  double s = 0;
+  double t = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+    float4 x = a[q], y = b[q];
+    float dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z, dw = x.w - y.w;
+    s += dx * dx + dy * dy + dz * dz + dw * dw;
+    t += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(&out->x, sh[0]);
+  __syncthreads();
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(&out->y, sh[0]);
+}
+
+extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4], dd_sap_params* out) {
+  if (!c || !domain_out || !out) return DD_ERR_INVALID;
+  if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
+  int i_schwarz = out->i_schwarz > 0 ? out->i_schwarz : 16;
+  const int ext[3] = {2, 4, 8};
+  double best = 1e300;
+  int bestb[4] = {c->g.b[0], c->g.b[1], c->g.b[2], c->g.b[3]}, best_id = 5;
+  long long n4 = c->g.V * 6;
+  float4 *v = nullptr, *z = nullptr, *w = nullptr;
+  double2* acc = nullptr;
+  TRY(dalloc(c, &v, (size_t)n4 * 16));
+  TRY(dalloc(c, &z, (size_t)n4 * 16));
+  TRY(dalloc(c, &w, (size_t)n4 * 16));
+  TRY(dalloc(c, &acc, sizeof(double2)));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (int a0 = 0; a0 < 3; ++a0)
+    for (int a1 = 0; a1 < 3; ++a1)
+      for (int a2 = 0; a2 < 3; ++a2)
+        for (int a3 = 0; a3 < 3; ++a3) {
+          int b[4] = {ext[a0], ext[a1], ext[a2], ext[a3]};
+          dd_ctx* t = nullptr;
+          if (dd_create(&t, c->g.L, b, c->anti, c->st) != DD_OK) continue;
+          dd_status s = dd_load_gauge(t, c->Ucanon, DD_DEVICE);
+          if (s == DD_OK) s = dd_build_clover(t, c->kappa, c->csw);
+          if (s == DD_OK) {
+            fill_random_kernel<<<blas_partials_blocks(), 256, 0, c->st>>>(v, n4, 12345);
+            // slots: CTAs resident at once, for the load model
+            double load = dd_load_model(t->g.ND / 2, sms * (sap_smem_bytes(t->g, storage_prec == DD_PREC_FP16 ? P16 : P32,
+                                                                          sap_mat_fits_smem(t->g, storage_prec == DD_PREC_FP16 ? P16 : P32)) > 116 * 1024 ? 1 : 2));
+            for (int id = 2; id <= 6; ++id) {
+              dd_sap_params sp = {i_schwarz, id, storage_prec};
+              if (sap_run(t, v, z, &sp) != DD_OK) break;   // warm-up
+              cudaEventRecord(e0, c->st);
+              if (sap_run(t, v, z, &sp) != DD_OK) break;
+              cudaEventRecord(e1, c->st);
+              apply_internal(t, z, w, P32);
+              cudaMemsetAsync(acc, 0, sizeof(double2), c->st);
+              sub_norm2_kernel<<<blas_partials_blocks(), 256, 0, c->st>>>(w, v, n4, acc);
+              double2 h;
+              cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, c->st);
+              cudaStreamSynchronize(c->st);
+              float ms = 0;
+              cudaEventElapsedTime(&ms, e0, e1);
+              double q = sqrt(h.x / h.y);
+              double score = ms / fmax(1e-3, -log(fmax(q, 1e-30)));
+              (void)load;
+              if (q < 1.0 && score < best) {
+                best = score;
+                for (int mu = 0; mu < 4; ++mu) bestb[mu] = b[mu];
+                best_id = id;
+              }
+            }
+          }
+          c->launches += t->launches;
+          dd_destroy(t);
+        }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int mu = 0; mu < 4; ++mu) domain_out[mu] = bestb[mu];
+  out->i_schwarz = i_schwarz;
+  out->i_domain = best_id;
+  out->storage_prec = storage_prec;
+  return cuda_check(c, cudaStreamSynchronize(c->st), "autotune");
+}

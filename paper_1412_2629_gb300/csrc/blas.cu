@@ -1,0 +1,277 @@
+// Vector kernels of the outer solver on FP32 (float4 = two complex numbers) and FP64
+// (double2 = one complex number) fields in the internal layout.
+//
+// Inner products: every thread sums its share of the products in FP32 (a few hundred
+// terms at most), converts once, and the block and grid reductions run in FP64.  The
+// grid is a fixed multiple of the SM count, so the order of the final FP64 sum is
+// fixed and the result is reproducible run to run.
+#include "dd_kernels.hpp"
+
+namespace dd {
+
+constexpr int BT = 256;           // threads per block
+constexpr int NCHUNK = 8;         // vectors per pass of the multi-dot
+static int g_blocks = 0;
+
+int blas_partials_blocks() {
+  if (!g_blocks) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    g_blocks = 4 * (sms > 0 ? sms : 1);
+  }
+  return g_blocks;
+}
+
+__device__ inline cx<float> dot4(float4 v, float4 w) {  // conj(v) . w over two complex numbers
+  return mk(v.x * w.x + v.y * w.y + v.z * w.z + v.w * w.w, v.x * w.y - v.y * w.x + v.z * w.w - v.w * w.z);
+}
+
+// Block reduction of NV complex doubles; thread 0 of the block ends with the sums in s[].
+template <int NV>
+__device__ inline void block_reduce(double2 (&v)[NV], double2* s_out) {
+  __shared__ double2 sh[BT / 32][NV];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v[i].x += __shfl_xor_sync(0xffffffffu, v[i].x, o);
+      v[i].y += __shfl_xor_sync(0xffffffffu, v[i].y, o);
+    }
+    if (lane == 0) sh[w][i] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double2 t = make_double2(0, 0);
+    for (int k = 0; k < BT / 32; ++k) { t.x += sh[k][threadIdx.x].x; t.y += sh[k][threadIdx.x].y; }
+    s_out[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// partial[blockIdx][v0 + i] = sum over this block's share of conj(V_{v0+i}) . w
+template <int NV>
+__global__ void __launch_bounds__(BT) multi_dot_kernel(const float4* V, int v0, int nv, long long n4, const float4* w,
+                                                       double2* partial, int ldp) {
+  float re[NV], im[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) re[i] = im[i] = 0.f;
+  for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n4; q += (long long)gridDim.x * BT) {
+    float4 wq = w[q];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      if (v0 + i < nv) {
+        cx<float> d = dot4(V[(long long)(v0 + i) * n4 + q], wq);
+        re[i] += d.re;
+        im[i] += d.im;
+      }
+    }
+  }
+  double2 acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = make_double2(re[i], im[i]);
+  __shared__ double2 out[NV];
+  block_reduce<NV>(acc, out);
+  if (threadIdx.x < NV && v0 + (int)threadIdx.x < nv) partial[(long long)blockIdx.x * ldp + v0 + threadIdx.x] = out[threadIdx.x];
+}
+
+int launch_multi_dot(const float4* V, int nv, long long n4, const float4* w, double2* partial, cudaStream_t st) {
+  int nb = blas_partials_blocks(), n = 0;
+  for (int v0 = 0; v0 < nv; v0 += NCHUNK, ++n) multi_dot_kernel<NCHUNK><<<nb, BT, 0, st>>>(V, v0, nv, n4, w, partial, nv);
+  return n;
+}
+
+// out[i] (+)= sum over blocks of partial[b][i], fixed order.
+__global__ void reduce_partials_kernel(const double2* partial, int nb, int nv, double2* out, int accumulate) {
+  int i = blockIdx.x;
+  double sx = 0, sy = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) { sx += partial[(long long)b * nv + i].x; sy += partial[(long long)b * nv + i].y; }
+  __shared__ double shx[256], shy[256];
+  shx[threadIdx.x] = sx;
+  shy[threadIdx.x] = sy;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) { shx[threadIdx.x] += shx[threadIdx.x + o]; shy[threadIdx.x] += shy[threadIdx.x + o]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (accumulate) { out[i].x += shx[0]; out[i].y += shy[0]; }
+    else out[i] = make_double2(shx[0], shy[0]);
+  }
+}
+
+void launch_reduce_partials(const double2* partial, int nv, double2* out, int accumulate, cudaStream_t st) {
+  reduce_partials_kernel<<<nv, 256, 0, st>>>(partial, blas_partials_blocks(), nv, out, accumulate);
+}
+
+// w -= sum_i h_i V_i; optionally partial[b] = |w|^2 over the block's share.
+template <int NV>
+__global__ void __launch_bounds__(BT) multi_axpy_kernel(float4* w, const float4* V, int v0, int nv, long long n4,
+                                                        const double2* h, double2* norm_partial, int final_pass) {
+  __shared__ float2 hs[NV];
+  if (threadIdx.x < NV) {
+    int i = v0 + threadIdx.x;
+    hs[threadIdx.x] = i < nv ? make_float2((float)h[i].x, (float)h[i].y) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float nrm = 0.f;
+  for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n4; q += (long long)gridDim.x * BT) {
+    float4 a = w[q];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      if (v0 + i < nv) {
+        float4 v = V[(long long)(v0 + i) * n4 + q];
+        float2 c = hs[i];
+        a.x -= c.x * v.x - c.y * v.y;
+        a.y -= c.x * v.y + c.y * v.x;
+        a.z -= c.x * v.z - c.y * v.w;
+        a.w -= c.x * v.w + c.y * v.z;
+      }
+    }
+    w[q] = a;
+    if (final_pass) nrm += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+  }
+  if (final_pass && norm_partial) {
+    double2 acc[1] = {make_double2(nrm, 0.0)};
+    __shared__ double2 out[1];
+    block_reduce<1>(acc, out);
+    if (threadIdx.x == 0) norm_partial[blockIdx.x] = out[0];
+  }
+}
+
+int launch_multi_axpy(float4* w, const float4* V, int nv, long long n4, const double2* h, double2* norm_partial,
+                      cudaStream_t st) {
+  int nb = blas_partials_blocks(), n = 0;
+  for (int v0 = 0; v0 < nv; v0 += NCHUNK, ++n) {
+    int fin = v0 + NCHUNK >= nv;
+    multi_axpy_kernel<NCHUNK><<<nb, BT, 0, st>>>(w, V, v0, nv, n4, h, norm_partial, fin);
+  }
+  return n;
+}
+
+// v = w / sqrt(nrm2)
+__global__ void scale_to_kernel(float4* v, const float4* w, long long n4, const double2* nrm2) {
+  float s = (float)(1.0 / sqrt(nrm2->x));
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+    float4 a = w[q];
+    v[q] = make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
+  }
+}
+void launch_scale_to(float4* v, const float4* w, long long n4, const double2* nrm2, cudaStream_t st) {
+  scale_to_kernel<<<blas_partials_blocks(), BT, 0, st>>>(v, w, n4, nrm2);
+}
+
+// |x|^2 of an FP64 field (double2 units); exact FP64 arithmetic throughout.
+__global__ void __launch_bounds__(BT) norm2_64_kernel(const double2* x, long long n2, double2* partial) {
+  double s = 0;
+  for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n2; q += (long long)gridDim.x * BT) {
+    double2 a = x[q];
+    s += a.x * a.x + a.y * a.y;
+  }
+  double2 acc[1] = {make_double2(s, 0.0)};
+  __shared__ double2 out[1];
+  block_reduce<1>(acc, out);
+  if (threadIdx.x == 0) partial[blockIdx.x] = out[0];
+}
+void launch_norm2_64(const double2* x, long long n2, double2* partial, cudaStream_t st) {
+  norm2_64_kernel<<<blas_partials_blocks(), BT, 0, st>>>(x, n2, partial);
+}
+
+// x += sum_i y_i Z_i (Z FP32, x FP64): the sum is formed in FP32, added in FP64.
+__global__ void __launch_bounds__(BT) x_update_kernel(double2* x, const float4* Z, int nz, long long n4, const double2* y) {
+  __shared__ float2 ys[64];
+  if (threadIdx.x < nz) ys[threadIdx.x] = make_float2((float)y[threadIdx.x].x, (float)y[threadIdx.x].y);
+  __syncthreads();
+  for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n4; q += (long long)gridDim.x * BT) {
+    float4 a = make_float4(0, 0, 0, 0);
+    for (int i = 0; i < nz; ++i) {
+      float4 v = Z[(long long)i * n4 + q];
+      float2 c = ys[i];
+      a.x += c.x * v.x - c.y * v.y;
+      a.y += c.x * v.y + c.y * v.x;
+      a.z += c.x * v.z - c.y * v.w;
+      a.w += c.x * v.w + c.y * v.z;
+    }
+    double2 x0 = x[2 * q], x1 = x[2 * q + 1];
+    x[2 * q] = make_double2(x0.x + a.x, x0.y + a.y);
+    x[2 * q + 1] = make_double2(x1.x + a.z, x1.y + a.w);
+  }
+}
+void launch_x_update(double2* x, const float4* Z, int nz, long long n4, const double2* y, cudaStream_t st) {
+  x_update_kernel<<<blas_partials_blocks(), BT, 0, st>>>(x, Z, nz, n4, y);
+}
+
+// v = r / sqrt(nrm2) in FP32 (the FP64 and FP32 layouts hold the same complex numbers
+// in the same order: double2 unit 2q and 2q+1 <-> float4 unit q).
+__global__ void r64_to_v32_kernel(float4* v, const double2* r, long long n4, const double2* nrm2) {
+  double s = 1.0 / sqrt(nrm2->x);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+    double2 a = r[2 * q], b = r[2 * q + 1];
+    v[q] = make_float4((float)(a.x * s), (float)(a.y * s), (float)(b.x * s), (float)(b.y * s));
+  }
+}
+void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2* nrm2, cudaStream_t st) {
+  r64_to_v32_kernel<<<blas_partials_blocks(), BT, 0, st>>>(v, r, n4, nrm2);
+}
+
+// out_l = sum_i P[i + l ldp] V_i for l < nout (P complex FP64, column-major).
+template <int NO>
+__global__ void __launch_bounds__(BT) recombine_kernel(float4* out, const float4* V, int nv, int l0, int nout, long long n4,
+                                                       const double2* P, int ldp) {
+  __shared__ float2 ps[64][NO];
+  for (int t = threadIdx.x; t < nv * NO; t += BT) {
+    int i = t / NO, l = t % NO;
+    ps[i][l] = l0 + l < nout ? make_float2((float)P[i + (long long)(l0 + l) * ldp].x, (float)P[i + (long long)(l0 + l) * ldp].y)
+                             : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n4; q += (long long)gridDim.x * BT) {
+    float4 a[NO];
+#pragma unroll
+    for (int l = 0; l < NO; ++l) a[l] = make_float4(0, 0, 0, 0);
+    for (int i = 0; i < nv; ++i) {
+      float4 v = V[(long long)i * n4 + q];
+#pragma unroll
+      for (int l = 0; l < NO; ++l) {
+        float2 c = ps[i][l];
+        a[l].x += c.x * v.x - c.y * v.y;
+        a[l].y += c.x * v.y + c.y * v.x;
+        a[l].z += c.x * v.z - c.y * v.w;
+        a[l].w += c.x * v.w + c.y * v.z;
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < NO; ++l)
+      if (l0 + l < nout) out[(long long)(l0 + l) * n4 + q] = a[l];
+  }
+}
+int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n4, const double2* P, int ldp,
+                     cudaStream_t st) {
+  int n = 0;
+  for (int l0 = 0; l0 < nout; l0 += 8, ++n)
+    recombine_kernel<8><<<blas_partials_blocks(), BT, 0, st>>>(out, V, nv, l0, nout, n4, P, ldp);
+  return n;
+}
+
+__global__ void copy64_to32_kernel(float4* out, const double2* in, long long n4) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+    double2 a = in[2 * q], b = in[2 * q + 1];
+    out[q] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+  }
+}
+void launch_copy64_to32(float4* out, const double2* in, long long n4, cudaStream_t st) {
+  copy64_to32_kernel<<<blas_partials_blocks(), BT, 0, st>>>(out, in, n4);
+}
+
+__global__ void axpy_64_kernel(double2* x, const double2* y, double a, long long n2) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n2; q += (long long)gridDim.x * blockDim.x) {
+    double2 u = x[q], v = y[q];
+    x[q] = make_double2(u.x + a * v.x, u.y + a * v.y);
+  }
+}
+void launch_axpy_64(double2* x, const double2* y, double a, long long n2, cudaStream_t st) {
+  axpy_64_kernel<<<blas_partials_blocks(), BT, 0, st>>>(x, y, a, n2);
+}
+
+}  // namespace dd

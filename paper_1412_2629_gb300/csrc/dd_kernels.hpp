@@ -1,0 +1,84 @@
+// Host-callable launchers for every device kernel of the library.  All launches are
+// asynchronous on the given stream; none of them allocates memory.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dd_common.cuh"
+
+namespace dd {
+
+enum Prec { P64 = 0, P32 = 1, P16 = 2 };
+
+// Opaque views of one spinor field in the internal layout.
+struct FieldView {
+  void* data;     // double2[] | float4[] | uint4[]
+  float* norm;    // FP16 only: per-site scale
+  int prec;
+};
+
+// Gauge / clover storage in the internal layout for one precision.
+struct GaugeView { const void* links; int prec; };
+struct CloverView { const void* m; int prec; };
+
+// ---- layout (layout_clover.cu)
+void launch_pack_spinor(const Geom& g, const void* canon, int canon_prec, FieldView out, cudaStream_t st);
+void launch_unpack_spinor(const Geom& g, FieldView in, void* canon, int canon_prec, cudaStream_t st);
+void launch_pack_gauge(const Geom& g, const double* canon, int t_antiperiodic, double2* u64, float2* u32,
+                       uint32_t* u16, cudaStream_t st);
+// Builds clover (all sites, with the 1/(2 kappa) diagonal) in FP64/FP32/FP16 and the
+// Schwarz matrices (even sites: clover block; odd sites: its inverse) in FP32/FP16.
+// status[0] counts sites with a (near-)singular block.
+void launch_build_clover(const Geom& g, const double* canon, double kappa, double csw, double2* c64,
+                         float4* c32, uint4* c16, float4* s32, uint4* s16, int* status, cudaStream_t st);
+
+// ---- Wilson-clover operator (dslash.cu)
+// out = A in, or out = f - A in when f != nullptr.  FP64 and FP32 fields use the matching
+// gauge/clover precision; FP16 fields use FP16 gauge/clover and FP32 arithmetic.
+void launch_apply_A(const Geom& g, GaugeView U, CloverView C, FieldView in, FieldView out, const FieldView* f,
+                    cudaStream_t st);
+
+// ---- Schwarz sweep (sap.cu)
+struct SapState {
+  int mat_prec;        // P32 or P16: gauge and Schwarz matrices
+  int vec_prec;        // P32 or P16: stored residual and solution
+  const void* links;   // gauge in mat_prec
+  const void* smat;    // Schwarz matrices in mat_prec
+  void* r_store;       // even-site residual, Hd sites per domain, vec_prec
+  float* r_norm;
+  void* u_store;       // solution, Vd sites per domain, vec_prec
+  float* u_norm;
+  float4* faces;       // projected half-spinors on the 8 faces of every domain (FP32)
+  int* err;            // set to 1 when a bounded device wait runs out
+  bool mat_in_smem;    // stage links and Schwarz matrices in shared memory
+};
+// One half-sweep: all domains of `colour`.  first: the residual is the input v (both
+// parities) and u = 0; use_faces: subtract the couplings to the other colour from the
+// face buffers; last: write u (FP32) into z.
+int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int use_faces, int last,
+                   const float4* v, float4* z, int i_domain, cudaStream_t st);
+size_t sap_smem_bytes(const Geom& g, int mat_prec, bool mat_in_smem);
+bool sap_mat_fits_smem(const Geom& g, int mat_prec);
+int sap_max_domain_sites();
+
+// ---- BLAS on FP32 / FP64 internal vectors (blas.cu).  n4 = number of float4 (or
+// double2) units in one vector; vectors of a basis are contiguous, stride n4.
+int blas_partials_blocks();
+int launch_multi_dot(const float4* V, int nv, long long n4, const float4* w, double2* partial, cudaStream_t st);
+void launch_reduce_partials(const double2* partial, int nv, double2* out, int accumulate, cudaStream_t st);
+int launch_multi_axpy(float4* w, const float4* V, int nv, long long n4, const double2* h, double2* norm_partial,
+                       cudaStream_t st);
+void launch_scale_to(float4* v, const float4* w, long long n4, const double2* nrm2, cudaStream_t st);
+void launch_norm2_64(const double2* x, long long n2, double2* partial, cudaStream_t st);
+void launch_dot_64_32(const float4* V, int nv, long long n4, const double2* r, double2* partial, cudaStream_t st);
+void launch_x_update(double2* x, const float4* Z, int nz, long long n4, const double2* y, cudaStream_t st);
+void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2* nrm2, cudaStream_t st);
+int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n4, const double2* P, int ldp,
+                      cudaStream_t st);
+void launch_copy64_to32(float4* out, const double2* in, long long n4, cudaStream_t st);
+void launch_axpy_64(double2* x, const double2* y, double a, long long n2, cudaStream_t st);
+
+// ---- small dense FP64 algebra run on the device (solver.cu)
+}  // namespace dd

@@ -1,0 +1,96 @@
+// Full-lattice Wilson-clover operator A = 1/(2 kappa) - 1/2 D_w + D_cl (Eq. 1-3).
+//
+// One thread per site in the domain-major layout: consecutive threads are consecutive
+// sites of one parity of one domain, so the site's own spinor, links and clover are read
+// with fully coalesced 16-byte (8- or 4-byte for links) loads, and most neighbours are
+// adjacent sites of the other parity (read through L1/L2).  Hops that leave the domain
+// go to the neighbouring domain's block; the antiperiodic time boundary is already in
+// the links.  The diagonal 1/(2 kappa) is folded into the stored clover.
+// Bytes per site (algorithmic, each field read once): 4 links + clover + in + out =
+// 192 reals; FP32 768 B, FP64 1536 B, FP16 384 B + 8 B of spinor norms.
+#include "dd_kernels.hpp"
+
+namespace dd {
+
+template <int MU, typename T>
+__device__ inline void hop_pair(const Geom& g, const Site& st, long long s, const SpinorPtr<T>& in,
+                                const LinkPtr<T>& U, Spinor<typename Arith<T>::type>& acc) {
+  typedef typename Arith<T>::type R;
+  Spinor<R> psi;
+  Half<R> h, uh;
+  Link<R> L;
+  // forward: (1 - gamma_mu) U_mu(x) psi(x + mu)
+  long long sf = neighbour(g, st, MU, +1);
+  in.load(g, sf, psi);
+  project<MU, -1>(psi, h);
+  U.load(g, s, MU, L);
+  su3_mul(L, h, uh);
+  accum_recon<MU, -1>(acc, uh);
+  // backward: (1 + gamma_mu) U_mu(x - mu)^dag psi(x - mu)
+  long long sb = neighbour(g, st, MU, -1);
+  in.load(g, sb, psi);
+  project<MU, +1>(psi, h);
+  U.load(g, sb, MU, L);
+  su3_dag_mul(L, h, uh);
+  accum_recon<MU, +1>(acc, uh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) apply_A_kernel(Geom g, LinkPtr<T> U, CloverPtr<T> C, SpinorPtr<T> in,
+                                                       SpinorPtr<T> out, SpinorPtr<T> f, int residual) {
+  typedef typename Arith<T>::type R;
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  Site st = decode(g, s);
+  Spinor<R> hop;
+  zero(hop);
+  hop_pair<0, T>(g, st, s, in, U, hop);
+  hop_pair<1, T>(g, st, s, in, U, hop);
+  hop_pair<2, T>(g, st, s, in, U, hop);
+  hop_pair<3, T>(g, st, s, in, U, hop);
+  Spinor<R> x, y;
+  in.load(g, s, x);
+  R m[72];
+  C.load(g, s, m);
+  clover_mul(m, x, y);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) y.c[a][b] = y.c[a][b] - R(0.5) * hop.c[a][b];
+  if (residual) {
+    Spinor<R> fv;
+    f.load(g, s, fv);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) y.c[a][b] = fv.c[a][b] - y.c[a][b];
+  }
+  out.store(g, s, y);
+}
+
+void launch_apply_A(const Geom& g, GaugeView U, CloverView C, FieldView in, FieldView out, const FieldView* f,
+                    cudaStream_t st) {
+  unsigned nb = (unsigned)((g.V + 255) / 256);
+  int res = f != nullptr;
+  if (in.prec == P64) {
+    SpinorPtr<double> fi{res ? (double2*)f->data : nullptr};
+    apply_A_kernel<double><<<nb, 256, 0, st>>>(g, LinkPtr<double>{(const double2*)U.links},
+                                               CloverPtr<double>{(const double2*)C.m},
+                                               SpinorPtr<double>{(double2*)in.data},
+                                               SpinorPtr<double>{(double2*)out.data}, fi, res);
+  } else if (in.prec == P32) {
+    SpinorPtr<float> fi{res ? (float4*)f->data : nullptr};
+    apply_A_kernel<float><<<nb, 256, 0, st>>>(g, LinkPtr<float>{(const float2*)U.links},
+                                              CloverPtr<float>{(const float4*)C.m},
+                                              SpinorPtr<float>{(float4*)in.data}, SpinorPtr<float>{(float4*)out.data},
+                                              fi, res);
+  } else {
+    SpinorPtr<__half> fi{res ? (uint4*)f->data : nullptr, res ? f->norm : nullptr};
+    apply_A_kernel<__half><<<nb, 256, 0, st>>>(g, LinkPtr<__half>{(const uint32_t*)U.links},
+                                               CloverPtr<__half>{(const uint4*)C.m},
+                                               SpinorPtr<__half>{(uint4*)in.data, in.norm},
+                                               SpinorPtr<__half>{(uint4*)out.data, out.norm}, fi, res);
+  }
+}
+
+}  // namespace dd

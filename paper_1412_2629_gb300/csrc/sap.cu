@@ -1,0 +1,600 @@
+// Multiplicative Schwarz (SAP) half-sweep: every domain of one colour is solved
+// approximately in one launch, one CTA per domain (Sec. II-C, Table I).
+//
+// Formulation.  Per site the state is u (accumulated solution) and, on even sites only,
+// the residual r of the last solve of its domain (the odd residual after a solve is
+// exactly zero, Eq. 5).  Between two visits of a domain its neighbours (all of the other
+// colour) changed their solution by delta'; their face buffers hold the half-spinors of
+// delta' that enter the coupling R.  A visit does:
+//   1. r = stored r (or the input v on the first sweep); r -= R delta' from the faces.
+//   2. even-odd: t_o = A_oo^{-1} r_o;  f_e = r_e - D_eo t_o.
+//   3. MR on D~_ee = A_ee - D_eo A_oo^{-1} D_oe, I_domain steps from x = 0.
+//   4. delta_e = x, delta_o = A_oo^{-1} (r_o - D_oe x); u += delta; store r = MR residual.
+//   5. write the projected half-spinors of delta on the eight faces.
+// D_eo, D_oe are the hops inside the domain with factor -1/2; A_ee is the clover block
+// (diagonal 1/(2 kappa) included), A_oo^{-1} its per-site inverse.
+//
+// Data movement.  The domain's links and Schwarz matrices (clover on even sites,
+// inverse on odd sites) form contiguous blocks in HBM; when they fit, one thread
+// stages both into shared memory with bulk asynchronous copies (TMA engine,
+// completion on an mbarrier) while the others load the residual.  The even-site and
+// odd-site work vectors live in shared memory as FP32; the thread for local index i
+// owns even site i and odd site i and keeps x, rho and r_o in registers, so every MR
+// step runs on chip.  The MR inner products are reduced with warp shuffles and one
+// exchange through shared memory.
+#include <type_traits>
+
+#include "dd_kernels.hpp"
+
+namespace dd {
+
+// ------------------------------------------------------------------ matrix views
+template <typename MT> struct MatBlock;
+
+template <> struct MatBlock<__half> {
+  const uint32_t* lk;  // [mu][9][Vd] half2
+  const uint4* cm;     // [9][Vd]     8 halves
+  int Vd;
+  __device__ void link(int mu, int r, Link<float>& U) const {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) { float2 v = h2f(lk[(mu * 9 + j) * Vd + r]); U.e[j / 3][j % 3] = mk(v.x, v.y); }
+  }
+  __device__ void mat(int r, float m[72]) const {
+#pragma unroll
+    for (int u = 0; u < 9; ++u) {
+      uint4 v = cm[u * Vd + r];
+      uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { float2 f = h2f(w[e]); m[8 * u + 2 * e] = f.x; m[8 * u + 2 * e + 1] = f.y; }
+    }
+  }
+  static constexpr int link_bytes_per_site = 4 * 9 * 4;
+  static constexpr int mat_bytes_per_site = 9 * 16;
+};
+
+template <> struct MatBlock<float> {
+  const float2* lk;    // [mu][9][Vd]
+  const float4* cm;    // [18][Vd]
+  int Vd;
+  __device__ void link(int mu, int r, Link<float>& U) const {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) { float2 v = lk[(mu * 9 + j) * Vd + r]; U.e[j / 3][j % 3] = mk(v.x, v.y); }
+  }
+  __device__ void mat(int r, float m[72]) const {
+#pragma unroll
+    for (int u = 0; u < 18; ++u) {
+      float4 v = cm[u * Vd + r];
+      m[4 * u] = v.x; m[4 * u + 1] = v.y; m[4 * u + 2] = v.z; m[4 * u + 3] = v.w;
+    }
+  }
+  static constexpr int link_bytes_per_site = 4 * 9 * 8;
+  static constexpr int mat_bytes_per_site = 18 * 16;
+};
+
+// ------------------------------------------------------------------ work buffers
+__device__ inline void ld_buf(const float4* buf, int Hd, int i, Spinor<float>& v) {
+#pragma unroll
+  for (int u = 0; u < 6; ++u) {
+    float4 q = buf[u * Hd + i];
+    int k = 2 * u;
+    v.c[k / 3][k % 3] = mk(q.x, q.y);
+    v.c[(k + 1) / 3][(k + 1) % 3] = mk(q.z, q.w);
+  }
+}
+__device__ inline void st_buf(float4* buf, int Hd, int i, const Spinor<float>& v) {
+#pragma unroll
+  for (int u = 0; u < 6; ++u) {
+    int k = 2 * u;
+    buf[u * Hd + i] = make_float4(v.c[k / 3][k % 3].re, v.c[k / 3][k % 3].im, v.c[(k + 1) / 3][(k + 1) % 3].re,
+                                  v.c[(k + 1) / 3][(k + 1) % 3].im);
+  }
+}
+
+// Even-site residual store: per domain Hd sites.
+template <typename VT> struct EvenStore;
+template <> struct EvenStore<float> {
+  float4* p;
+  float* unused;
+  __device__ void load(long long d, int Hd, int i, Spinor<float>& v) const { ld_buf(p + d * 6 * Hd, Hd, i, v); }
+  __device__ void store(long long d, int Hd, int i, const Spinor<float>& v) const { st_buf(p + d * 6 * Hd, Hd, i, v); }
+};
+template <> struct EvenStore<__half> {
+  uint4* p;
+  float* norm;
+  __device__ void load(long long d, int Hd, int i, Spinor<float>& v) const {
+    float n = norm[d * Hd + i];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      uint4 q = p[(d * 3 + u) * Hd + i];
+      uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float2 f = h2f(w[e]);
+        int k = 4 * u + e;
+        v.c[k / 3][k % 3] = mk(f.x * n, f.y * n);
+      }
+    }
+  }
+  __device__ void store(long long d, int Hd, int i, const Spinor<float>& v) const {
+    float m = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) m = fmaxf(m, fmaxf(fabsf(v.c[a][b].re), fabsf(v.c[a][b].im)));
+    float inv = m > 0.f ? 1.f / m : 0.f;
+    norm[d * Hd + i] = m;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        int k = 4 * u + e;
+        w[e] = f2h(v.c[k / 3][k % 3].re * inv, v.c[k / 3][k % 3].im * inv);
+      }
+      p[(d * 3 + u) * Hd + i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+};
+
+template <typename VT> struct VecPtr;
+template <> struct VecPtr<float> {
+  typedef SpinorPtr<float> type;
+  __device__ static type make(void* p, float*) { return type{(float4*)p}; }
+};
+template <> struct VecPtr<__half> {
+  typedef SpinorPtr<__half> type;
+  __device__ static type make(void* p, float* n) { return type{(uint4*)p, n}; }
+};
+
+// ------------------------------------------------------------------ hop helpers
+// acc += sum of the hops of one site that stay inside its domain (no -1/2 factor).
+// src holds the other parity's vector; links come from the domain's block.
+template <int MU, typename MT>
+__device__ inline void inside_hop_mu(const Geom& g, const int l[4], int lex, int p, int r_self, const float4* src,
+                                     const MatBlock<MT>& M, Spinor<float>& acc) {
+  Spinor<float> psi;
+  Half<float> h, uh;
+  Link<float> L;
+  if (l[MU] + 1 < g.b[MU]) {
+    int j = (lex + g.bstride[MU]) >> 1;
+    ld_buf(src, g.Hd, j, psi);
+    project<MU, -1>(psi, h);
+    M.link(MU, r_self, L);
+    su3_mul(L, h, uh);
+    accum_recon<MU, -1>(acc, uh);
+  }
+  if (l[MU] > 0) {
+    int j = (lex - g.bstride[MU]) >> 1;
+    ld_buf(src, g.Hd, j, psi);
+    project<MU, +1>(psi, h);
+    M.link(MU, (1 - p) * g.Hd + j, L);
+    su3_dag_mul(L, h, uh);
+    accum_recon<MU, +1>(acc, uh);
+  }
+}
+
+template <typename MT>
+__device__ inline void inside_hops(const Geom& g, const int l[4], int lex, int p, int r_self, const float4* src,
+                                   const MatBlock<MT>& M, Spinor<float>& acc) {
+  inside_hop_mu<0>(g, l, lex, p, r_self, src, M, acc);
+  inside_hop_mu<1>(g, l, lex, p, r_self, src, M, acc);
+  inside_hop_mu<2>(g, l, lex, p, r_self, src, M, acc);
+  inside_hop_mu<3>(g, l, lex, p, r_self, src, M, acc);
+}
+
+__device__ inline void ld_half(const float4* q, Half<float>& h) {
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    float4 v = q[u];
+    int k = 2 * u;
+    h.c[k / 3][k % 3] = mk(v.x, v.y);
+    h.c[(k + 1) / 3][(k + 1) % 3] = mk(v.z, v.w);
+  }
+}
+__device__ inline void st_half(float4* q, const Half<float>& h) {
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    int k = 2 * u;
+    q[u] = make_float4(h.c[k / 3][k % 3].re, h.c[k / 3][k % 3].im, h.c[(k + 1) / 3][(k + 1) % 3].re,
+                       h.c[(k + 1) / 3][(k + 1) % 3].im);
+  }
+}
+
+// acc += hops from the neighbouring domains, read from their face buffers.
+//   +mu face of this domain: neighbour d+mu wrote P^-_mu delta on its -mu face;
+//     the hop is (1 - gamma_mu) U_mu(x) delta(x + mu).
+//   -mu face: neighbour d-mu wrote U_mu(y)^dag P^+_mu delta(y) on its +mu face.
+template <int MU, typename MT>
+__device__ inline void face_hop_mu(const Geom& g, int d, const int n[4], const int l[4], int r_self,
+                                   const float4* faces, const MatBlock<MT>& M, Spinor<float>& acc) {
+  Half<float> h, uh;
+  if (l[MU] == g.b[MU] - 1) {
+    long long dn = neighbour_domain(g, d, n, MU, +1);
+    const float4* q = faces + (dn * g.face_block + g.face_off[2 * MU] + face_index(g, l, MU)) * 3;
+    ld_half(q, h);
+    Link<float> L;
+    M.link(MU, r_self, L);
+    su3_mul(L, h, uh);
+    accum_recon<MU, -1>(acc, uh);
+  }
+  if (l[MU] == 0) {
+    long long dn = neighbour_domain(g, d, n, MU, -1);
+    const float4* q = faces + (dn * g.face_block + g.face_off[2 * MU + 1] + face_index(g, l, MU)) * 3;
+    ld_half(q, h);
+    accum_recon<MU, +1>(acc, h);
+  }
+}
+
+template <typename MT>
+__device__ inline void face_hops(const Geom& g, int d, const int n[4], const int l[4], int r_self,
+                                 const float4* faces, const MatBlock<MT>& M, Spinor<float>& acc) {
+  face_hop_mu<0>(g, d, n, l, r_self, faces, M, acc);
+  face_hop_mu<1>(g, d, n, l, r_self, faces, M, acc);
+  face_hop_mu<2>(g, d, n, l, r_self, faces, M, acc);
+  face_hop_mu<3>(g, d, n, l, r_self, faces, M, acc);
+}
+
+template <int MU, typename MT>
+__device__ inline void face_write_mu(const Geom& g, long long d, const int l[4], int r_self, float4* faces,
+                                     const MatBlock<MT>& M, const Spinor<float>& dl) {
+  Half<float> h, uh;
+  if (l[MU] == 0) {
+    project<MU, -1>(dl, h);
+    st_half(faces + (d * g.face_block + g.face_off[2 * MU] + face_index(g, l, MU)) * 3, h);
+  }
+  if (l[MU] == g.b[MU] - 1) {
+    project<MU, +1>(dl, h);
+    Link<float> L;
+    M.link(MU, r_self, L);
+    su3_dag_mul(L, h, uh);
+    st_half(faces + (d * g.face_block + g.face_off[2 * MU + 1] + face_index(g, l, MU)) * 3, uh);
+  }
+}
+
+template <typename MT>
+__device__ inline void face_write(const Geom& g, long long d, const int l[4], int r_self, float4* faces,
+                                  const MatBlock<MT>& M, const Spinor<float>& dl) {
+  face_write_mu<0>(g, d, l, r_self, faces, M, dl);
+  face_write_mu<1>(g, d, l, r_self, faces, M, dl);
+  face_write_mu<2>(g, d, l, r_self, faces, M, dl);
+  face_write_mu<3>(g, d, l, r_self, faces, M, dl);
+}
+
+// ------------------------------------------------------------------ TMA bulk copy + mbarrier
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ inline unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the given phase parity of the barrier, for at most limit_ns nanoseconds;
+// returns false if the limit ran out.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t phase, unsigned long long limit_ns) {
+  const unsigned long long t0 = globaltimer_ns();
+  while (true) {
+    uint32_t ok = 0;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    if (ok) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+struct SapArgs {
+  Geom g;
+  int colour, first, use_faces, last, i_domain;
+  const void* links;
+  const void* smat;
+  void* r_store;
+  float* r_norm;
+  void* u_store;
+  float* u_norm;
+  float4* faces;
+  const float4* v;
+  float4* z;
+  int* err;
+};
+
+constexpr int SAP_MAX_THREADS = 256;
+
+template <typename MT, typename VT, bool MSMEM>
+__global__ void __launch_bounds__(SAP_MAX_THREADS, 1) sap_kernel(SapArgs a) {
+  const Geom& g = a.g;
+  extern __shared__ float4 smem[];
+  __shared__ uint64_t mbar;
+  __shared__ float4 red[SAP_MAX_THREADS / 32];
+  const int tid = threadIdx.x;
+  const int Hd = g.Hd, Vd = g.Vd;
+
+  // domain of this CTA: the blockIdx.x-th domain of the given colour
+  int n[4];
+  {
+    int half = g.N[0] >> 1;
+    int j = blockIdx.x % half;
+    int row = blockIdx.x / half;
+    n[1] = row % g.N[1];
+    n[2] = (row / g.N[1]) % g.N[2];
+    n[3] = row / (g.N[1] * g.N[2]);
+    n[0] = 2 * j + ((a.colour + n[1] + n[2] + n[3]) & 1);
+  }
+  const long long d = n[0] + (long long)g.dstride[1] * n[1] + (long long)g.dstride[2] * n[2] +
+                      (long long)g.dstride[3] * n[3];
+
+  const size_t lk_elems = (size_t)4 * 9 * Vd;
+  const size_t lk_bytes = (size_t)MatBlock<MT>::link_bytes_per_site * Vd;
+  const size_t cm_bytes = (size_t)MatBlock<MT>::mat_bytes_per_site * Vd;
+  char* sbase = reinterpret_cast<char*>(smem);
+  MatBlock<MT> M;
+  M.Vd = Vd;
+  typedef typename std::remove_const<typename std::remove_pointer<decltype(M.lk)>::type>::type LkT;
+  typedef typename std::remove_const<typename std::remove_pointer<decltype(M.cm)>::type>::type CmT;
+  const LkT* glk = reinterpret_cast<const LkT*>(a.links) + d * lk_elems;
+  const CmT* gcm = reinterpret_cast<const CmT*>(a.smat) + d * (cm_bytes / sizeof(CmT));
+  float4* sE;
+  if (MSMEM) {
+    M.lk = reinterpret_cast<const LkT*>(sbase);
+    M.cm = reinterpret_cast<const CmT*>(sbase + lk_bytes);
+    sE = reinterpret_cast<float4*>(sbase + lk_bytes + cm_bytes);
+    if (tid == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes));
+      bulk_g2s(sbase, glk, (uint32_t)lk_bytes, &mbar);
+      bulk_g2s(sbase + lk_bytes, gcm, (uint32_t)cm_bytes, &mbar);
+    }
+  } else {
+    M.lk = glk;
+    M.cm = gcm;
+    sE = smem;
+  }
+  float4* sO = sE + 6 * Hd;
+
+  int le[4], lo[4];
+  local_coords(g, 0, tid, le);
+  local_coords(g, 1, tid, lo);
+  const int lex_e = le[0] + g.bstride[1] * le[1] + g.bstride[2] * le[2] + g.bstride[3] * le[3];
+  const int lex_o = lo[0] + g.bstride[1] * lo[1] + g.bstride[2] * lo[2] + g.bstride[3] * lo[3];
+  const long long s_e = (d << g.lgVd) + tid, s_o = s_e + Hd;
+  const int r_e = tid, r_o = Hd + tid;
+
+  // 1. residual
+  Spinor<float> re, ro;
+  const SpinorPtr<float> vin{const_cast<float4*>(a.v)};
+  EvenStore<VT> rst{reinterpret_cast<decltype(EvenStore<VT>::p)>(a.r_store), a.r_norm};
+  if (a.first) {
+    vin.load(g, s_e, re);
+    vin.load(g, s_o, ro);
+  } else {
+    rst.load(d, Hd, tid, re);
+    zero(ro);
+  }
+  if (MSMEM) {
+    bool ok = mbar_wait(&mbar, 0, 2000000000ull);
+    if (__syncthreads_or(!ok)) {
+      // the copy did not complete in time: flag it, give it one more bounded wait, leave
+      if (tid == 0) atomicExch(a.err, 1);
+      mbar_wait(&mbar, 0, 2000000000ull);
+      return;
+    }
+  }
+  if (a.use_faces) {
+    Spinor<float> ae, ao;
+    zero(ae);
+    zero(ao);
+    face_hops(g, (int)d, n, le, r_e, a.faces, M, ae);
+    face_hops(g, (int)d, n, lo, r_o, a.faces, M, ao);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        re.c[s][c] = re.c[s][c] + 0.5f * ae.c[s][c];
+        ro.c[s][c] = ro.c[s][c] + 0.5f * ao.c[s][c];
+      }
+  }
+
+  // 2. even-odd preparation
+  float m[72];
+  Spinor<float> t, acc, rho, x;
+  M.mat(r_o, m);
+  clover_mul(m, ro, t);
+  st_buf(sO, Hd, tid, t);
+  __syncthreads();
+  zero(acc);
+  inside_hops(g, le, lex_e, 0, r_e, sO, M, acc);
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      rho.c[s][c] = re.c[s][c] + 0.5f * acc.c[s][c];
+      x.c[s][c] = mk(0.f, 0.f);
+    }
+  st_buf(sE, Hd, tid, rho);
+  __syncthreads();
+
+  // 3. MR on the Schur complement
+  const int nwarp = (Hd + 31) >> 5;
+  for (int it = 0; it < a.i_domain; ++it) {
+    // odd sites: t = A_oo^{-1} H_oe rho
+    zero(acc);
+    inside_hops(g, lo, lex_o, 1, r_o, sE, M, acc);
+    M.mat(r_o, m);
+    clover_mul(m, acc, t);
+    st_buf(sO, Hd, tid, t);
+    __syncthreads();
+    // even sites: p = A_ee rho - 1/4 H_eo t
+    zero(acc);
+    inside_hops(g, le, lex_e, 0, r_e, sO, M, acc);
+    Spinor<float> pv;
+    M.mat(r_e, m);
+    clover_mul(m, rho, pv);
+    float pr_re = 0.f, pr_im = 0.f, pp = 0.f;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pv.c[s][c] = pv.c[s][c] - 0.25f * acc.c[s][c];
+        cx<float> q = cjmul(pv.c[s][c], rho.c[s][c]);
+        pr_re += q.re;
+        pr_im += q.im;
+        pp += pv.c[s][c].re * pv.c[s][c].re + pv.c[s][c].im * pv.c[s][c].im;
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      pr_re += __shfl_xor_sync(0xffffffffu, pr_re, o);
+      pr_im += __shfl_xor_sync(0xffffffffu, pr_im, o);
+      pp += __shfl_xor_sync(0xffffffffu, pp, o);
+    }
+    if ((tid & 31) == 0) red[tid >> 5] = make_float4(pr_re, pr_im, pp, 0.f);
+    __syncthreads();
+    float sr = 0.f, si = 0.f, sp = 0.f;
+    for (int w = 0; w < nwarp; ++w) {
+      float4 q = red[w];
+      sr += q.x;
+      si += q.y;
+      sp += q.z;
+    }
+    cx<float> alpha = sp > 0.f ? mk(sr / sp, si / sp) : mk(0.f, 0.f);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        x.c[s][c] = x.c[s][c] + cmul(alpha, rho.c[s][c]);
+        rho.c[s][c] = rho.c[s][c] - cmul(alpha, pv.c[s][c]);
+      }
+    st_buf(sE, Hd, tid, rho);
+    __syncthreads();
+  }
+
+  // 4. odd reconstruction: delta_o = A_oo^{-1} (r_o + 1/2 H_oe x)
+  st_buf(sE, Hd, tid, x);
+  __syncthreads();
+  zero(acc);
+  inside_hops(g, lo, lex_o, 1, r_o, sE, M, acc);
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc.c[s][c] = ro.c[s][c] + 0.5f * acc.c[s][c];
+  Spinor<float> dlo;
+  M.mat(r_o, m);
+  clover_mul(m, acc, dlo);
+
+  // solution and residual
+  typename VecPtr<VT>::type ust = VecPtr<VT>::make(a.u_store, a.u_norm);
+  Spinor<float> ue, uo;
+  if (a.first) {
+    ue = x;
+    uo = dlo;
+  } else {
+    ust.load(g, s_e, ue);
+    ust.load(g, s_o, uo);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        ue.c[s][c] = ue.c[s][c] + x.c[s][c];
+        uo.c[s][c] = uo.c[s][c] + dlo.c[s][c];
+      }
+  }
+  if (a.last) {
+    SpinorPtr<float> zo{a.z};
+    zo.store(g, s_e, ue);
+    zo.store(g, s_o, uo);
+  } else {
+    ust.store(g, s_e, ue);
+    ust.store(g, s_o, uo);
+    rst.store(d, Hd, tid, rho);
+  }
+  // 5. faces for the other colour (not needed after the very last half-sweep)
+  if (!(a.last && a.colour == 1)) {
+    face_write(g, d, le, r_e, a.faces, M, x);
+    face_write(g, d, lo, r_o, a.faces, M, dlo);
+  }
+}
+
+size_t sap_smem_bytes(const Geom& g, int mat_prec, bool mat_in_smem) {
+  size_t vec = (size_t)2 * 6 * g.Hd * 16;
+  if (!mat_in_smem) return vec;
+  size_t per = mat_prec == P16 ? (MatBlock<__half>::link_bytes_per_site + MatBlock<__half>::mat_bytes_per_site)
+                               : (MatBlock<float>::link_bytes_per_site + MatBlock<float>::mat_bytes_per_site);
+  return vec + per * g.Vd;
+}
+
+static int smem_optin();
+bool sap_mat_fits_smem(const Geom& g, int mat_prec) {
+  return sap_smem_bytes(g, mat_prec, true) + 1024 <= (size_t)smem_optin();
+}
+
+static int smem_optin() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  return v;
+}
+
+int sap_max_domain_sites() { return 2 * SAP_MAX_THREADS; }
+
+template <typename MT, typename VT, bool MSMEM>
+static int launch_one(const SapArgs& a, int grid, cudaStream_t st) {
+  size_t smem = sap_smem_bytes(a.g, std::is_same<MT, __half>::value ? P16 : P32, MSMEM);
+  static int configured = 0;
+  if (!configured) {
+    // static shared memory (barrier, reduction slots) is small; the rest may be dynamic
+    cudaFuncSetAttribute(sap_kernel<MT, VT, MSMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin() - 1024);
+    configured = 1;
+  }
+  sap_kernel<MT, VT, MSMEM><<<grid, a.g.Hd, smem, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int use_faces, int last,
+                   const float4* v, float4* z, int i_domain, cudaStream_t st) {
+  if (g.Hd > SAP_MAX_THREADS || (g.Hd & 31)) return -1;
+  SapArgs a;
+  a.g = g;
+  a.colour = colour;
+  a.first = first;
+  a.use_faces = use_faces;
+  a.last = last;
+  a.i_domain = i_domain;
+  a.links = S.links;
+  a.smat = S.smat;
+  a.r_store = S.r_store;
+  a.r_norm = S.r_norm;
+  a.u_store = S.u_store;
+  a.u_norm = S.u_norm;
+  a.faces = S.faces;
+  a.v = v;
+  a.z = z;
+  a.err = S.err;
+  int grid = g.ND / 2;
+  bool ms = S.mat_in_smem;
+  if (S.mat_prec == P16) {
+    if (S.vec_prec == P16) return ms ? launch_one<__half, __half, true>(a, grid, st) : launch_one<__half, __half, false>(a, grid, st);
+    return ms ? launch_one<__half, float, true>(a, grid, st) : launch_one<__half, float, false>(a, grid, st);
+  }
+  if (S.vec_prec == P16) return ms ? launch_one<float, __half, true>(a, grid, st) : launch_one<float, __half, false>(a, grid, st);
+  return ms ? launch_one<float, float, true>(a, grid, st) : launch_one<float, float, false>(a, grid, st);
+}
+
+}  // namespace dd

@@ -1,0 +1,186 @@
+"""ctypes binding of include/dd.h: argument marshalling only.
+
+Every numerical step runs in libdd.so.  Loading fails loudly if the library has not
+been built (python -m paper_1412_2629_gb300.build); there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdd.so")
+
+DD_OK = 0
+DD_ERR_INVALID, DD_ERR_DIMS, DD_ERR_NO_GAUGE, DD_ERR_NO_CLOVER = 1, 2, 3, 4
+DD_ERR_SINGULAR_CLOVER, DD_ERR_NOT_CONVERGED, DD_ERR_NONFINITE = 5, 6, 7
+DD_ERR_TIMEOUT, DD_ERR_OOM, DD_ERR_CUDA = 8, 9, 10
+DD_PREC_FP64, DD_PREC_FP32, DD_PREC_FP16 = 0, 1, 2
+DD_HOST, DD_DEVICE = 0, 1
+DD_LAYOUT_CANONICAL, DD_LAYOUT_INTERNAL = 0, 1
+
+
+class dd_sap_params(C.Structure):
+    _fields_ = [("i_schwarz", C.c_int), ("i_domain", C.c_int), ("storage_prec", C.c_int)]
+
+
+class dd_solve_params(C.Structure):
+    _fields_ = [("tol", C.c_double), ("m", C.c_int), ("k", C.c_int), ("max_iter", C.c_int),
+                ("sap", dd_sap_params)]
+
+
+class dd_solve_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("restarts", C.c_int),
+                ("reliable_updates", C.c_int), ("deflated_restarts", C.c_int),
+                ("true_rel_residual", C.c_double), ("t_total", C.c_double), ("t_A", C.c_double),
+                ("t_M", C.c_double), ("t_GS", C.c_double), ("t_other", C.c_double),
+                ("flops_nominal", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class DDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"dd status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1412_2629_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        P, I, D = C.c_void_p, C.c_int, C.c_double
+        sig = {
+            "dd_create": (I, [C.POINTER(P), C.POINTER(I), C.POINTER(I), I, P]),
+            "dd_destroy": (I, [P]),
+            "dd_last_error": (C.c_char_p, [P]),
+            "dd_load_gauge": (I, [P, P, I]),
+            "dd_build_clover": (I, [P, D, D]),
+            "dd_apply_D": (I, [P, P, P, I, I]),
+            "dd_sap_precondition": (I, [P, P, P, C.POINTER(dd_sap_params), I]),
+            "dd_solve": (I, [P, P, P, I, I, C.POINTER(dd_solve_params), C.POINTER(dd_solve_info)]),
+            "dd_spinor_bytes": (C.c_size_t, [P, I, I]),
+            "dd_pack_spinor": (I, [P, P, I, P, I]),
+            "dd_unpack_spinor": (I, [P, P, I, P, I]),
+            "dd_launch_count": (C.c_longlong, [P]),
+            "dd_load_model": (D, [C.c_longlong, I]),
+            "dd_autotune": (I, [P, I, C.POINTER(I), C.POINTER(dd_sap_params)]),
+            "dd_deflate_host": (I, [I, I, P, P, P, P, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype, f.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor (host or device)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x)
+
+
+def _ints(v):
+    return (C.c_int * 4)(*[int(a) for a in v])
+
+
+class Context:
+    """Owner of one dd_ctx.  All calls map one to one onto the C ABI."""
+
+    def __init__(self, dims, domain, t_antiperiodic=True, stream=None):
+        self._h = C.c_void_p()
+        s = lib().dd_create(C.byref(self._h), _ints(dims), _ints(domain), int(bool(t_antiperiodic)),
+                            C.c_void_p(stream) if stream else None)
+        if s != DD_OK:
+            raise DDError(s, "dd_create rejected the lattice / domain shape")
+        self.dims, self.domain = tuple(dims), tuple(domain)
+
+    def close(self):
+        if self._h:
+            lib().dd_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, s):
+        if s != DD_OK:
+            raise DDError(s, lib().dd_last_error(self._h).decode())
+        return s
+
+    def dd_load_gauge(self, U, where=DD_HOST):
+        return self._check(lib().dd_load_gauge(self._h, _ptr(U), where))
+
+    def dd_build_clover(self, kappa, csw):
+        return self._check(lib().dd_build_clover(self._h, float(kappa), float(csw)))
+
+    def dd_apply_D(self, inp, out, prec, layout=DD_LAYOUT_CANONICAL):
+        return self._check(lib().dd_apply_D(self._h, _ptr(inp), _ptr(out), prec, layout))
+
+    def dd_sap_precondition(self, inp, out, i_schwarz, i_domain, storage_prec, layout=DD_LAYOUT_CANONICAL):
+        p = dd_sap_params(i_schwarz, i_domain, storage_prec)
+        return self._check(lib().dd_sap_precondition(self._h, _ptr(inp), _ptr(out), C.byref(p), layout))
+
+    def dd_solve(self, f, x, nrhs=1, where=DD_HOST, tol=1e-10, m=16, k=0, max_iter=1000, i_schwarz=16,
+                 i_domain=4, storage_prec=DD_PREC_FP16, check=True):
+        p = dd_solve_params(tol, m, k, max_iter, dd_sap_params(i_schwarz, i_domain, storage_prec))
+        info = dd_solve_info()
+        s = lib().dd_solve(self._h, _ptr(f), _ptr(x), nrhs, where, C.byref(p), C.byref(info))
+        if check:
+            self._check(s)
+        return info
+
+    def dd_spinor_bytes(self, prec, layout):
+        return lib().dd_spinor_bytes(self._h, prec, layout)
+
+    def dd_pack_spinor(self, canon, canon_prec, internal, internal_prec):
+        return self._check(lib().dd_pack_spinor(self._h, _ptr(canon), canon_prec, _ptr(internal), internal_prec))
+
+    def dd_unpack_spinor(self, internal, internal_prec, canon, canon_prec):
+        return self._check(lib().dd_unpack_spinor(self._h, _ptr(internal), internal_prec, _ptr(canon), canon_prec))
+
+    def dd_launch_count(self):
+        return lib().dd_launch_count(self._h)
+
+    def dd_autotune(self, storage_prec=DD_PREC_FP16, i_schwarz=16):
+        dom = (C.c_int * 4)()
+        p = dd_sap_params(i_schwarz, 0, storage_prec)
+        self._check(lib().dd_autotune(self._h, storage_prec, dom, C.byref(p)))
+        return tuple(dom), (p.i_schwarz, p.i_domain, p.storage_prec)
+
+
+def dd_load_model(n_domains_per_colour, slots):
+    return lib().dd_load_model(int(n_domains_per_colour), int(slots))
+
+
+def dd_deflate_host(Hbar, c, y, k):
+    """Host build of the deflated-restart algebra (for checks without a GPU)."""
+    m = Hbar.shape[1]
+    H = np.asfortranarray(Hbar.astype(np.complex128))
+    P = np.zeros((m + 1, k + 1), dtype=np.complex128, order="F")
+    Hn = np.zeros((m + 1, k), dtype=np.complex128, order="F")
+    cn = np.zeros(k + 1, dtype=np.complex128)
+    th = np.zeros(m, dtype=np.complex128)
+    cc = np.ascontiguousarray(c, dtype=np.complex128)
+    yy = np.ascontiguousarray(y, dtype=np.complex128)
+    s = lib().dd_deflate_host(m, k, H.ctypes.data, cc.ctypes.data, yy.ctypes.data, P.ctypes.data,
+                              Hn.ctypes.data, cn.ctypes.data, th.ctypes.data)
+    if s != DD_OK:
+        raise DDError(s, "dd_deflate_host failed")
+    return P, Hn[:k + 1], cn, th

@@ -1,0 +1,60 @@
+"""End-to-end: dd_solve's solution, checked by the oracle in FP64 (true residual) and
+against the oracle's own SAP-FGMRES-DR solution and a sparse direct solve."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spl
+
+import synth
+from oracle import dense as DN
+from oracle import solve as S
+from paper_1412_2629_gb300 import dd
+
+from gpu_helpers import ctx_for, gauge, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", [dd.DD_PREC_FP16, dd.DD_PREC_FP32], ids=["mixed", "fp32"])
+def test_solve_8x4_workload(prec):
+    w = synth.WORKLOADS["8^4"]
+    U = synth.make_gauge(w).numpy()
+    f = synth.make_sources(w)[0]
+    c = ctx_for(w.dims, w.domain, U, w.kappa, w.csw)
+    x = np.zeros_like(f)
+    info = c.dd_solve(f, x, tol=w.tol, m=w.m, k=w.k, i_schwarz=w.i_schwarz, i_domain=w.i_domain, storage_prec=prec)
+    assert S.true_residual(U, x, f, w.kappa, w.csw) <= 1e-10
+    assert info.true_rel_residual <= 1e-10
+    xo, _ = S.solve(U, f, w.kappa, w.csw, w.domain, w.i_schwarz, w.i_domain, w.m, w.k, tol=1e-12)
+    assert rel(x, xo) <= 1e-8
+
+
+def test_solve_matches_sparse_direct_with_deflation():
+    dims, dom = (8, 8, 4, 4), (4, 4, 2, 2)
+    U = gauge(dims, 0.5, 21, ape=2)
+    f = synth.gaussian_source(dims, 22)
+    kappa, csw = 0.1390, 1.5
+    c = ctx_for(dims, dom, U, kappa, csw)
+    x = np.zeros_like(f)
+    info = c.dd_solve(f, x, tol=1e-10, m=6, k=3, i_schwarz=2, i_domain=2, storage_prec=dd.DD_PREC_FP16)
+    A = DN.assemble_A(U, kappa, csw).tocsc()
+    xl = spl.spsolve(A, f.ravel()).reshape(f.shape)
+    assert S.true_residual(U, x, f, kappa, csw) <= 1e-10
+    cond_bound = 1e-10 * 1e3
+    assert rel(x, xl) <= cond_bound
+    assert info.restarts >= 1
+
+
+def test_initial_guess_and_zero_source():
+    w = synth.WORKLOADS["8^4"]
+    U = synth.make_gauge(w).numpy()
+    f = synth.make_sources(w)[0]
+    c = ctx_for(w.dims, w.domain, U, w.kappa, w.csw)
+    x = np.zeros_like(f)
+    c.dd_solve(f, x, tol=1e-10, m=16, k=0, i_schwarz=16, i_domain=4)
+    x2 = x.copy()
+    info = c.dd_solve(f, x2, tol=1e-10, m=16, k=0, i_schwarz=16, i_domain=4)
+    assert info.iterations == 0 and np.array_equal(x2, x)
+    z = np.zeros_like(f)
+    xz = np.ones_like(f)
+    c.dd_solve(z, xz, tol=1e-10, m=16, k=0, i_schwarz=16, i_domain=4)
+    assert np.abs(xz).max() == 0
