@@ -1,0 +1,359 @@
+"""Benchmark: time-to-solution of the mixed-precision SAP-FGMRES-DR solver on the
+32^3x64 Wilson-clover workload (one GB300), with the plain-FP32 form, the full
+Wilson-clover operator's bandwidth and the Schwarz kernel's FP32 rate beside it.
+
+A step is one full solve A x = f to |f - A x| / |f| <= 1e-10 (FP64-recomputed), from
+x = 0, with the gauge field, clover and source already resident in HBM.  Set-up
+(gauge load, clover build) is timed separately.  Every field of this workload
+(0.2-1.2 GB) is larger than the 129 MB L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "32^3x64"
+METRIC = "time-to-solution to 1e-10 true residual, mixed FP16/FP32/FP64 SAP-FGMRES-DR"
+FLOP_HOP, FLOP_CLOVER, FLOP_A = 168, 504, 1848      # Sec. II-B: 1344 = 8 x 168, 504, 1848
+# Outer iterations the 32^3x64 solve takes (measured on the GPU, mixed and FP32 alike);
+# only used to scale the oracle's sampled cost to a whole solve.
+ORACLE_ITERS_32x64 = 12
+
+
+# ------------------------------------------------------------------ flop / byte model
+def sap_visit_flops(b, i_domain):
+    """Useful FP32 flops per site for one domain visit of the Schwarz kernel.
+
+    Hops that cross the domain face do not exist in the domain operator, so per
+    direction only the fraction (b_mu - 1)/b_mu of the 2 hops per site is counted.
+    Per MR step: the hops of D_oe and D_eo (168 each), the clover block on even sites
+    and its inverse on odd sites (504 per site), and 384 flops of inner products and
+    updates per even site.  Preparation and odd reconstruction each cost half the
+    domain's hops plus half the clover; the face coupling, face output and the
+    solution update add ~ 300 flops per site on average.
+    """
+    inside = sum(2.0 * (bb - 1) / bb for bb in b)           # inside hops per site
+    face = sum(2.0 / bb for bb in b)                           # crossing hops per site
+    mr = FLOP_HOP * inside + FLOP_CLOVER + 192.0
+    prep = 0.5 * FLOP_HOP * inside + 0.5 * FLOP_CLOVER + 24.0
+    recon = 0.5 * FLOP_HOP * inside + 0.5 * FLOP_CLOVER + 24.0
+    faces = face * (0.5 * 156 + 0.5 * 24) + face * (12 + 0.5 * 132) + 24.0 + 48.0
+    useful = i_domain * mr + prep + recon + faces
+    nominal = i_domain * (FLOP_A + 192.0) + FLOP_A
+    return useful, nominal
+
+
+def dslash_bytes_per_site(prec):
+    """Algorithmic bytes of one full operator application per site: 4 links (18 reals),
+    clover (72 reals), input and output spinors (24 reals each) = 192 reals; FP16
+    storage adds the two 4-byte spinor norms."""
+    return {"fp64": 192 * 8, "fp32": 192 * 4, "fp16": 192 * 2 + 8}[prec]
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def src_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_profile(name, sha):
+    """Per-launch DRAM traffic from a committed ncu summary, if it was taken on the
+    current kernel source (its `source_sha` line matches)."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ oracle arm
+def oracle_sample(w, U_host, f):
+    """Time one FP64 oracle application of A on the full lattice (field strength
+    precomputed, not timed).  Returns seconds."""
+    from oracle import wilson as W
+    F = W.field_strength(U_host)
+    t0 = time.perf_counter()
+    W.apply_A(U_host, f, w.kappa, w.csw, F)
+    return time.perf_counter() - t0
+
+
+def a_equivalents(w, iters, reliable):
+    """Operator-application equivalents of one solve: per outer iteration one A and one
+    Schwarz application (I_Schwarz x 2 half-sweeps, each ~ (I_domain + 1) D
+    applications on half the lattice, i.e. (I_domain + 1) / 2 A-equivalents), plus the
+    FP64 residuals."""
+    sap = w.i_schwarz * 2 * (w.i_domain + 1) / 2.0
+    return iters * (1 + sap) + reliable
+
+
+def make_inputs(w, device):
+    import synth
+    U = synth.make_gauge(w, device=device)
+    f = synth.make_sources(w)[0]
+    return U, f
+
+
+def reference_arm(args):
+    import torch
+    w = __import__("synth").WORKLOADS[WORKLOAD]
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    U, f = make_inputs(w, dev)
+    U = U.cpu().numpy()
+    del_t = []
+    from oracle import wilson as W
+    F = W.field_strength(U)
+    n = a_equivalents(w, ORACLE_ITERS_32x64, 3)
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        W.apply_A(U, f, w.kappa, w.csw, F)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            del_t.append(dt)
+    t = statistics.median(del_t)
+    val = t * n
+    sample = (f"one FP64 oracle application of A on the full {WORKLOAD} lattice (numpy, field strength "
+              f"precomputed), median of {args.steps}, scaled by {n:.0f} A-equivalents of a {ORACLE_ITERS_32x64}-"
+              f"iteration solve")
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_dict(w),
+           "cpu_baseline": {"value": val, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def config_dict(w):
+    return {"workload": f"{WORKLOAD} Wilson-clover, random SU(3) width {w.width} + {w.ape_steps} APE, "
+                        f"kappa {w.kappa}, c_sw {w.csw}, 1 Gaussian source",
+            "lattice": list(w.dims), "domain": list(w.domain), "i_schwarz": w.i_schwarz, "i_domain": w.i_domain,
+            "fgmres_m": w.m, "fgmres_k": w.k, "tol": w.tol, "l2": "inputs larger than L2 (no flush)"}
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if args.impl == "reference":
+        if rank == 0:
+            reference_arm(args)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    import synth
+    from paper_1412_2629_gb300 import build as B
+    B.build()
+    from paper_1412_2629_gb300 import dd
+
+    torch.cuda.set_device(local)
+    w = synth.WORKLOADS[WORKLOAD]
+    st = torch.cuda.current_stream()
+    U, f = make_inputs(w, "cuda")
+    ctx = dd.Context(w.dims, w.domain, True, st.cuda_stream)
+    t0 = time.perf_counter()
+    ctx.dd_load_gauge(torch.view_as_real(U).contiguous(), dd.DD_DEVICE)
+    ctx.dd_build_clover(w.kappa, w.csw)
+    setup_s = time.perf_counter() - t0
+    U_host = U.cpu().numpy() if (rank == 0 and not args.no_cpu_baseline) else None
+    del U
+    ft = torch.view_as_real(torch.from_numpy(f)).contiguous()
+    f_dev = ft.to("cuda")
+    x_dev = torch.zeros_like(f_dev)
+    f_pin = ft.pin_memory()
+    x_pin = torch.zeros_like(ft).pin_memory()
+    kw = dict(tol=w.tol, m=w.m, k=w.k, i_schwarz=w.i_schwarz, i_domain=w.i_domain, max_iter=2000)
+
+    def solve(prec, where=dd.DD_DEVICE):
+        if where == dd.DD_DEVICE:
+            x_dev.zero_()
+            return ctx.dd_solve(f_dev, x_dev, where=dd.DD_DEVICE, storage_prec=prec, **kw)
+        x_pin.zero_()
+        return ctx.dd_solve(f_pin, x_pin, where=dd.DD_HOST, storage_prec=prec, **kw)
+
+    def timed(prec, where, steps, warmup):
+        for _ in range(warmup):
+            solve(prec, where)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = ctx.dd_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        e0.record(st)
+        for _ in range(steps):
+            infos.append(solve(prec, where).as_dict())
+        e1.record(st)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = e0.elapsed_time(e1) / steps
+        return ms, infos, ctx.dd_launch_count() - l0
+
+    clk = ClockSampler(local)
+    clk.start()
+    ms_mixed, infos, launches = timed(dd.DD_PREC_FP16, dd.DD_DEVICE, args.steps, args.warmup)
+    clocks = clk.stop()
+    ms_e2e, infos_e2e, _ = timed(dd.DD_PREC_FP16, dd.DD_HOST, args.steps, 1)
+    ms_fp32, infos32, _ = timed(dd.DD_PREC_FP32, dd.DD_DEVICE, max(2, args.steps // 2), 1)
+
+    if world > 1:
+        t = torch.tensor([ms_mixed, ms_e2e, ms_fp32], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_mixed, ms_e2e, ms_fp32 = [float(v) for v in t]
+
+    V = int(np.prod(w.dims))
+    mean = lambda key, L: statistics.mean(i[key] for i in L)
+    iters = mean("iterations", infos)
+    t_M, t_A, t_GS, t_other = (mean(k, infos) for k in ("t_M", "t_A", "t_GS", "t_other"))
+    # Schwarz kernel: every launch is one half-sweep over the V/2 sites of one colour
+    n_sap = iters * 2 * w.i_schwarz
+    sap_launch_s = t_M / n_sap
+    useful, nominal = sap_visit_flops(w.domain, w.i_domain)
+    sap_flops_launch = useful * V / 2
+    sap_tflops = sap_flops_launch / sap_launch_s / 1e12
+    props = torch.cuda.get_device_properties(local)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    sap_sha = src_sha(["paper_1412_2629_gb300/csrc/sap.cu", "paper_1412_2629_gb300/csrc/dd_common.cuh"])
+    dsl_sha = src_sha(["paper_1412_2629_gb300/csrc/dslash.cu", "paper_1412_2629_gb300/csrc/dd_common.cuh"])
+    sap_traffic = read_profile("sap_kernel_32x64.txt", sap_sha)
+    # full operator inside the solve: one FP32 application per outer iteration
+    a_launch_s = t_A / iters
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    dsl_gbs = dslash_bytes_per_site("fp32") * V / a_launch_s / 1e9
+    dsl_traffic = read_profile("dslash_fp32_32x64.txt", dsl_sha)
+
+    cpu = None
+    if rank == 0 and U_host is not None:
+        t_or = oracle_sample(w, U_host, f)
+        n_eq = a_equivalents(w, iters, mean("reliable_updates", infos))
+        cpu = {"value": t_or * n_eq, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"one FP64 oracle application of A on the full {WORKLOAD} lattice ({t_or:.2f} s, numpy, "
+                         f"one thread), scaled by the {n_eq:.0f} A-equivalents of this solve"}
+
+    value = ms_mixed / 1e3
+    out = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16-storage/f32-arith/f64-residual", "data": "synthetic",
+        "config": config_dict(w),
+        "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": 2 * V * 24 * 8,
+                "d2h_bytes_per_step": V * 24 * 8},
+        "roofline": {"kernel": "sap_kernel (Schwarz half-sweep, FP16 storage)", "bound": "alu",
+                     "achieved": sap_tflops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": sap_tflops / fp32_peak,
+                     "traffic": sap_traffic,
+                     "peak_note": f"FP32 CUDA cores: {props.multi_processor_count} SMs x 128 lanes x 2 flop x "
+                                  f"{sm_max:.0f} MHz (max SM clock)",
+                     "flops_per_launch": sap_flops_launch, "launch_ms": 1e3 * sap_launch_s},
+        "dslash": {"kernel": "apply_A_kernel<float>", "bound": "hbm", "achieved": dsl_gbs, "peak": hbm,
+                   "unit": "GB/s", "frac": dsl_gbs / hbm, "traffic": dsl_traffic, "launch_ms": 1e3 * a_launch_s,
+                   "bytes_per_launch": dslash_bytes_per_site("fp32") * V, "peak_note": "of measured (MEASURED_PEAKS hbm_gbs)"},
+        "fp32_form": {"value": ms_fp32 / 1e3, "unit": "s", "iterations": mean("iterations", infos32),
+                      "true_rel_residual": max(i["true_rel_residual"] for i in infos32),
+                      "speedup_mixed_over_fp32": ms_fp32 / ms_mixed},
+        "solve": {"iterations": iters, "restarts": mean("restarts", infos),
+                  "deflated_restarts": mean("deflated_restarts", infos),
+                  "reliable_updates": mean("reliable_updates", infos),
+                  "true_rel_residual": max(i["true_rel_residual"] for i in infos),
+                  "split_s": {"A": t_A, "M": t_M, "GS": t_GS, "other": t_other},
+                  "sap_gflops_nominal": nominal * V / 2 / sap_launch_s / 1e9,
+                  "setup_s": setup_s},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

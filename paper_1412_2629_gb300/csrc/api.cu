@@ -3,7 +3,8 @@
 //
 // Outer solver (Table I): flexible GMRES with deflated restarts.  Krylov vectors V, Z are
 // FP32 fields; Gram-Schmidt coefficients, the Hessenberg matrix, its least-squares
-// problem and the deflation algebra are FP64 on the device; the solution is accumulated
+// problem are FP64 on the device (the m x m harmonic-Ritz eigenproblem of a deflated
+// restart runs on the host, the basis recombination on the device); the solution is accumulated
 // in FP64 and at every restart the residual is recomputed with the FP64 operator
 // (reliable update), which is what makes the 1e-10 target reachable with FP32 Krylov
 // vectors.  A deflated restart keeps the k harmonic Ritz vectors of smallest modulus;
@@ -46,7 +47,12 @@ struct SolverBuffers {
   double* status = nullptr;            // [0] residual estimate, [1] deflate status
   double* h_status = nullptr;          // pinned host mirror
   LsqState* lsq = nullptr;
-  DeflateWork* dw = nullptr;
+  int* flag = nullptr;                 // Gram-Schmidt: 1 when a second projection is needed
+  double* nu2 = nullptr;               // squared norm of the projected vector
+  // host side of the deflated restart (pinned)
+  zd *h_H = nullptr, *h_c0 = nullptr, *h_y = nullptr, *h_P = nullptr, *h_Hn = nullptr, *h_cn = nullptr;
+  zd* h_theta = nullptr;
+  DeflateWork* h_dw = nullptr;
 };
 
 struct dd_ctx {
@@ -191,11 +197,13 @@ extern "C" dd_status dd_create(dd_ctx** out, const int dims[4], const int domain
   return DD_OK;
 }
 
+static void release_solver(dd_ctx* c);
+
 extern "C" dd_status dd_destroy(dd_ctx* c) {
   if (!c) return DD_ERR_INVALID;
   cudaStreamSynchronize(c->st);
+  release_solver(c);
   for (void* p : c->allocs) cudaFree(p);
-  if (c->sv.h_status) cudaFreeHost(c->sv.h_status);
   delete c;
   return DD_OK;
 }
@@ -396,11 +404,28 @@ extern "C" dd_status dd_sap_precondition(dd_ctx* c, const float* in, float* out,
 }
 
 // ------------------------------------------------------------------ small dense kernels
-__global__ void arnoldi_finish_kernel(zd* H, zd* R, int ldh, int j, const zd* hA, const zd* hB, const double2* nrm2,
+__global__ void gs_decide_kernel(const zd* hA, int nv, zd* hB, int* flag, double* nu2) {
+  double ww = hA[nv].re, hh = 0;
+  for (int i = 0; i < nv; ++i) hh += abs2(hA[i]);
+  double v = ww - hh;
+  for (int i = 0; i <= nv; ++i) hB[i] = Z(0.0);
+  if (v >= 0.5 * ww && v > 0) { *flag = 0; *nu2 = v; }
+  else *flag = 1;
+}
+
+__global__ void gs_decide2_kernel(const zd* hB, int nv, const int* flag, double* nu2) {
+  if (!*flag) return;
+  double ww = hB[nv].re, hh = 0;
+  for (int i = 0; i < nv; ++i) hh += abs2(hB[i]);
+  double v = ww - hh;
+  *nu2 = v > 0 ? v : (ww > 0 ? ww : 1e-300);
+}
+
+__global__ void arnoldi_finish_kernel(zd* H, zd* R, int ldh, int j, const zd* hA, const zd* hB, const double* nu2,
                                       LsqState* lsq, zd* g, double* status) {
   zd* col = H + (long)j * ldh;
   for (int i = 0; i <= j; ++i) col[i] = hA[i] + hB[i];
-  double h = sqrt(nrm2->x);
+  double h = sqrt(*nu2);
   col[j + 1] = Z(h);
   zd* rc = R + (long)j * ldh;
   for (int i = 0; i <= j + 1; ++i) rc[i] = col[i];
@@ -409,11 +434,6 @@ __global__ void arnoldi_finish_kernel(zd* H, zd* R, int ldh, int j, const zd* hA
 }
 
 __global__ void lsq_solve_kernel(const zd* R, int ldh, int n, const zd* g, zd* y) { lsq_solve(R, ldh, n, g, y); }
-
-__global__ void deflate_kernel(const zd* H, int ldh, int m, int k, const zd* c, const zd* y, zd* P, zd* Hn, zd* cn,
-                               zd* theta, DeflateWork* W, double* status) {
-  status[1] = deflate(H, ldh, m, k, c, y, P, Hn, cn, theta, *W);
-}
 
 // After a deflated restart: H <- Hn (k+1 x k), g <- cp, and the rotations of the dense
 // block are rebuilt.
@@ -446,10 +466,37 @@ __global__ void scale_coeffs_kernel(zd* cp, int n, const double2* nrm2) {
 }
 
 // ------------------------------------------------------------------ solver
+static void release(dd_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->allocs.size(); ++i)
+    if (c->allocs[i] == p) {
+      cudaFree(p);
+      c->allocs.erase(c->allocs.begin() + i);
+      return;
+    }
+}
+
+// Free the outer solver's buffers (they are sized by the basis size m).
+static void release_solver(dd_ctx* c) {
+  SolverBuffers& s = c->sv;
+  cudaStreamSynchronize(c->st);
+  for (void* p : {(void*)s.V[0], (void*)s.V[1], (void*)s.Z[0], (void*)s.Z[1], (void*)s.w, (void*)s.x64,
+                  (void*)s.f64, (void*)s.r64, (void*)s.canon64, (void*)s.H, (void*)s.R, (void*)s.P, (void*)s.Hn,
+                  (void*)s.g, (void*)s.c0, (void*)s.y, (void*)s.hA, (void*)s.hB, (void*)s.cn, (void*)s.theta,
+                  (void*)s.cp, (void*)s.partial, (void*)s.nrm2, (void*)s.status, (void*)s.lsq,
+                  (void*)s.flag, (void*)s.nu2})
+    release(c, p);
+  for (void* p : {(void*)s.h_status, (void*)s.h_H, (void*)s.h_c0, (void*)s.h_y, (void*)s.h_P, (void*)s.h_Hn,
+                  (void*)s.h_cn, (void*)s.h_theta})
+    if (p) cudaFreeHost(p);
+  delete s.h_dw;
+  s = SolverBuffers();
+}
+
 static dd_status ensure_solver(dd_ctx* c, int m) {
   SolverBuffers& s = c->sv;
   if (s.m >= m) return DD_OK;
-  if (s.m) return fail(c, DD_ERR_INVALID, "basis size larger than the first solve's is not supported by this context");
+  if (s.m) release_solver(c);
   const Geom& g = c->g;
   long long n4 = g.V * 6;
   size_t vb = (size_t)n4 * 16;
@@ -473,8 +520,15 @@ static dd_status ensure_solver(dd_ctx* c, int m) {
   TRY(dalloc(c, &s.nrm2, 4 * sizeof(double2)));
   TRY(dalloc(c, &s.status, 8 * sizeof(double)));
   TRY(dalloc(c, &s.lsq, sizeof(LsqState)));
-  TRY(dalloc(c, &s.dw, sizeof(DeflateWork)));
+  TRY(dalloc(c, &s.flag, 16));
+  TRY(dalloc(c, &s.nu2, 16));
   if (cudaMallocHost(&s.h_status, 8 * sizeof(double)) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned status");
+  size_t hb = (size_t)ld * (m + 1) * sizeof(zd);
+  for (zd** p : {&s.h_H, &s.h_P, &s.h_Hn})
+    if (cudaMallocHost(p, hb) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned deflation buffers");
+  for (zd** p : {&s.h_c0, &s.h_y, &s.h_cn, &s.h_theta})
+    if (cudaMallocHost(p, (m + 2) * sizeof(zd)) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned deflation buffers");
+  s.h_dw = new DeflateWork();
   s.m = m;
   return DD_OK;
 }
@@ -546,17 +600,18 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
       cudaEventRecord(e1, c->st);
       TRY(apply_internal(c, Zv(j), s.w, P32));
       cudaEventRecord(e2, c->st);
-      // classical Gram-Schmidt, two passes
-      int nk = launch_multi_dot(Vv(0), j + 1, n4, s.w, s.partial, c->st);
-      launch_reduce_partials(s.partial, j + 1, (double2*)s.hA, 0, c->st);
-      nk += launch_multi_axpy(s.w, Vv(0), j + 1, n4, (const double2*)s.hA, nullptr, c->st);
-      nk += launch_multi_dot(Vv(0), j + 1, n4, s.w, s.partial, c->st);
-      launch_reduce_partials(s.partial, j + 1, (double2*)s.hB, 0, c->st);
-      nk += launch_multi_axpy(s.w, Vv(0), j + 1, n4, (const double2*)s.hB, s.partial, c->st);
-      launch_reduce_partials(s.partial, 1, s.nrm2, 0, c->st);
-      arnoldi_finish_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, j, s.hA, s.hB, s.nrm2, s.lsq, s.g, s.status);
-      launch_scale_to(Vv(j + 1), s.w, n4, s.nrm2, c->st);
-      TRY(launched(c, nk + 5));
+      // Gram-Schmidt: one projection, repeated only when it cancels more than half of w
+      int nk = launch_gs_dot(Vv(0), j + 1, n4, s.w, s.partial, nullptr, 0, c->st);
+      launch_gs_reduce(s.partial, j + 1, (double2*)s.hA, nullptr, 0, c->st);
+      gs_decide_kernel<<<1, 1, 0, c->st>>>(s.hA, j + 1, s.hB, s.flag, s.nu2);
+      launch_gs_axpy(Vv(j + 1), s.w, Vv(0), j + 1, n4, (const double2*)s.hA, s.nu2, s.flag, 0, c->st);
+      launch_gs_axpy(nullptr, s.w, Vv(0), j + 1, n4, (const double2*)s.hA, nullptr, s.flag, 1, c->st);
+      nk += launch_gs_dot(Vv(0), j + 1, n4, s.w, s.partial, s.flag, 1, c->st);
+      launch_gs_reduce(s.partial, j + 1, (double2*)s.hB, s.flag, 1, c->st);
+      gs_decide2_kernel<<<1, 1, 0, c->st>>>(s.hB, j + 1, s.flag, s.nu2);
+      launch_gs_axpy(Vv(j + 1), s.w, Vv(0), j + 1, n4, (const double2*)s.hB, s.nu2, s.flag, 1, c->st);
+      arnoldi_finish_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, j, s.hA, s.hB, s.nu2, s.lsq, s.g, s.status);
+      TRY(launched(c, nk + 8));
       cudaEventRecord(e3, c->st);
       TRY(read_status(c));
       float ms;
@@ -582,10 +637,17 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
     restarts++;
     bool done_defl = false;
     if (k > 0 && mm > k) {
-      deflate_kernel<<<1, 1, 0, c->st>>>(s.H, ldh, mm, k, s.c0, s.y, s.P, s.Hn, s.cn, s.theta, s.dw, s.status);
-      TRY(launched(c));
-      TRY(read_status(c, 2));
-      if (s.h_status[1] == 0.0) {
+      // the (m+1) x m eigen-problem of the harmonic Ritz values is tiny: solve it on the
+      // host (same code as the device build) and keep the basis recombination on the GPU
+      size_t hb = (size_t)ldh * (m + 1) * sizeof(zd);
+      TRY(cuda_check(c, cudaMemcpyAsync(s.h_H, s.H, hb, cudaMemcpyDeviceToHost, c->st), "H"));
+      TRY(cuda_check(c, cudaMemcpyAsync(s.h_c0, s.c0, (m + 1) * sizeof(zd), cudaMemcpyDeviceToHost, c->st), "c"));
+      TRY(cuda_check(c, cudaMemcpyAsync(s.h_y, s.y, m * sizeof(zd), cudaMemcpyDeviceToHost, c->st), "y"));
+      TRY(cuda_check(c, cudaStreamSynchronize(c->st), "deflation inputs"));
+      int drc = deflate(s.h_H, ldh, mm, k, s.h_c0, s.h_y, s.h_P, s.h_Hn, s.h_cn, s.h_theta, *s.h_dw);
+      if (drc == 0) {
+        TRY(cuda_check(c, cudaMemcpyAsync(s.P, s.h_P, hb, cudaMemcpyHostToDevice, c->st), "P"));
+        TRY(cuda_check(c, cudaMemcpyAsync(s.Hn, s.h_Hn, hb, cudaMemcpyHostToDevice, c->st), "Hn"));
         int nxt = 1 - cur;
         float4* Vn = s.V[nxt];
         float4* Zn = s.Z[nxt];

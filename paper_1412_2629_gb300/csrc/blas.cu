@@ -275,3 +275,101 @@ void launch_axpy_64(double2* x, const double2* y, double a, long long n2, cudaSt
 }
 
 }  // namespace dd
+
+namespace dd {
+
+// ------------------------------------------------------------------ single-pass Gram-Schmidt
+// Classical Gram-Schmidt with selective reorthogonalisation, gated on the device so no
+// host round trip is needed.  Pass 1 forms h = V^H w and |w|^2 in one read of the basis.
+// The norm of the projected vector follows from Pythagoras, nu^2 = |w|^2 - |h|^2; when
+// that cancels by less than half (nu^2 >= |w|^2 / 2) one projection is accurate to FP32
+// rounding and the new basis vector (w - V h) / nu is written in a single fused pass.
+// Otherwise the projection is repeated once (the classical "twice is enough" rule).
+template <int NV>
+__global__ void __launch_bounds__(BT) gs_dot_kernel(const float4* V, int v0, int nv, long long n4, const float4* w,
+                                                    double2* partial, int ldp, const int* gate, int want) {
+  if (gate && *gate != want) return;
+  float re[NV], im[NV], ww = 0.f;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) re[i] = im[i] = 0.f;
+  const bool self = v0 == 0;
+  for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n4; q += (long long)gridDim.x * BT) {
+    float4 wq = w[q];
+    if (self) ww += wq.x * wq.x + wq.y * wq.y + wq.z * wq.z + wq.w * wq.w;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      if (v0 + i < nv) {
+        cx<float> d = dot4(V[(long long)(v0 + i) * n4 + q], wq);
+        re[i] += d.re;
+        im[i] += d.im;
+      }
+    }
+  }
+  double2 acc[NV + 1];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = make_double2(re[i], im[i]);
+  acc[NV] = make_double2(ww, 0.0);
+  __shared__ double2 out[NV + 1];
+  block_reduce<NV + 1>(acc, out);
+  if (threadIdx.x < NV && v0 + (int)threadIdx.x < nv) partial[(long long)blockIdx.x * ldp + v0 + threadIdx.x] = out[threadIdx.x];
+  if (self && threadIdx.x == 0) partial[(long long)blockIdx.x * ldp + nv] = out[NV];
+}
+
+// partial layout [block][nv + 1]: entries 0..nv-1 are V^H w, entry nv is |w|^2.
+int launch_gs_dot(const float4* V, int nv, long long n4, const float4* w, double2* partial, const int* gate, int want,
+                  cudaStream_t st) {
+  int nb = blas_partials_blocks(), n = 0;
+  for (int v0 = 0; v0 < (nv > 0 ? nv : 1); v0 += 16, ++n)
+    gs_dot_kernel<16><<<nb, BT, 0, st>>>(V, v0, nv, n4, w, partial, nv + 1, gate, want);
+  return n;
+}
+
+__global__ void gs_reduce_kernel(const double2* partial, int nb, int ld, double2* out, const int* gate, int want) {
+  if (gate && *gate != want) return;
+  int i = blockIdx.x;
+  double sx = 0, sy = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) { sx += partial[(long long)b * ld + i].x; sy += partial[(long long)b * ld + i].y; }
+  __shared__ double shx[256], shy[256];
+  shx[threadIdx.x] = sx;
+  shy[threadIdx.x] = sy;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) { shx[threadIdx.x] += shx[threadIdx.x + o]; shy[threadIdx.x] += shy[threadIdx.x + o]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[i] = make_double2(shx[0], shy[0]);
+}
+
+void launch_gs_reduce(const double2* partial, int nv, double2* out, const int* gate, int want, cudaStream_t st) {
+  gs_reduce_kernel<<<nv + 1, 256, 0, st>>>(partial, blas_partials_blocks(), nv + 1, out, gate, want);
+}
+
+// nu2 == nullptr: w -= V h in place.  Otherwise out = (w - V h) / sqrt(*nu2).
+__global__ void __launch_bounds__(BT) gs_axpy_kernel(float4* out, float4* w, const float4* V, int nv, long long n4,
+                                                     const double2* h, const double* nu2, const int* gate, int want) {
+  if (gate && *gate != want) return;
+  __shared__ float2 hs[64];
+  for (int i = threadIdx.x; i < nv; i += BT) hs[i] = make_float2((float)h[i].x, (float)h[i].y);
+  __syncthreads();
+  const float s = nu2 ? (float)(1.0 / sqrt(*nu2)) : 1.f;
+  float4* dst = nu2 ? out : w;
+  for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n4; q += (long long)gridDim.x * BT) {
+    float4 a = w[q];
+    for (int i = 0; i < nv; ++i) {
+      float4 v = V[(long long)i * n4 + q];
+      float2 c = hs[i];
+      a.x -= c.x * v.x - c.y * v.y;
+      a.y -= c.x * v.y + c.y * v.x;
+      a.z -= c.x * v.z - c.y * v.w;
+      a.w -= c.x * v.w + c.y * v.z;
+    }
+    dst[q] = make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
+  }
+}
+
+void launch_gs_axpy(float4* out, float4* w, const float4* V, int nv, long long n4, const double2* h, const double* nu2,
+                    const int* gate, int want, cudaStream_t st) {
+  gs_axpy_kernel<<<blas_partials_blocks(), BT, 0, st>>>(out, w, V, nv, n4, h, nu2, gate, want);
+}
+
+}  // namespace dd

@@ -255,8 +255,8 @@ __device__ inline void clover_mul(const R* m72, const Spinor<R>& x, Spinor<R>& y
 }
 
 // ------------------------------------------------------------------ field access
-// Spinor storage types.  FP64: 12 double2 units; FP32: 6 float4 units; FP16: 3 uint4
-// units of 8 halves each, scaled by a per-site FP32 norm (max |component|).
+// Spinor storage types.  FP64: 6 units of two double2; FP32: 6 float4 units; FP16: 3
+// uint4 units of 8 halves each, scaled by a per-site FP32 norm (max |component|).
 __device__ inline long long unit_addr(const Geom& g, long long s, int nunits, int u) {
   long long d = s >> g.lgVd;
   long long r = s & (g.Vd - 1);
@@ -265,18 +265,28 @@ __device__ inline long long unit_addr(const Geom& g, long long s, int nunits, in
 
 template <typename T> struct SpinorPtr;
 
+// FP64 spinors use the FP32 unit structure (6 units of two complex numbers, here 32 B
+// each), so the flat index of a complex number is the same in both precisions: double2
+// 2q and 2q + 1 hold the two complex numbers of float4 q.  Vector kernels that mix the
+// precisions rely on this.
 template <> struct SpinorPtr<double> {
   double2* p;
   __device__ void load(const Geom& g, long long s, Spinor<double>& v) const {
 #pragma unroll
-    for (int u = 0; u < 12; ++u) {
-      double2 q = p[unit_addr(g, s, 12, u)];
-      v.c[u / 3][u % 3] = mk(q.x, q.y);
+    for (int u = 0; u < 6; ++u) {
+      long long a = 2 * unit_addr(g, s, 6, u);
+      double2 q0 = p[a], q1 = p[a + 1];
+      v.c[(2 * u) / 3][(2 * u) % 3] = mk(q0.x, q0.y);
+      v.c[(2 * u + 1) / 3][(2 * u + 1) % 3] = mk(q1.x, q1.y);
     }
   }
   __device__ void store(const Geom& g, long long s, const Spinor<double>& v) const {
 #pragma unroll
-    for (int u = 0; u < 12; ++u) p[unit_addr(g, s, 12, u)] = make_double2(v.c[u / 3][u % 3].re, v.c[u / 3][u % 3].im);
+    for (int u = 0; u < 6; ++u) {
+      long long a = 2 * unit_addr(g, s, 6, u);
+      p[a] = make_double2(v.c[(2 * u) / 3][(2 * u) % 3].re, v.c[(2 * u) / 3][(2 * u) % 3].im);
+      p[a + 1] = make_double2(v.c[(2 * u + 1) / 3][(2 * u + 1) % 3].re, v.c[(2 * u + 1) / 3][(2 * u + 1) % 3].im);
+    }
   }
 };
 

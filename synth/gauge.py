@@ -13,6 +13,8 @@ rounding of those steps.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 import torch
 
@@ -60,11 +62,20 @@ def reunitarize(M: torch.Tensor) -> torch.Tensor:
     return torch.stack([r0, r1, r2], dim=-2)
 
 
-def _expi_hermitian(Hm: torch.Tensor) -> torch.Tensor:
-    """exp(i H) for Hermitian [..., 3, 3] H via its eigendecomposition."""
-    w, V = torch.linalg.eigh(Hm)
-    phase = torch.polar(torch.ones_like(w), w)
-    return (V * phase.unsqueeze(-2)) @ V.conj().transpose(-1, -2)
+def _expi_hermitian(Hm: torch.Tensor, terms: int = 18) -> torch.Tensor:
+    """exp(i H) for Hermitian [..., 3, 3] H by scaling and squaring: X = i H / 2^s with
+    |X|_F <= 1/2, a Taylor polynomial of X (Horner form, remainder < 1e-20), then s
+    squarings.  Batched matrix products only, so it runs on any device."""
+    nrm = float(torch.linalg.matrix_norm(Hm).max()) if Hm.numel() else 0.0
+    s = max(0, math.ceil(math.log2(nrm / 0.5))) if nrm > 0.5 else 0
+    X = (1j / 2 ** s) * Hm
+    eye = torch.eye(3, dtype=Hm.dtype, device=Hm.device).expand_as(Hm)
+    E = eye.clone()
+    for n in range(terms, 0, -1):
+        E = eye + (X @ E) / n
+    for _ in range(s):
+        E = E @ E
+    return E
 
 
 def random_su3_field(dims, width: float, seed: int, device="cpu", chunk=1 << 20) -> torch.Tensor:
