@@ -13,6 +13,7 @@
 // than `defl_tol` of the residual.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <string>
@@ -43,6 +44,7 @@ struct SolverBuffers {
   zd *H = nullptr, *R = nullptr, *g = nullptr, *c0 = nullptr, *y = nullptr;
   zd *hA = nullptr, *hB = nullptr, *P = nullptr, *Hn = nullptr, *cn = nullptr, *theta = nullptr, *cp = nullptr;
   double2* partial = nullptr;
+  double2* partial2 = nullptr;         // per-block norm partials of the Gram-Schmidt projection
   double2* nrm2 = nullptr;
   double* status = nullptr;            // [0] residual estimate, [1] deflate status
   double* h_status = nullptr;          // pinned host mirror
@@ -61,6 +63,7 @@ struct dd_ctx {
   cudaStream_t st = nullptr;
   std::string err;
   long long launches = 0;
+  bool trace = false;   // DD_TRACE=1 in the environment: one line per solver step on stderr
   // gauge
   double* Ucanon = nullptr;
   double2* U64 = nullptr;
@@ -186,6 +189,8 @@ extern "C" dd_status dd_create(dd_ctx** out, const int dims[4], const int domain
   c->g = g;
   c->anti = t_antiperiodic ? 1 : 0;
   c->st = (cudaStream_t)stream;
+  const char* tr = getenv("DD_TRACE");
+  c->trace = tr && tr[0] && tr[0] != '0';
   if (dalloc(c, &c->dstatus, 64) != DD_OK || dalloc(c, &c->sap_err, 64) != DD_OK) {
     for (void* p : c->allocs) cudaFree(p);
     delete c;
@@ -404,21 +409,17 @@ extern "C" dd_status dd_sap_precondition(dd_ctx* c, const float* in, float* out,
 }
 
 // ------------------------------------------------------------------ small dense kernels
-__global__ void gs_decide_kernel(const zd* hA, int nv, zd* hB, int* flag, double* nu2) {
-  double ww = hA[nv].re, hh = 0;
-  for (int i = 0; i < nv; ++i) hh += abs2(hA[i]);
-  double v = ww - hh;
+// After the first projection: |w - V h|^2 is known exactly; ask for a second projection
+// when it is below half of |w|^2.
+__global__ void gs_decide_kernel(const zd* hA, int nv, const double2* nrm_a, zd* hB, int* flag, double* nu2) {
+  double ww = hA[nv].re, v = nrm_a->x;
   for (int i = 0; i <= nv; ++i) hB[i] = Z(0.0);
-  if (v >= 0.5 * ww && v > 0) { *flag = 0; *nu2 = v; }
-  else *flag = 1;
+  *nu2 = v;
+  *flag = v < 0.5 * ww ? 1 : 0;
 }
 
-__global__ void gs_decide2_kernel(const zd* hB, int nv, const int* flag, double* nu2) {
-  if (!*flag) return;
-  double ww = hB[nv].re, hh = 0;
-  for (int i = 0; i < nv; ++i) hh += abs2(hB[i]);
-  double v = ww - hh;
-  *nu2 = v > 0 ? v : (ww > 0 ? ww : 1e-300);
+__global__ void gs_decide2_kernel(const int* flag, const double2* nrm_b, double* nu2) {
+  if (*flag) *nu2 = nrm_b->x;
 }
 
 __global__ void arnoldi_finish_kernel(zd* H, zd* R, int ldh, int j, const zd* hA, const zd* hB, const double* nu2,
@@ -431,6 +432,7 @@ __global__ void arnoldi_finish_kernel(zd* H, zd* R, int ldh, int j, const zd* hA
   for (int i = 0; i <= j + 1; ++i) rc[i] = col[i];
   status[0] = lsq_add_column(*lsq, R, ldh, j, j + 2, g);
   status[2] = h;
+  status[3] = abs2(hB[0]) > 0 ? 1.0 : 0.0;
 }
 
 __global__ void lsq_solve_kernel(const zd* R, int ldh, int n, const zd* g, zd* y) { lsq_solve(R, ldh, n, g, y); }
@@ -483,7 +485,7 @@ static void release_solver(dd_ctx* c) {
   for (void* p : {(void*)s.V[0], (void*)s.V[1], (void*)s.Z[0], (void*)s.Z[1], (void*)s.w, (void*)s.x64,
                   (void*)s.f64, (void*)s.r64, (void*)s.canon64, (void*)s.H, (void*)s.R, (void*)s.P, (void*)s.Hn,
                   (void*)s.g, (void*)s.c0, (void*)s.y, (void*)s.hA, (void*)s.hB, (void*)s.cn, (void*)s.theta,
-                  (void*)s.cp, (void*)s.partial, (void*)s.nrm2, (void*)s.status, (void*)s.lsq,
+                  (void*)s.cp, (void*)s.partial, (void*)s.partial2, (void*)s.nrm2, (void*)s.status, (void*)s.lsq,
                   (void*)s.flag, (void*)s.nu2})
     release(c, p);
   for (void* p : {(void*)s.h_status, (void*)s.h_H, (void*)s.h_c0, (void*)s.h_y, (void*)s.h_P, (void*)s.h_Hn,
@@ -517,6 +519,7 @@ static dd_status ensure_solver(dd_ctx* c, int m) {
   TRY(dalloc(c, &s.Hn, hm));
   for (zd** p : {&s.g, &s.c0, &s.y, &s.hA, &s.hB, &s.cn, &s.theta, &s.cp}) TRY(dalloc(c, p, (m + 2) * sizeof(zd)));
   TRY(dalloc(c, &s.partial, (size_t)blas_partials_blocks() * (m + 2) * sizeof(double2)));
+  TRY(dalloc(c, &s.partial2, (size_t)blas_partials_blocks() * sizeof(double2)));
   TRY(dalloc(c, &s.nrm2, 4 * sizeof(double2)));
   TRY(dalloc(c, &s.status, 8 * sizeof(double)));
   TRY(dalloc(c, &s.lsq, sizeof(LsqState)));
@@ -539,7 +542,7 @@ struct Timer {
   ~Timer() { cudaEventDestroy(a); cudaEventDestroy(b); }
 };
 
-static dd_status read_status(dd_ctx* c, int n = 3) {
+static dd_status read_status(dd_ctx* c, int n = 4) {
   SolverBuffers& s = c->sv;
   TRY(cuda_check(c, cudaMemcpyAsync(s.h_status, s.status, n * sizeof(double), cudaMemcpyDeviceToHost, c->st), "status"));
   return cuda_check(c, cudaStreamSynchronize(c->st), "solver step");
@@ -600,18 +603,24 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
       cudaEventRecord(e1, c->st);
       TRY(apply_internal(c, Zv(j), s.w, P32));
       cudaEventRecord(e2, c->st);
-      // Gram-Schmidt: one projection, repeated only when it cancels more than half of w
+      // Gram-Schmidt: classical projection with the exact norm of the result, repeated
+      // once when it cancels more than half of |w| (Daniel-Gragg-Kaufman-Stewart test)
+      float4* vn = Vv(j + 1);
+      double2* nrm_a = s.nrm2 + 1;
+      double2* nrm_b = s.nrm2 + 2;
       int nk = launch_gs_dot(Vv(0), j + 1, n4, s.w, s.partial, nullptr, 0, c->st);
       launch_gs_reduce(s.partial, j + 1, (double2*)s.hA, nullptr, 0, c->st);
-      gs_decide_kernel<<<1, 1, 0, c->st>>>(s.hA, j + 1, s.hB, s.flag, s.nu2);
-      launch_gs_axpy(Vv(j + 1), s.w, Vv(0), j + 1, n4, (const double2*)s.hA, s.nu2, s.flag, 0, c->st);
-      launch_gs_axpy(nullptr, s.w, Vv(0), j + 1, n4, (const double2*)s.hA, nullptr, s.flag, 1, c->st);
-      nk += launch_gs_dot(Vv(0), j + 1, n4, s.w, s.partial, s.flag, 1, c->st);
+      launch_gs_project(vn, s.w, Vv(0), j + 1, n4, (const double2*)s.hA, s.partial2, nullptr, 0, c->st);
+      launch_gs_reduce(s.partial2, 0, nrm_a, nullptr, 0, c->st);
+      gs_decide_kernel<<<1, 1, 0, c->st>>>(s.hA, j + 1, nrm_a, s.hB, s.flag, s.nu2);
+      nk += launch_gs_dot(Vv(0), j + 1, n4, vn, s.partial, s.flag, 1, c->st);
       launch_gs_reduce(s.partial, j + 1, (double2*)s.hB, s.flag, 1, c->st);
-      gs_decide2_kernel<<<1, 1, 0, c->st>>>(s.hB, j + 1, s.flag, s.nu2);
-      launch_gs_axpy(Vv(j + 1), s.w, Vv(0), j + 1, n4, (const double2*)s.hB, s.nu2, s.flag, 1, c->st);
+      launch_gs_project(vn, vn, Vv(0), j + 1, n4, (const double2*)s.hB, s.partial2, s.flag, 1, c->st);
+      launch_gs_reduce(s.partial2, 0, nrm_b, s.flag, 1, c->st);
+      gs_decide2_kernel<<<1, 1, 0, c->st>>>(s.flag, nrm_b, s.nu2);
+      launch_scale_inplace(vn, n4, s.nu2, c->st);
       arnoldi_finish_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, j, s.hA, s.hB, s.nu2, s.lsq, s.g, s.status);
-      TRY(launched(c, nk + 8));
+      TRY(launched(c, nk + 11));
       cudaEventRecord(e3, c->st);
       TRY(read_status(c));
       float ms;
@@ -620,6 +629,9 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
       cudaEventElapsedTime(&ms, e2, e3); tGS += ms * 1e-3;
       iters++;
       double est = s.h_status[0];
+      if (c->trace)
+        fprintf(stderr, "[dd] it %d j %d est/rho %.3e h %.3e reorth %d\n", iters, j, est / rho_cycle, s.h_status[2],
+                (int)s.h_status[3]);
       if (!isfinite(est) || !isfinite(s.h_status[2])) { rc = fail(c, DD_ERR_NONFINITE, "non-finite Arnoldi step"); break; }
       // stop the cycle when the target is met or FP32 vectors cannot resolve further
       if (est <= 0.5 * tol * nf || est <= 2e-6 * rho_cycle || iters >= p->max_iter) { mm = j + 1; break; }
@@ -635,6 +647,19 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
     if (rel <= tol) break;
     if (iters >= p->max_iter) { rc = fail(c, DD_ERR_NOT_CONVERGED, "iteration limit reached"); break; }
     restarts++;
+    if (c->trace && getenv("DD_TRACE")[0] == '2') {
+      // orthogonality of the finished basis: max |V^H V - I|
+      double dev = 0;
+      std::vector<zd> row(mm + 1);
+      for (int i = 0; i <= mm; ++i) {
+        launch_multi_dot(Vv(0), mm + 1, n4, Vv(i), s.partial, c->st);
+        launch_reduce_partials(s.partial, mm + 1, (double2*)s.cp, 0, c->st);
+        cudaMemcpyAsync(row.data(), s.cp, (mm + 1) * sizeof(zd), cudaMemcpyDeviceToHost, c->st);
+        cudaStreamSynchronize(c->st);
+        for (int l = 0; l <= mm; ++l) dev = fmax(dev, zabs(row[l] - Z(l == i ? 1.0 : 0.0)));
+      }
+      fprintf(stderr, "[dd] basis orthogonality max|V^H V - I| = %.3e over %d vectors\n", dev, mm + 1);
+    }
     bool done_defl = false;
     if (k > 0 && mm > k) {
       // the (m+1) x m eigen-problem of the harmonic Ritz values is tiny: solve it on the
@@ -666,6 +691,7 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
         double pc = 0;
         for (auto& z : cp) pc += abs2(z);
         double miss = sqrt(fmax(0.0, 1.0 - pc / rho2));
+        if (c->trace) fprintf(stderr, "[dd] restart: true residual %.3e, deflation misses %.3e\n", rel, miss);
         if (miss <= defl_tol) {
           restart_lsq_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, k, s.Hn, s.cp, s.g, s.c0, s.lsq, s.status);
           TRY(launched(c));

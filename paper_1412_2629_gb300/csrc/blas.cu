@@ -373,3 +373,53 @@ void launch_gs_axpy(float4* out, float4* w, const float4* V, int nv, long long n
 }
 
 }  // namespace dd
+
+namespace dd {
+
+// out = w - V h with |out|^2 partials per block (exact norm of the projected vector).
+// in_place: out aliases w.
+__global__ void __launch_bounds__(BT) gs_project_kernel(float4* out, const float4* w, const float4* V, int nv,
+                                                        long long n4, const double2* h, double2* norm_partial,
+                                                        const int* gate, int want) {
+  if (gate && *gate != want) return;
+  __shared__ float2 hs[64];
+  for (int i = threadIdx.x; i < nv; i += BT) hs[i] = make_float2((float)h[i].x, (float)h[i].y);
+  __syncthreads();
+  float nrm = 0.f;
+  for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n4; q += (long long)gridDim.x * BT) {
+    float4 a = w[q];
+    for (int i = 0; i < nv; ++i) {
+      float4 v = V[(long long)i * n4 + q];
+      float2 c = hs[i];
+      a.x -= c.x * v.x - c.y * v.y;
+      a.y -= c.x * v.y + c.y * v.x;
+      a.z -= c.x * v.z - c.y * v.w;
+      a.w -= c.x * v.w + c.y * v.z;
+    }
+    out[q] = a;
+    nrm += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+  }
+  double2 acc[1] = {make_double2(nrm, 0.0)};
+  __shared__ double2 o[1];
+  block_reduce<1>(acc, o);
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = o[0];
+}
+
+void launch_gs_project(float4* out, const float4* w, const float4* V, int nv, long long n4, const double2* h,
+                       double2* norm_partial, const int* gate, int want, cudaStream_t st) {
+  gs_project_kernel<<<blas_partials_blocks(), BT, 0, st>>>(out, w, V, nv, n4, h, norm_partial, gate, want);
+}
+
+// v *= 1 / sqrt(*nu2)
+__global__ void scale_inplace_kernel(float4* v, long long n4, const double* nu2) {
+  float s = (float)(1.0 / sqrt(*nu2));
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+    float4 a = v[q];
+    v[q] = make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
+  }
+}
+void launch_scale_inplace(float4* v, long long n4, const double* nu2, cudaStream_t st) {
+  scale_inplace_kernel<<<blas_partials_blocks(), BT, 0, st>>>(v, n4, nu2);
+}
+
+}  // namespace dd

@@ -87,4 +87,7 @@ int launch_gs_dot(const float4* V, int nv, long long n4, const float4* w, double
 void launch_gs_reduce(const double2* partial, int nv, double2* out, const int* gate, int want, cudaStream_t st);
 void launch_gs_axpy(float4* out, float4* w, const float4* V, int nv, long long n4, const double2* h, const double* nu2,
                     const int* gate, int want, cudaStream_t st);
+void launch_gs_project(float4* out, const float4* w, const float4* V, int nv, long long n4, const double2* h,
+                       double2* norm_partial, const int* gate, int want, cudaStream_t st);
+void launch_scale_inplace(float4* v, long long n4, const double* nu2, cudaStream_t st);
 }  // namespace dd
