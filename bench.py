@@ -32,7 +32,7 @@ METRIC = "time-to-solution to 1e-10 true residual, mixed FP16/FP32/FP64 SAP-FGMR
 FLOP_HOP, FLOP_CLOVER, FLOP_A = 168, 504, 1848      # Sec. II-B: 1344 = 8 x 168, 504, 1848
 # Outer iterations the 32^3x64 solve takes (measured on the GPU, mixed and FP32 alike);
 # only used to scale the oracle's sampled cost to a whole solve.
-ORACLE_ITERS_32x64 = 12
+ORACLE_ITERS_32x64 = 888
 
 
 # ------------------------------------------------------------------ flop / byte model
@@ -203,10 +203,14 @@ def config_dict(w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-mixed", action="store_true", help="time the mixed solve only (profiling runs)")
+    ap.add_argument("--case", default="solve", choices=["solve", "sap", "dslash"],
+                    help="sap / dslash: time one kernel alone on --lattice (kernel studies, ncu captures)")
+    ap.add_argument("--lattice", default="32,32,32,64")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -228,6 +232,8 @@ def main():
     from paper_1412_2629_gb300 import build as B
     B.build()
     from paper_1412_2629_gb300 import dd
+    if args.case != "solve":
+        return kernel_case(args, local)
 
     torch.cuda.set_device(local)
     w = synth.WORKLOADS[WORKLOAD]
@@ -254,7 +260,7 @@ def main():
         x_pin.zero_()
         return ctx.dd_solve(f_pin, x_pin, where=dd.DD_HOST, storage_prec=prec, **kw)
 
-    def timed(prec, where, steps, warmup):
+    def timed(prec, where, steps, warmup, tag):
         for _ in range(warmup):
             solve(prec, where)
         if world > 1:
@@ -263,11 +269,13 @@ def main():
         l0 = ctx.dd_launch_count()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         infos = []
+        torch.cuda.nvtx.range_push(tag)
         e0.record(st)
         for _ in range(steps):
             infos.append(solve(prec, where).as_dict())
         e1.record(st)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         if world > 1:
             dist.barrier()
         ms = e0.elapsed_time(e1) / steps
@@ -275,10 +283,13 @@ def main():
 
     clk = ClockSampler(local)
     clk.start()
-    ms_mixed, infos, launches = timed(dd.DD_PREC_FP16, dd.DD_DEVICE, args.steps, args.warmup)
+    ms_mixed, infos, launches = timed(dd.DD_PREC_FP16, dd.DD_DEVICE, args.steps, args.warmup, "timed_mixed")
     clocks = clk.stop()
-    ms_e2e, infos_e2e, _ = timed(dd.DD_PREC_FP16, dd.DD_HOST, args.steps, 1)
-    ms_fp32, infos32, _ = timed(dd.DD_PREC_FP32, dd.DD_DEVICE, max(2, args.steps // 2), 1)
+    if args.only_mixed:
+        ms_e2e, ms_fp32, infos32 = float("nan"), float("nan"), infos
+    else:
+        ms_e2e, infos_e2e, _ = timed(dd.DD_PREC_FP16, dd.DD_HOST, args.steps, 1, "timed_e2e")
+        ms_fp32, infos32, _ = timed(dd.DD_PREC_FP32, dd.DD_DEVICE, max(2, args.steps // 2), 1, "timed_fp32")
 
     if world > 1:
         t = torch.tensor([ms_mixed, ms_e2e, ms_fp32], device="cuda")
@@ -353,6 +364,55 @@ def main():
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def kernel_case(args, local):
+    """Time one kernel alone (Schwarz half-sweeps or the FP32 operator) on a lattice of
+    the 32^3x64 workload's kind, with CUDA events on the launching stream."""
+    import torch
+
+    import synth
+    from paper_1412_2629_gb300 import dd
+    base = synth.WORKLOADS[WORKLOAD]
+    dims = tuple(int(v) for v in args.lattice.split(","))
+    w = synth.Workload("case", dims, base.width, base.ape_steps, base.kappa, base.csw, base.domain, base.i_schwarz,
+                       base.i_domain, base.m, base.k, base.gauge_seed, base.source_seed)
+    st = torch.cuda.current_stream()
+    U, f = make_inputs(w, "cuda")
+    ctx = dd.Context(w.dims, w.domain, True, st.cuda_stream)
+    ctx.dd_load_gauge(torch.view_as_real(U).contiguous(), dd.DD_DEVICE)
+    ctx.dd_build_clover(w.kappa, w.csw)
+    del U
+    V = int(np.prod(dims))
+    src = torch.view_as_real(torch.from_numpy(f)).to(torch.float32).cuda().contiguous()
+    a = torch.empty(ctx.dd_spinor_bytes(dd.DD_PREC_FP32, dd.DD_LAYOUT_INTERNAL), dtype=torch.uint8, device="cuda")
+    b = torch.empty_like(a)
+    ctx.dd_pack_spinor(src, dd.DD_PREC_FP32, a, dd.DD_PREC_FP32)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = args.steps
+    if args.case == "sap":
+        run = lambda: ctx.dd_sap_precondition(a, b, w.i_schwarz, w.i_domain, dd.DD_PREC_FP16, dd.DD_LAYOUT_INTERNAL)
+        launches = 2 * w.i_schwarz
+    else:
+        run = lambda: ctx.dd_apply_D(a, b, dd.DD_PREC_FP32, dd.DD_LAYOUT_INTERNAL)
+        launches = 1
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        run()
+    e1.record(st)
+    torch.cuda.synchronize()
+    launch_s = e0.elapsed_time(e1) / 1e3 / (reps * launches)
+    if args.case == "sap":
+        useful, nominal = sap_visit_flops(w.domain, w.i_domain)
+        out = {"case": "sap_kernel", "lattice": dims, "launch_ms": 1e3 * launch_s,
+               "tflops_useful": useful * V / 2 / launch_s / 1e12, "gflops_nominal": nominal * V / 2 / launch_s / 1e9}
+    else:
+        out = {"case": "apply_A_kernel<float>", "lattice": dims, "launch_ms": 1e3 * launch_s,
+               "gbs_algorithmic": dslash_bytes_per_site("fp32") * V / launch_s / 1e9}
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
