@@ -60,7 +60,7 @@ enum { DD_PREC_FP64 = 0, DD_PREC_FP32 = 1, DD_PREC_FP16 = 2 };
 enum { DD_HOST = 0, DD_DEVICE = 1 };
 enum { DD_LAYOUT_CANONICAL = 0, DD_LAYOUT_INTERNAL = 1 };
 
-/* Schwarz preconditioner parameters (Sec. II-C, Table I). */
+/* Schwarz preconditioner parameters (Sec. II-D, Table I). */
 typedef struct {
   int i_schwarz;      /* Schwarz iterations; one iteration = black then white half-sweep (paper: 16) */
   int i_domain;       /* MR steps per domain solve (paper: 4-5) */
@@ -91,7 +91,7 @@ typedef struct {
 
 /* Create a context for a lattice dims = {Lx, Ly, Lz, Lt} split into domains of shape
  * domain = {bx, by, bz, bt}.  Each b_mu must be a power of two >= 2 and divide L_mu,
- * each L_mu / b_mu must be even (two-colouring of the domains, Sec. IV-D) and >= 2, and
+ * each L_mu / b_mu must be even (two-colouring of the domains, Sec. IV-B, Eq. 6) and >= 2, and
  * the Schwarz kernel needs 64 <= prod(b) <= 512.  stream: a cudaStream_t or NULL.
  * Allocates its device memory with cudaMalloc. */
 dd_status dd_create(dd_ctx** out, const int dims[4], const int domain[4], int t_antiperiodic, void* stream);
@@ -112,12 +112,12 @@ dd_status dd_build_clover(dd_ctx* ctx, double kappa, double c_sw);
  * arithmetic).  in and out must not overlap. */
 dd_status dd_apply_D(dd_ctx* ctx, const void* in, void* out, int prec, int layout);
 
-/* out = M in: the multiplicative Schwarz preconditioner (Table I, Sec. II-C) with
+/* out = M in: the multiplicative Schwarz preconditioner (Table I, Sec. II-D) with
  * I_Schwarz black/white sweeps of even-odd MR domain solves.  in/out: FP32 device
  * buffers in `layout`; they may not overlap. */
 dd_status dd_sap_precondition(dd_ctx* ctx, const float* in, float* out, const dd_sap_params* p, int layout);
 
-/* Solve A x = f (Sec. III, Table I) for nrhs right-hand sides stored one after another
+/* Solve A x = f (Sec. II-C, Table I) for nrhs right-hand sides stored one after another
  * in the canonical FP64 layout (host or device memory per `where`).  x holds the
  * initial guess on entry (zeros are fine) and the solution on exit.  Outer FGMRES-DR
  * in FP32 vectors with FP64 Hessenberg, Gram-Schmidt coefficients and least squares;

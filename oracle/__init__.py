@@ -8,7 +8,7 @@ dependency is the seeded input generator in ``synth``.
 Modules:
   wilson  -- gamma matrices, Wilson hopping term (Eq. 2), clover term (Eq. 3) and the
              Wilson-clover operator A (Eq. 1); a per-site variant for sampled checks.
-  dd      -- domains and colours, block-diagonal D / coupling R split (Sec. II-C),
+  dd      -- domains and colours, block-diagonal D / coupling R split (Sec. II-D),
              even-odd Schur complement (Eq. 5), MR domain solver, multiplicative SAP
              (Table I).
   fgmres  -- flexible GMRES with deflated restarts (Table I, outer solver).

@@ -1,4 +1,4 @@
-"""Oracle for the Schwarz preconditioner (Sec. II-C, Eq. 4-5, Table I).
+"""Oracle for the Schwarz preconditioner (Sec. II-D, Eq. 4-5, Table I).
 
 Test infrastructure only (see the package docstring).
 

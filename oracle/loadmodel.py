@@ -1,4 +1,4 @@
-"""Domain count and load of Sec. V-B (Eq. 6-7).  Test infrastructure only.
+"""Domain count and load of Sec. IV-B (Eq. 6-7).  Test infrastructure only.
 
 n_domain = V / (2 V_domain): domains of one colour processed in parallel.
 load     = n_domain / (N_core * ceil(n_domain / N_core)).

@@ -1,5 +1,5 @@
 // Multiplicative Schwarz (SAP) half-sweep: every domain of one colour is solved
-// approximately in one launch, one CTA per domain (Sec. II-C, Table I).
+// approximately in one launch, one CTA per domain (Sec. II-D, Table I).
 //
 // Formulation.  Per site the state is u (accumulated solution) and, on even sites only,
 // the residual r of the last solve of its domain (the odd residual after a solve is

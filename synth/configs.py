@@ -1,7 +1,7 @@
 """The five synthetic workloads: lattice shapes, couplings, seeds and solver settings.
 
 They stand in for the paper's production ensembles (32^3x64, 48^3x64, 64^3x128
-clover lattices, Sec. V), which are not available: random SU(3) fields of a stated
+clover lattices, Sec. IV-C), which are not available: random SU(3) fields of a stated
 width, optionally APE smoothed, with Gaussian or point sources.
 """
 from __future__ import annotations

@@ -1,4 +1,4 @@
-"""GPU parity of the Schwarz preconditioner M (Sec. II-C, Table I) against the oracle's
+"""GPU parity of the Schwarz preconditioner M (Sec. II-D, Table I) against the oracle's
 multiplicative SAP with the same domains, colours and MR step count.
 
 Bars (MR step lengths depend on the data, so rounding compounds mildly): FP32 storage

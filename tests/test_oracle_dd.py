@@ -1,4 +1,4 @@
-"""Pins for the oracle's domain decomposition, Schur complement, MR and SAP (Sec. II-C)."""
+"""Pins for the oracle's domain decomposition, Schur complement, MR and SAP (Sec. II-D)."""
 import numpy as np
 import pytest
 
