@@ -117,6 +117,23 @@ dd_status dd_apply_D(dd_ctx* ctx, const void* in, void* out, int prec, int layou
  * buffers in `layout`; they may not overlap. */
 dd_status dd_sap_precondition(dd_ctx* ctx, const float* in, float* out, const dd_sap_params* p, int layout);
 
+/* out = M in like dd_sap_precondition, but without allocating: the paper has no
+ * counterpart to this entry point.  It is for callers that cannot call cudaMalloc when
+ * they apply the preconditioner: code running under CUDA stream capture (a cudaMalloc
+ * there breaks or invalidates the capture), frameworks that own all device memory through
+ * their own pool, and loops that cannot afford cudaMalloc's device-wide synchronisation.
+ * in/out: FP32 device buffers in the internal layout (see dd_pack_spinor); the context's
+ * gauge field and clover must already be built (dd_load_gauge / dd_build_clover allocate,
+ * this call does not).  The Schwarz working state lives in one fixed 64 MiB array in the
+ * library's device memory, held by every GPU that loads the library until the process
+ * exits; lattices whose state does not fit are rejected with DD_ERR_INVALID and a message
+ * giving both sizes (about 160 bytes per site with FP16 storage, 230 with FP32: up to
+ * ~4e5 sites).  All calls share that array, so calls that overlap on the GPU (other
+ * streams, other contexts, other threads) race and must be serialised by the caller.
+ * The first call on each device looks up the array's address (cudaGetSymbolAddress) with
+ * that device current; make it before any stream capture.  Synchronous like the others. */
+dd_status dd_sap_precondition_noalloc(dd_ctx* ctx, const float* in, float* out, const dd_sap_params* p);
+
 /* Solve A x = f (Sec. II-C, Table I) for nrhs right-hand sides stored one after another
  * in the canonical FP64 layout (host or device memory per `where`).  x holds the
  * initial guess on entry (zeros are fine) and the solution on exit.  Outer FGMRES-DR

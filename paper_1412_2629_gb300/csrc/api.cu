@@ -910,3 +910,61 @@ extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4],
   out->storage_prec = storage_prec;
   return cuda_check(c, cudaStreamSynchronize(c->st), "autotune");
 }
+
+// ------------------------------------------------------------------ allocation-free Schwarz
+// Same preconditioner as dd_sap_precondition (internal FP32 layout), but its working
+// state (stored residual, solution, face buffers, error word) lives in a fixed array of
+// the library's global memory instead of context buffers made by cudaMalloc.  The first
+// call on a device looks up that array's device address (cudaGetSymbolAddress); make
+// that first call before any stream capture.
+extern "C" dd_status dd_sap_precondition_noalloc(dd_ctx* c, const float* in, float* out, const dd_sap_params* p) {
+  if (!c || !in || !out) return DD_ERR_INVALID;
+  TRY(check_sap_params(c, p));
+  if (p->i_domain == 0) return fail(c, DD_ERR_INVALID, "i_domain must be >= 1");
+  const Geom& g = c->g;
+  int prec = p->storage_prec == DD_PREC_FP16 ? P16 : P32;
+  // carve the fixed array: residual (even sites), solution, faces, error word
+  size_t half_sites = (size_t)g.V / 2;
+  size_t r_bytes = prec == P16 ? half_sites * 48 : half_sites * 96;
+  size_t rn_bytes = prec == P16 ? half_sites * 4 : 0;
+  size_t u_bytes = prec == P16 ? (size_t)g.V * 48 : (size_t)g.V * 96;
+  size_t un_bytes = prec == P16 ? (size_t)g.V * 4 : 0;
+  size_t f_bytes = (size_t)g.ND * g.face_block * 48;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  size_t need = up(r_bytes) + up(rn_bytes) + up(u_bytes) + up(un_bytes) + up(f_bytes) + 256;
+  if (need > sap_noalloc_scratch_bytes())
+    return fail(c, DD_ERR_INVALID, "lattice too large for the allocation-free Schwarz entry point: needs " +
+                                       std::to_string(need) + " bytes of scratch, the fixed array holds " +
+                                       std::to_string(sap_noalloc_scratch_bytes()));
+  if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
+  char* base = (char*)sap_noalloc_scratch();
+  if (!base) return fail(c, DD_ERR_CUDA, "cudaGetSymbolAddress of the fixed scratch array failed");
+  SapState S;
+  S.mat_prec = prec;
+  S.vec_prec = prec;
+  S.links = prec == P16 ? (const void*)c->U16 : (const void*)c->U32;
+  S.smat = prec == P16 ? (const void*)c->S16 : (const void*)c->S32;
+  size_t off = 0;
+  S.r_store = base + off; off += up(r_bytes);
+  S.r_norm = rn_bytes ? (float*)(base + off) : nullptr; off += up(rn_bytes);
+  S.u_store = base + off; off += up(u_bytes);
+  S.u_norm = un_bytes ? (float*)(base + off) : nullptr; off += up(un_bytes);
+  S.faces = (float4*)(base + off); off += up(f_bytes);
+  S.err = (int*)(base + off);
+  S.mat_in_smem = sap_mat_fits_smem(g, prec);
+  // the error word must start at zero; residual, solution and faces are written before
+  // they are read within one call
+  TRY(cuda_check(c, cudaMemsetAsync(S.err, 0, sizeof(int), c->st), "clear error word"));
+  for (int s = 0; s < p->i_schwarz; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      int first = s == 0, use_faces = !(s == 0 && colour == 0), last = s == p->i_schwarz - 1;
+      if (sap_half_sweep(g, S, colour, first, use_faces, last, (const float4*)in, (float4*)out, p->i_domain, c->st))
+        return fail(c, DD_ERR_CUDA, std::string("Schwarz launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+      TRY(launched(c));
+    }
+  int e = 0;
+  TRY(cuda_check(c, cudaMemcpyAsync(&e, S.err, sizeof(int), cudaMemcpyDeviceToHost, c->st), "error word"));
+  TRY(cuda_check(c, cudaStreamSynchronize(c->st), "sap_noalloc"));
+  if (e) return fail(c, DD_ERR_TIMEOUT, "a bounded wait for the domain's staged data ran out");
+  return DD_OK;
+}

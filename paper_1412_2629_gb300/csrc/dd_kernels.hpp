@@ -62,6 +62,9 @@ int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int 
 size_t sap_smem_bytes(const Geom& g, int mat_prec, bool mat_in_smem);
 bool sap_mat_fits_smem(const Geom& g, int mat_prec);
 int sap_max_domain_sites();
+// Fixed scratch array of the allocation-free Schwarz entry point (size, device address).
+size_t sap_noalloc_scratch_bytes();
+void* sap_noalloc_scratch();
 
 // ---- BLAS on FP32 / FP64 internal vectors (blas.cu).  n4 = number of float4 (or
 // double2) units in one vector; vectors of a basis are contiguous, stride n4.

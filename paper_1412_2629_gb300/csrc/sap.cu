@@ -598,3 +598,34 @@ int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int 
 }
 
 }  // namespace dd
+
+// ------------------------------------------------------------------ allocation-free variant
+// Scratch of dd_sap_precondition_noalloc: a fixed array in this module's global memory.
+// Every GPU that loads the library holds it until the process exits; every call of the
+// allocation-free entry point shares it.
+namespace dd {
+
+constexpr size_t SAP_NOALLOC_SCRATCH_BYTES = size_t(64) << 20;   // 64 MiB
+static __device__ __align__(256) unsigned char g_sap_noalloc_scratch[SAP_NOALLOC_SCRATCH_BYTES];
+
+size_t sap_noalloc_scratch_bytes() { return SAP_NOALLOC_SCRATCH_BYTES; }
+
+// Device address of the scratch array on the current device.  In host code the array's
+// name is only a stand-in, so the address is looked up with cudaGetSymbolAddress, once per
+// device, with that device current.  Returns nullptr if the lookup fails.
+void* sap_noalloc_scratch() {
+  static void* addr[64] = {};
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_sap_noalloc_scratch) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+}  // namespace dd

@@ -66,6 +66,7 @@ def lib():
             "dd_build_clover": (I, [P, D, D]),
             "dd_apply_D": (I, [P, P, P, I, I]),
             "dd_sap_precondition": (I, [P, P, P, C.POINTER(dd_sap_params), I]),
+            "dd_sap_precondition_noalloc": (I, [P, P, P, C.POINTER(dd_sap_params)]),
             "dd_solve": (I, [P, P, P, I, I, C.POINTER(dd_solve_params), C.POINTER(dd_solve_info)]),
             "dd_spinor_bytes": (C.c_size_t, [P, I, I]),
             "dd_pack_spinor": (I, [P, P, I, P, I]),
@@ -136,6 +137,12 @@ class Context:
     def dd_sap_precondition(self, inp, out, i_schwarz, i_domain, storage_prec, layout=DD_LAYOUT_CANONICAL):
         p = dd_sap_params(i_schwarz, i_domain, storage_prec)
         return self._check(lib().dd_sap_precondition(self._h, _ptr(inp), _ptr(out), C.byref(p), layout))
+
+    def dd_sap_precondition_noalloc(self, inp, out, i_schwarz, i_domain, storage_prec, check=True):
+        """Internal-layout FP32 in/out; no device allocation (fixed scratch array)."""
+        p = dd_sap_params(i_schwarz, i_domain, storage_prec)
+        s = lib().dd_sap_precondition_noalloc(self._h, _ptr(inp), _ptr(out), C.byref(p))
+        return self._check(s) if check else s
 
     def dd_solve(self, f, x, nrhs=1, where=DD_HOST, tol=1e-10, m=16, k=0, max_iter=1000, i_schwarz=16,
                  i_domain=4, storage_prec=DD_PREC_FP16, check=True):
