@@ -212,7 +212,8 @@ def main():
                     help="sap / dslash: time one kernel alone on --lattice (kernel studies, ncu captures)")
     ap.add_argument("--lattice", default="32,32,32,64")
     args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
+    if not args.only_mixed:
+        args.warmup = max(args.warmup, 3)   # profiling runs (--only-mixed) may skip the warm-up
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
