@@ -211,6 +211,7 @@ def main():
     ap.add_argument("--case", default="solve", choices=["solve", "sap", "dslash"],
                     help="sap / dslash: time one kernel alone on --lattice (kernel studies, ncu captures)")
     ap.add_argument("--lattice", default="32,32,32,64")
+    ap.add_argument("--tps", type=int, default=0, help="Schwarz kernel threads per site (0: library default)")
     args = ap.parse_args()
     if not args.only_mixed:
         args.warmup = max(args.warmup, 3)   # profiling runs (--only-mixed) may skip the warm-up
@@ -392,7 +393,8 @@ def kernel_case(args, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = args.steps
     if args.case == "sap":
-        run = lambda: ctx.dd_sap_precondition(a, b, w.i_schwarz, w.i_domain, dd.DD_PREC_FP16, dd.DD_LAYOUT_INTERNAL)
+        run = lambda: ctx.dd_sap_precondition(a, b, w.i_schwarz, w.i_domain, dd.DD_PREC_FP16, dd.DD_LAYOUT_INTERNAL,
+                                              threads_per_site=args.tps)
         launches = 2 * w.i_schwarz
     else:
         run = lambda: ctx.dd_apply_D(a, b, dd.DD_PREC_FP32, dd.DD_LAYOUT_INTERNAL)
@@ -408,7 +410,7 @@ def kernel_case(args, local):
     launch_s = e0.elapsed_time(e1) / 1e3 / (reps * launches)
     if args.case == "sap":
         useful, nominal = sap_visit_flops(w.domain, w.i_domain)
-        out = {"case": "sap_kernel", "lattice": dims, "launch_ms": 1e3 * launch_s,
+        out = {"case": "sap_kernel", "threads_per_site": args.tps or 2, "lattice": dims, "launch_ms": 1e3 * launch_s,
                "tflops_useful": useful * V / 2 / launch_s / 1e12, "gflops_nominal": nominal * V / 2 / launch_s / 1e9}
     else:
         out = {"case": "apply_A_kernel<float>", "lattice": dims, "launch_ms": 1e3 * launch_s,

@@ -66,6 +66,7 @@ typedef struct {
   int i_domain;       /* MR steps per domain solve (paper: 4-5) */
   int storage_prec;   /* DD_PREC_FP16: FP16 links, Schwarz matrices and spinors (FP32 arithmetic);
                          DD_PREC_FP32: everything FP32 */
+  int threads_per_site; /* 1 or 2 GPU threads per lattice site in the domain solve; 0 = default (2) */
 } dd_sap_params;
 
 /* Outer solver parameters (flexible GMRES with deflated restarts, Table I). */

@@ -19,7 +19,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/dd.h"
+#include "dd.h"
 #include "dd_kernels.hpp"
 #include "smalldense.cuh"
 
@@ -363,6 +363,7 @@ static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_par
   S.faces = b.faces;
   S.err = c->sap_err;
   S.mat_in_smem = sap_mat_fits_smem(c->g, prec);
+  S.threads_per_site = p->threads_per_site ? p->threads_per_site : 2;
   for (int s = 0; s < p->i_schwarz; ++s)
     for (int colour = 0; colour < 2; ++colour) {
       int first = s == 0, use_faces = !(s == 0 && colour == 0), last = s == p->i_schwarz - 1;
@@ -374,7 +375,8 @@ static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_par
 }
 
 static dd_status check_sap_params(dd_ctx* c, const dd_sap_params* p) {
-  if (!p || p->i_schwarz < 1 || p->i_domain < 0 || (p->storage_prec != DD_PREC_FP16 && p->storage_prec != DD_PREC_FP32))
+  if (!p || p->i_schwarz < 1 || p->i_domain < 0 || (p->storage_prec != DD_PREC_FP16 && p->storage_prec != DD_PREC_FP32) ||
+      p->threads_per_site < 0 || p->threads_per_site > 2)
     return fail(c, DD_ERR_INVALID, "bad Schwarz parameters");
   return DD_OK;
 }
@@ -847,7 +849,7 @@ extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4],
   int i_schwarz = out->i_schwarz > 0 ? out->i_schwarz : 16;
   const int ext[3] = {2, 4, 8};
   double best = 1e300;
-  int bestb[4] = {c->g.b[0], c->g.b[1], c->g.b[2], c->g.b[3]}, best_id = 5;
+  int bestb[4] = {c->g.b[0], c->g.b[1], c->g.b[2], c->g.b[3]}, best_id = 5, best_tps = 2;
   long long n4 = c->g.V * 6;
   float4 *v = nullptr, *z = nullptr, *w = nullptr;
   double2* acc = nullptr;
@@ -875,8 +877,9 @@ extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4],
             // slots: CTAs resident at once, for the load model
             double load = dd_load_model(t->g.ND / 2, sms * (sap_smem_bytes(t->g, storage_prec == DD_PREC_FP16 ? P16 : P32,
                                                                           sap_mat_fits_smem(t->g, storage_prec == DD_PREC_FP16 ? P16 : P32)) > 116 * 1024 ? 1 : 2));
-            for (int id = 2; id <= 6; ++id) {
-              dd_sap_params sp = {i_schwarz, id, storage_prec};
+            for (int cand = 0; cand < 10; ++cand) {
+              const int id = 2 + cand / 2, tps = 1 + cand % 2;
+              dd_sap_params sp = {i_schwarz, id, storage_prec, tps};
               if (sap_run(t, v, z, &sp) != DD_OK) break;   // warm-up
               cudaEventRecord(e0, c->st);
               if (sap_run(t, v, z, &sp) != DD_OK) break;
@@ -896,6 +899,7 @@ extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4],
                 best = score;
                 for (int mu = 0; mu < 4; ++mu) bestb[mu] = b[mu];
                 best_id = id;
+                best_tps = tps;
               }
             }
           }
@@ -907,6 +911,7 @@ extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4],
   for (int mu = 0; mu < 4; ++mu) domain_out[mu] = bestb[mu];
   out->i_schwarz = i_schwarz;
   out->i_domain = best_id;
+  out->threads_per_site = best_tps;
   out->storage_prec = storage_prec;
   return cuda_check(c, cudaStreamSynchronize(c->st), "autotune");
 }
@@ -952,6 +957,7 @@ extern "C" dd_status dd_sap_precondition_noalloc(dd_ctx* c, const float* in, flo
   S.faces = (float4*)(base + off); off += up(f_bytes);
   S.err = (int*)(base + off);
   S.mat_in_smem = sap_mat_fits_smem(g, prec);
+  S.threads_per_site = p->threads_per_site ? p->threads_per_site : 2;
   // the error word must start at zero; residual, solution and faces are written before
   // they are read within one call
   TRY(cuda_check(c, cudaMemsetAsync(S.err, 0, sizeof(int), c->st), "clear error word"));

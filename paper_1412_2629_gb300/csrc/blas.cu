@@ -319,8 +319,9 @@ __global__ void __launch_bounds__(BT) gs_dot_kernel(const float4* V, int v0, int
 int launch_gs_dot(const float4* V, int nv, long long n4, const float4* w, double2* partial, const int* gate, int want,
                   cudaStream_t st) {
   int nb = blas_partials_blocks(), n = 0;
-  for (int v0 = 0; v0 < (nv > 0 ? nv : 1); v0 += 16, ++n)
-    gs_dot_kernel<16><<<nb, BT, 0, st>>>(V, v0, nv, n4, w, partial, nv + 1, gate, want);
+  // 8 basis vectors per pass: 16 per pass needs 124 registers and halves the bandwidth
+  for (int v0 = 0; v0 < (nv > 0 ? nv : 1); v0 += 8, ++n)
+    gs_dot_kernel<8><<<nb, BT, 0, st>>>(V, v0, nv, n4, w, partial, nv + 1, gate, want);
   return n;
 }
 

@@ -529,6 +529,352 @@ __global__ void __launch_bounds__(SAP_MAX_THREADS, 1) sap_kernel(SapArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ two threads per site
+// Same algorithm with 2 Hd threads per domain.  In the MR phases thread (h, i) works on
+// even site i and odd site i: h = 0 computes the hops along x and y, h = 1 along z and t,
+// and each keeps chirality half h (spins 2h, 2h+1) of x, rho and r_o.  Because the clover
+// block and its inverse act within one chirality, the only exchange is of the two
+// threads' partial hop sums, half by half, through the shared work buffer that the phase
+// does not otherwise read.  Prologue and epilogue run one thread per site (h = parity).
+
+// Half h of a site vector in a work buffer: units 3h .. 3h+2.
+__device__ inline void ld_hbuf(const float4* buf, int Hd, int i, int h, Half<float>& v) {
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    float4 q = buf[(3 * h + u) * Hd + i];
+    int k = 2 * u;
+    v.c[k / 3][k % 3] = mk(q.x, q.y);
+    v.c[(k + 1) / 3][(k + 1) % 3] = mk(q.z, q.w);
+  }
+}
+__device__ inline void st_hbuf(float4* buf, int Hd, int i, int h, const Half<float>& v) {
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    int k = 2 * u;
+    buf[(3 * h + u) * Hd + i] = make_float4(v.c[k / 3][k % 3].re, v.c[k / 3][k % 3].im, v.c[(k + 1) / 3][(k + 1) % 3].re,
+                                            v.c[(k + 1) / 3][(k + 1) % 3].im);
+  }
+}
+__device__ inline void half_of(const Spinor<float>& s, int h, Half<float>& o) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o.c[a][c] = h ? s.c[2 + a][c] : s.c[a][c];
+}
+
+// Clover block H (36 reals) of site r.
+template <typename MT> struct BlockLoad;
+template <> struct BlockLoad<__half> {
+  template <int H>
+  __device__ static void load(const MatBlock<__half>& M, int r, float m[36]) {
+    // 72 halves in 9 units of 8; block H holds halves 36 H .. 36 H + 35 (units 4 H .. 4 H + 4)
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+      uint4 v = M.cm[(4 * H + u) * M.Vd + r];
+      uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float2 f = h2f(w[e]);
+        const int k = 8 * u + 2 * e - 4 * H;   // position inside the block
+        if (k >= 0 && k < 36) { m[k] = f.x; m[k + 1] = f.y; }
+      }
+    }
+  }
+};
+template <> struct BlockLoad<float> {
+  template <int H>
+  __device__ static void load(const MatBlock<float>& M, int r, float m[36]) {
+#pragma unroll
+    for (int u = 0; u < 9; ++u) {
+      float4 v = M.cm[(9 * H + u) * M.Vd + r];
+      m[4 * u] = v.x; m[4 * u + 1] = v.y; m[4 * u + 2] = v.z; m[4 * u + 3] = v.w;
+    }
+  }
+};
+
+template <typename MT>
+__device__ inline void block_apply(const MatBlock<MT>& M, int r, int h, const Half<float>& x, Half<float>& y) {
+  float m[36];
+  if (h == 0) BlockLoad<MT>::template load<0>(M, r, m);
+  else BlockLoad<MT>::template load<1>(M, r, m);
+  cx<float> v[6], w[6];
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[3 * s + c] = x.c[s][c];
+  clover_block_mul(m, v, w);
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y.c[s][c] = w[3 * s + c];
+}
+
+template <typename MT>
+__device__ inline void hops_half(int h, const Geom& g, const int l[4], int lex, int p, int r_self, const float4* src,
+                                 const MatBlock<MT>& M, Spinor<float>& acc) {
+  if (h == 0) {
+    inside_hop_mu<0>(g, l, lex, p, r_self, src, M, acc);
+    inside_hop_mu<1>(g, l, lex, p, r_self, src, M, acc);
+  } else {
+    inside_hop_mu<2>(g, l, lex, p, r_self, src, M, acc);
+    inside_hop_mu<3>(g, l, lex, p, r_self, src, M, acc);
+  }
+}
+
+// acc: this thread's partial sum over its two directions.  The other thread of the site
+// holds the rest.  Returns the full sum of chirality half h.  buf is scratch here.
+__device__ inline void exchange(const Spinor<float>& acc, int h, float4* buf, int Hd, int i, Half<float>& own) {
+  Half<float> give, mine, got;
+  half_of(acc, 1 - h, give);
+  half_of(acc, h, mine);
+  st_hbuf(buf, Hd, i, 1 - h, give);
+  __syncthreads();
+  ld_hbuf(buf, Hd, i, h, got);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) own.c[a][c] = mine.c[a][c] + got.c[a][c];
+}
+
+// Store half h of the even-site residual; FP16 needs the norm of the whole site, which
+// the two threads share through nrm (2 Hd floats of shared memory).
+template <typename VT> struct EvenHalfStore;
+template <> struct EvenHalfStore<float> {
+  __device__ static void store(const EvenStore<float>& E, float*, long long d, int Hd, int i, int h,
+                               const Half<float>& v) {
+    st_hbuf(E.p + d * 6 * Hd, Hd, i, h, v);
+  }
+};
+template <> struct EvenHalfStore<__half> {
+  __device__ static void store(const EvenStore<__half>& E, float* nrm, long long d, int Hd, int i, int h,
+                               const Half<float>& v) {
+    float m = 0.f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) m = fmaxf(m, fmaxf(fabsf(v.c[a][c].re), fabsf(v.c[a][c].im)));
+    nrm[h * Hd + i] = m;
+    __syncthreads();
+    m = fmaxf(nrm[i], nrm[Hd + i]);
+    float inv = m > 0.f ? 1.f / m : 0.f;
+    if (h == 0) E.norm[d * Hd + i] = m;
+    uint2* q = reinterpret_cast<uint2*>(E.p);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      int k = 2 * t;            // complex pair (k, k+1) of this half
+      int pair = 3 * h + t;     // pair number inside the site's 12 complex numbers
+      int u = pair >> 1, j = pair & 1;
+      q[((d * 3 + u) * Hd + i) * 2 + j] =
+          make_uint2(f2h(v.c[k / 3][k % 3].re * inv, v.c[k / 3][k % 3].im * inv),
+                     f2h(v.c[(k + 1) / 3][(k + 1) % 3].re * inv, v.c[(k + 1) / 3][(k + 1) % 3].im * inv));
+    }
+  }
+};
+
+template <typename MT, typename VT, bool MSMEM>
+__global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArgs a) {
+  const Geom& g = a.g;
+  extern __shared__ float4 smem[];
+  __shared__ uint64_t mbar;
+  __shared__ float4 red[2 * SAP_MAX_THREADS / 32];
+  __shared__ float nrm[2 * SAP_MAX_THREADS];
+  const int tid = threadIdx.x;
+  const int Hd = g.Hd, Vd = g.Vd;
+  const int h = tid >= Hd;          // MR phases: chirality half and hop directions; ends: parity
+  const int i = tid - h * Hd;
+
+  int n[4];
+  {
+    int hx = g.N[0] >> 1;
+    int j = blockIdx.x % hx;
+    int row = blockIdx.x / hx;
+    n[1] = row % g.N[1];
+    n[2] = (row / g.N[1]) % g.N[2];
+    n[3] = row / (g.N[1] * g.N[2]);
+    n[0] = 2 * j + ((a.colour + n[1] + n[2] + n[3]) & 1);
+  }
+  const long long d = n[0] + (long long)g.dstride[1] * n[1] + (long long)g.dstride[2] * n[2] +
+                      (long long)g.dstride[3] * n[3];
+  const size_t lk_elems = (size_t)4 * 9 * Vd;
+  const size_t lk_bytes = (size_t)MatBlock<MT>::link_bytes_per_site * Vd;
+  const size_t cm_bytes = (size_t)MatBlock<MT>::mat_bytes_per_site * Vd;
+  char* sbase = reinterpret_cast<char*>(smem);
+  MatBlock<MT> M;
+  M.Vd = Vd;
+  typedef typename std::remove_const<typename std::remove_pointer<decltype(M.lk)>::type>::type LkT;
+  typedef typename std::remove_const<typename std::remove_pointer<decltype(M.cm)>::type>::type CmT;
+  const LkT* glk = reinterpret_cast<const LkT*>(a.links) + d * lk_elems;
+  const CmT* gcm = reinterpret_cast<const CmT*>(a.smat) + d * (cm_bytes / sizeof(CmT));
+  float4* sE;
+  if (MSMEM) {
+    M.lk = reinterpret_cast<const LkT*>(sbase);
+    M.cm = reinterpret_cast<const CmT*>(sbase + lk_bytes);
+    sE = reinterpret_cast<float4*>(sbase + lk_bytes + cm_bytes);
+    if (tid == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes));
+      bulk_g2s(sbase, glk, (uint32_t)lk_bytes, &mbar);
+      bulk_g2s(sbase + lk_bytes, gcm, (uint32_t)cm_bytes, &mbar);
+    }
+  } else {
+    M.lk = glk;
+    M.cm = gcm;
+    sE = smem;
+  }
+  float4* sO = sE + 6 * Hd;
+
+  int le[4], lo[4];
+  local_coords(g, 0, i, le);
+  local_coords(g, 1, i, lo);
+  const int lex_e = le[0] + g.bstride[1] * le[1] + g.bstride[2] * le[2] + g.bstride[3] * le[3];
+  const int lex_o = lo[0] + g.bstride[1] * lo[1] + g.bstride[2] * lo[2] + g.bstride[3] * lo[3];
+  const int r_e = i, r_o = Hd + i;
+  const int* lsite = h ? lo : le;            // prologue / epilogue: site (parity h, index i)
+  const long long s_site = (d << g.lgVd) + h * Hd + i;
+  const int r_site = h * Hd + i;
+
+  // 1. residual of site (h, i), with the couplings to the other colour
+  EvenStore<VT> rst{reinterpret_cast<decltype(EvenStore<VT>::p)>(a.r_store), a.r_norm};
+  {
+    Spinor<float> r;
+    const SpinorPtr<float> vin{const_cast<float4*>(a.v)};
+    if (a.first) vin.load(g, s_site, r);
+    else if (h == 0) rst.load(d, Hd, i, r);
+    else zero(r);
+    if (MSMEM) {
+      bool ok = mbar_wait(&mbar, 0, 2000000000ull);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(a.err, 1);
+        mbar_wait(&mbar, 0, 2000000000ull);
+        return;
+      }
+    }
+    if (a.use_faces) {
+      Spinor<float> acc;
+      zero(acc);
+      face_hops(g, (int)d, n, lsite, r_site, a.faces, M, acc);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r.c[s][c] = r.c[s][c] + 0.5f * acc.c[s][c];
+    }
+    st_buf(h ? sO : sE, Hd, i, r);
+  }
+  __syncthreads();
+  Half<float> reh, roh, t, own, rho, x;
+  ld_hbuf(sE, Hd, i, h, reh);
+  ld_hbuf(sO, Hd, i, h, roh);
+  __syncthreads();
+
+  // 2. even-odd preparation: t_o = A_oo^{-1} r_o (per chirality), f_e = r_e + 1/2 H_eo t_o
+  block_apply(M, r_o, h, roh, t);
+  st_hbuf(sO, Hd, i, h, t);
+  __syncthreads();
+  Spinor<float> acc;
+  zero(acc);
+  hops_half(h, g, le, lex_e, 0, r_e, sO, M, acc);
+  exchange(acc, h, sE, Hd, i, own);
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      rho.c[s][c] = reh.c[s][c] + 0.5f * own.c[s][c];
+      x.c[s][c] = mk(0.f, 0.f);
+    }
+  st_hbuf(sE, Hd, i, h, rho);
+  __syncthreads();
+
+  // 3. MR on the Schur complement
+  const int nwarp = (2 * Hd + 31) >> 5;
+  for (int it = 0; it < a.i_domain; ++it) {
+    zero(acc);
+    hops_half(h, g, lo, lex_o, 1, r_o, sE, M, acc);
+    exchange(acc, h, sO, Hd, i, own);
+    block_apply(M, r_o, h, own, t);
+    st_hbuf(sO, Hd, i, h, t);
+    __syncthreads();
+    zero(acc);
+    hops_half(h, g, le, lex_e, 0, r_e, sO, M, acc);
+    exchange(acc, h, sE, Hd, i, own);
+    Half<float> pv;
+    block_apply(M, r_e, h, rho, pv);
+    float pr_re = 0.f, pr_im = 0.f, pp = 0.f;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pv.c[s][c] = pv.c[s][c] - 0.25f * own.c[s][c];
+        cx<float> q = cjmul(pv.c[s][c], rho.c[s][c]);
+        pr_re += q.re;
+        pr_im += q.im;
+        pp += pv.c[s][c].re * pv.c[s][c].re + pv.c[s][c].im * pv.c[s][c].im;
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      pr_re += __shfl_xor_sync(0xffffffffu, pr_re, o);
+      pr_im += __shfl_xor_sync(0xffffffffu, pr_im, o);
+      pp += __shfl_xor_sync(0xffffffffu, pp, o);
+    }
+    if ((tid & 31) == 0) red[tid >> 5] = make_float4(pr_re, pr_im, pp, 0.f);
+    __syncthreads();
+    float sr = 0.f, si = 0.f, sp = 0.f;
+    for (int w = 0; w < nwarp; ++w) {
+      float4 q = red[w];
+      sr += q.x;
+      si += q.y;
+      sp += q.z;
+    }
+    cx<float> alpha = sp > 0.f ? mk(sr / sp, si / sp) : mk(0.f, 0.f);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        x.c[s][c] = x.c[s][c] + cmul(alpha, rho.c[s][c]);
+        rho.c[s][c] = rho.c[s][c] - cmul(alpha, pv.c[s][c]);
+      }
+    st_hbuf(sE, Hd, i, h, rho);
+    __syncthreads();
+  }
+
+  // 4. odd reconstruction delta_o = A_oo^{-1} (r_o + 1/2 H_oe x); store the MR residual
+  st_hbuf(sE, Hd, i, h, x);
+  __syncthreads();
+  zero(acc);
+  hops_half(h, g, lo, lex_o, 1, r_o, sE, M, acc);
+  exchange(acc, h, sO, Hd, i, own);
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) own.c[s][c] = roh.c[s][c] + 0.5f * own.c[s][c];
+  block_apply(M, r_o, h, own, t);
+  st_hbuf(sO, Hd, i, h, t);
+  if (!a.last) EvenHalfStore<VT>::store(rst, nrm, d, Hd, i, h, rho);
+  __syncthreads();
+
+  // 5. site (h, i): u += delta, faces of delta
+  Spinor<float> dl;
+  ld_buf(h ? sO : sE, Hd, i, dl);
+  typename VecPtr<VT>::type ust = VecPtr<VT>::make(a.u_store, a.u_norm);
+  Spinor<float> u;
+  if (a.first) {
+    u = dl;
+  } else {
+    ust.load(g, s_site, u);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u.c[s][c] = u.c[s][c] + dl.c[s][c];
+  }
+  if (a.last) {
+    SpinorPtr<float> zo{a.z};
+    zo.store(g, s_site, u);
+  } else {
+    ust.store(g, s_site, u);
+  }
+  if (!(a.last && a.colour == 1)) face_write(g, d, lsite, r_site, a.faces, M, dl);
+}
+
 size_t sap_smem_bytes(const Geom& g, int mat_prec, bool mat_in_smem) {
   size_t vec = (size_t)2 * 6 * g.Hd * 16;
   if (!mat_in_smem) return vec;
@@ -555,15 +901,25 @@ static int smem_optin() {
 int sap_max_domain_sites() { return 2 * SAP_MAX_THREADS; }
 
 template <typename MT, typename VT, bool MSMEM>
-static int launch_one(const SapArgs& a, int grid, cudaStream_t st) {
+static int launch_one(const SapArgs& a, int grid, int pair, cudaStream_t st) {
   size_t smem = sap_smem_bytes(a.g, std::is_same<MT, __half>::value ? P16 : P32, MSMEM);
-  static int configured = 0;
-  if (!configured) {
-    // static shared memory (barrier, reduction slots) is small; the rest may be dynamic
-    cudaFuncSetAttribute(sap_kernel<MT, VT, MSMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin() - 1024);
-    configured = 1;
+  // static shared memory (barrier, reduction slots) is at most a few KB; the rest may be dynamic
+  if (pair) {
+    static int configured = 0;
+    if (!configured) {
+      cudaFuncSetAttribute(sap_kernel_pair<MT, VT, MSMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem_optin() - 4096);
+      configured = 1;
+    }
+    sap_kernel_pair<MT, VT, MSMEM><<<grid, 2 * a.g.Hd, smem, st>>>(a);
+  } else {
+    static int configured = 0;
+    if (!configured) {
+      cudaFuncSetAttribute(sap_kernel<MT, VT, MSMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin() - 1024);
+      configured = 1;
+    }
+    sap_kernel<MT, VT, MSMEM><<<grid, a.g.Hd, smem, st>>>(a);
   }
-  sap_kernel<MT, VT, MSMEM><<<grid, a.g.Hd, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
@@ -589,12 +945,15 @@ int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int 
   a.err = S.err;
   int grid = g.ND / 2;
   bool ms = S.mat_in_smem;
+  int pr = S.threads_per_site == 2;
   if (S.mat_prec == P16) {
-    if (S.vec_prec == P16) return ms ? launch_one<__half, __half, true>(a, grid, st) : launch_one<__half, __half, false>(a, grid, st);
-    return ms ? launch_one<__half, float, true>(a, grid, st) : launch_one<__half, float, false>(a, grid, st);
+    if (S.vec_prec == P16)
+      return ms ? launch_one<__half, __half, true>(a, grid, pr, st) : launch_one<__half, __half, false>(a, grid, pr, st);
+    return ms ? launch_one<__half, float, true>(a, grid, pr, st) : launch_one<__half, float, false>(a, grid, pr, st);
   }
-  if (S.vec_prec == P16) return ms ? launch_one<float, __half, true>(a, grid, st) : launch_one<float, __half, false>(a, grid, st);
-  return ms ? launch_one<float, float, true>(a, grid, st) : launch_one<float, float, false>(a, grid, st);
+  if (S.vec_prec == P16)
+    return ms ? launch_one<float, __half, true>(a, grid, pr, st) : launch_one<float, __half, false>(a, grid, pr, st);
+  return ms ? launch_one<float, float, true>(a, grid, pr, st) : launch_one<float, float, false>(a, grid, pr, st);
 }
 
 }  // namespace dd

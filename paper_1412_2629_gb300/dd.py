@@ -23,7 +23,8 @@ DD_LAYOUT_CANONICAL, DD_LAYOUT_INTERNAL = 0, 1
 
 
 class dd_sap_params(C.Structure):
-    _fields_ = [("i_schwarz", C.c_int), ("i_domain", C.c_int), ("storage_prec", C.c_int)]
+    _fields_ = [("i_schwarz", C.c_int), ("i_domain", C.c_int), ("storage_prec", C.c_int),
+                ("threads_per_site", C.c_int)]
 
 
 class dd_solve_params(C.Structure):
@@ -134,19 +135,21 @@ class Context:
     def dd_apply_D(self, inp, out, prec, layout=DD_LAYOUT_CANONICAL):
         return self._check(lib().dd_apply_D(self._h, _ptr(inp), _ptr(out), prec, layout))
 
-    def dd_sap_precondition(self, inp, out, i_schwarz, i_domain, storage_prec, layout=DD_LAYOUT_CANONICAL):
-        p = dd_sap_params(i_schwarz, i_domain, storage_prec)
+    def dd_sap_precondition(self, inp, out, i_schwarz, i_domain, storage_prec, layout=DD_LAYOUT_CANONICAL,
+                            threads_per_site=0):
+        p = dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site)
         return self._check(lib().dd_sap_precondition(self._h, _ptr(inp), _ptr(out), C.byref(p), layout))
 
-    def dd_sap_precondition_noalloc(self, inp, out, i_schwarz, i_domain, storage_prec, check=True):
+    def dd_sap_precondition_noalloc(self, inp, out, i_schwarz, i_domain, storage_prec, check=True,
+                                    threads_per_site=0):
         """Internal-layout FP32 in/out; no device allocation (fixed scratch array)."""
-        p = dd_sap_params(i_schwarz, i_domain, storage_prec)
+        p = dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site)
         s = lib().dd_sap_precondition_noalloc(self._h, _ptr(inp), _ptr(out), C.byref(p))
         return self._check(s) if check else s
 
     def dd_solve(self, f, x, nrhs=1, where=DD_HOST, tol=1e-10, m=16, k=0, max_iter=1000, i_schwarz=16,
-                 i_domain=4, storage_prec=DD_PREC_FP16, check=True):
-        p = dd_solve_params(tol, m, k, max_iter, dd_sap_params(i_schwarz, i_domain, storage_prec))
+                 i_domain=4, storage_prec=DD_PREC_FP16, check=True, threads_per_site=0):
+        p = dd_solve_params(tol, m, k, max_iter, dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site))
         info = dd_solve_info()
         s = lib().dd_solve(self._h, _ptr(f), _ptr(x), nrhs, where, C.byref(p), C.byref(info))
         if check:
@@ -169,7 +172,7 @@ class Context:
         dom = (C.c_int * 4)()
         p = dd_sap_params(i_schwarz, 0, storage_prec)
         self._check(lib().dd_autotune(self._h, storage_prec, dom, C.byref(p)))
-        return tuple(dom), (p.i_schwarz, p.i_domain, p.storage_prec)
+        return tuple(dom), (p.i_schwarz, p.i_domain, p.storage_prec, p.threads_per_site)
 
 
 def dd_load_model(n_domains_per_colour, slots):

@@ -17,10 +17,10 @@ from gpu_helpers import ctx_for, dev, gauge, host, rel
 pytestmark = pytest.mark.gpu
 
 
-def sap_gpu(c, f, i_s, i_d, prec):
+def sap_gpu(c, f, i_s, i_d, prec, tps=0):
     src = dev(f, torch.float32)
     out = torch.empty_like(src)
-    c.dd_sap_precondition(src, out, i_s, i_d, prec, dd.DD_LAYOUT_CANONICAL)
+    c.dd_sap_precondition(src, out, i_s, i_d, prec, dd.DD_LAYOUT_CANONICAL, threads_per_site=tps)
     return host(out)
 
 
@@ -48,10 +48,11 @@ def test_sap_matches_oracle(case):
             r = f - W.apply_A(U, u, kappa, csw, F, bc_t=bc)
             u = u + solver_solve(solver, r, colour, i_d, U, bc)
     c = ctx_for(dims, dom, U, kappa, csw, anti)
-    got32 = sap_gpu(c, f, i_s, i_d, dd.DD_PREC_FP32)
-    assert rel(got32, u) <= 1e-5
-    got16 = sap_gpu(c, f, i_s, i_d, dd.DD_PREC_FP16)
-    assert rel(got16, u) <= 5e-3
+    for tps in (1, 2):   # one thread per site, or hop directions and chirality split over two
+        got32 = sap_gpu(c, f, i_s, i_d, dd.DD_PREC_FP32, tps)
+        assert rel(got32, u) <= 1e-5
+        got16 = sap_gpu(c, f, i_s, i_d, dd.DD_PREC_FP16, tps)
+        assert rel(got16, u) <= 5e-3
 
 
 def solver_solve(solver, r, colour, i_d, U, bc):
