@@ -135,6 +135,16 @@ def read_profile(name, sha):
         return None
 
 
+def max_over_ranks(vals, device="cpu"):
+    """Element-wise max of per-rank timings over all ranks (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
 # ------------------------------------------------------------------ oracle arm
 def oracle_sample(w, U_host, f):
     """Time one FP64 oracle application of A on the full lattice (field strength
@@ -293,10 +303,7 @@ def main():
         ms_e2e, infos_e2e, _ = timed(dd.DD_PREC_FP16, dd.DD_HOST, args.steps, 1, "timed_e2e")
         ms_fp32, infos32, _ = timed(dd.DD_PREC_FP32, dd.DD_DEVICE, max(2, args.steps // 2), 1, "timed_fp32")
 
-    if world > 1:
-        t = torch.tensor([ms_mixed, ms_e2e, ms_fp32], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_mixed, ms_e2e, ms_fp32 = [float(v) for v in t]
+    ms_mixed, ms_e2e, ms_fp32 = max_over_ranks([ms_mixed, ms_e2e, ms_fp32], "cuda")
 
     V = int(np.prod(w.dims))
     mean = lambda key, L: statistics.mean(i[key] for i in L)

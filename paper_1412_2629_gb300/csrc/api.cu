@@ -64,6 +64,10 @@ struct dd_ctx {
   std::string err;
   long long launches = 0;
   bool trace = false;   // DD_TRACE=1 in the environment: one line per solver step on stderr
+  // DD_INJECT_WAIT_TIMEOUT=1 at dd_create: the Schwarz kernel's bounded wait for its staged
+  // data is made to run out (it expects 16 bytes nobody sends, limit 50 ms), to exercise
+  // the DD_ERR_TIMEOUT path without any fault
+  bool inject_wait_timeout = false;
   // gauge
   double* Ucanon = nullptr;
   double2* U64 = nullptr;
@@ -191,6 +195,8 @@ extern "C" dd_status dd_create(dd_ctx** out, const int dims[4], const int domain
   c->st = (cudaStream_t)stream;
   const char* tr = getenv("DD_TRACE");
   c->trace = tr && tr[0] && tr[0] != '0';
+  const char* inj = getenv("DD_INJECT_WAIT_TIMEOUT");
+  c->inject_wait_timeout = inj && inj[0] && inj[0] != '0';
   if (dalloc(c, &c->dstatus, 64) != DD_OK || dalloc(c, &c->sap_err, 64) != DD_OK) {
     for (void* p : c->allocs) cudaFree(p);
     delete c;
@@ -364,6 +370,7 @@ static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_par
   S.err = c->sap_err;
   S.mat_in_smem = sap_mat_fits_smem(c->g, prec);
   S.threads_per_site = p->threads_per_site ? p->threads_per_site : 2;
+  S.inject_wait_timeout = c->inject_wait_timeout;
   for (int s = 0; s < p->i_schwarz; ++s)
     for (int colour = 0; colour < 2; ++colour) {
       int first = s == 0, use_faces = !(s == 0 && colour == 0), last = s == p->i_schwarz - 1;

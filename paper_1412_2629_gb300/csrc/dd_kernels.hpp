@@ -54,6 +54,7 @@ struct SapState {
   int* err;            // set to 1 when a bounded device wait runs out
   bool mat_in_smem;    // stage links and Schwarz matrices in shared memory
   int threads_per_site = 2;   // 1: one thread per site; 2: hop directions and chirality split
+  bool inject_wait_timeout = false;   // test hook: make the bounded wait run out (no fault)
 };
 // One half-sweep: all domains of `colour`.  first: the residual is the input v (both
 // parities) and u = 0; use_faces: subtract the couplings to the other colour from the

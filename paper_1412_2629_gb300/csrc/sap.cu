@@ -311,6 +311,10 @@ struct SapArgs {
   const float4* v;
   float4* z;
   int* err;
+  // Bound of the wait for the staged matrices, and extra bytes the barrier is told to
+  // expect: 0 normally; a test sets it so the wait runs out and the error path is taken.
+  unsigned long long wait_ns;
+  unsigned extra_tx;
 };
 
 constexpr int SAP_MAX_THREADS = 256;
@@ -356,7 +360,7 @@ __global__ void __launch_bounds__(SAP_MAX_THREADS, 1) sap_kernel(SapArgs a) {
     if (tid == 0) mbar_init(&mbar, 1);
     __syncthreads();
     if (tid == 0) {
-      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes));
+      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes) + a.extra_tx);
       bulk_g2s(sbase, glk, (uint32_t)lk_bytes, &mbar);
       bulk_g2s(sbase + lk_bytes, gcm, (uint32_t)cm_bytes, &mbar);
     }
@@ -387,11 +391,11 @@ __global__ void __launch_bounds__(SAP_MAX_THREADS, 1) sap_kernel(SapArgs a) {
     zero(ro);
   }
   if (MSMEM) {
-    bool ok = mbar_wait(&mbar, 0, 2000000000ull);
+    bool ok = mbar_wait(&mbar, 0, a.wait_ns);
     if (__syncthreads_or(!ok)) {
       // the copy did not complete in time: flag it, give it one more bounded wait, leave
       if (tid == 0) atomicExch(a.err, 1);
-      mbar_wait(&mbar, 0, 2000000000ull);
+      mbar_wait(&mbar, 0, a.wait_ns);
       return;
     }
   }
@@ -713,7 +717,7 @@ __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArg
     if (tid == 0) mbar_init(&mbar, 1);
     __syncthreads();
     if (tid == 0) {
-      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes));
+      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes) + a.extra_tx);
       bulk_g2s(sbase, glk, (uint32_t)lk_bytes, &mbar);
       bulk_g2s(sbase + lk_bytes, gcm, (uint32_t)cm_bytes, &mbar);
     }
@@ -743,10 +747,10 @@ __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArg
     else if (h == 0) rst.load(d, Hd, i, r);
     else zero(r);
     if (MSMEM) {
-      bool ok = mbar_wait(&mbar, 0, 2000000000ull);
+      bool ok = mbar_wait(&mbar, 0, a.wait_ns);
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicExch(a.err, 1);
-        mbar_wait(&mbar, 0, 2000000000ull);
+        mbar_wait(&mbar, 0, a.wait_ns);
         return;
       }
     }
@@ -943,6 +947,8 @@ int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int 
   a.v = v;
   a.z = z;
   a.err = S.err;
+  a.extra_tx = S.inject_wait_timeout ? 16u : 0u;
+  a.wait_ns = S.inject_wait_timeout ? 50000000ull : 2000000000ull;
   int grid = g.ND / 2;
   bool ms = S.mat_in_smem;
   int pr = S.threads_per_site == 2;
