@@ -676,7 +676,7 @@ template <> struct EvenHalfStore<__half> {
 };
 
 template <typename MT, typename VT, bool MSMEM>
-__global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArgs a) {
+__global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair_unrolled(SapArgs a) {
   const Geom& g = a.g;
   extern __shared__ float4 smem[];
   __shared__ uint64_t mbar;
@@ -877,6 +877,442 @@ __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArg
     ust.store(g, s_site, u);
   }
   if (!(a.last && a.colour == 1)) face_write(g, d, lsite, r_site, a.faces, M, dl);
+}
+
+// ------------------------------------------------------------------ compact hop code
+// The domain solve runs ~2 + 2 I_domain hop phases per visit; written out for every
+// direction and phase the kernel outgrows the instruction cache.  Here a hop has one
+// body: the direction is a loop variable and only the few additions of the spin
+// projection and reconstruction are selected per direction (warp-uniform switches).
+__device__ inline void project_rt(int mu, int dir, const Spinor<float>& p, Half<float>& h) {
+  // forward hop uses (1 - gamma_mu), backward (1 + gamma_mu)
+  switch (2 * mu + (dir < 0)) {
+    case 0: project<0, -1>(p, h); break;
+    case 1: project<0, +1>(p, h); break;
+    case 2: project<1, -1>(p, h); break;
+    case 3: project<1, +1>(p, h); break;
+    case 4: project<2, -1>(p, h); break;
+    case 5: project<2, +1>(p, h); break;
+    case 6: project<3, -1>(p, h); break;
+    default: project<3, +1>(p, h); break;
+  }
+}
+__device__ inline void recon_rt(int mu, int dir, Spinor<float>& acc, const Half<float>& h) {
+  switch (2 * mu + (dir < 0)) {
+    case 0: accum_recon<0, -1>(acc, h); break;
+    case 1: accum_recon<0, +1>(acc, h); break;
+    case 2: accum_recon<1, -1>(acc, h); break;
+    case 3: accum_recon<1, +1>(acc, h); break;
+    case 4: accum_recon<2, -1>(acc, h); break;
+    case 5: accum_recon<2, +1>(acc, h); break;
+    case 6: accum_recon<3, -1>(acc, h); break;
+    default: accum_recon<3, +1>(acc, h); break;
+  }
+}
+
+// U_mu(site r) for dir > 0, U_mu(site r)^dag for dir < 0.
+template <typename MT>
+__device__ inline void link_rt(const MatBlock<MT>& M, int mu, int r, int dir, Link<float>& U) {
+  Link<float> L;
+  M.link(mu, r, L);
+  if (dir > 0) {
+    U = L;
+  } else {
+#pragma unroll
+    for (int a2 = 0; a2 < 3; ++a2)
+#pragma unroll
+      for (int b2 = 0; b2 < 3; ++b2) U.e[a2][b2] = mk(L.e[b2][a2].re, -L.e[b2][a2].im);
+  }
+}
+
+// Masks of the directions whose forward / backward neighbour is inside the domain.
+__device__ inline void inside_masks(const Geom& g, const int l[4], unsigned& fwd, unsigned& bwd) {
+  fwd = bwd = 0;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    fwd |= (l[mu] + 1 < g.b[mu] ? 1u : 0u) << mu;
+    bwd |= (l[mu] > 0 ? 1u : 0u) << mu;
+  }
+}
+
+// acc += hops inside the domain along mu = mu0, mu0 + 1 (both senses), no -1/2 factor.
+template <typename MT>
+__device__ inline void hops_rt(const Geom& g, int mu0, unsigned fwd, unsigned bwd, int lex, int p, int r_self,
+                               const float4* src, const MatBlock<MT>& M, Spinor<float>& acc) {
+#pragma unroll 1
+  for (int k = 0; k < 4; ++k) {
+    const int mu = mu0 + (k >> 1);
+    const int dir = (k & 1) ? -1 : 1;
+    if (!(((dir > 0 ? fwd : bwd) >> mu) & 1u)) continue;
+    const int j = (lex + dir * g.bstride[mu]) >> 1;
+    Spinor<float> psi;
+    ld_buf(src, g.Hd, j, psi);
+    Half<float> h, uh;
+    project_rt(mu, dir, psi, h);
+    Link<float> U;
+    link_rt(M, mu, dir > 0 ? r_self : (1 - p) * g.Hd + j, dir, U);
+    su3_mul(U, h, uh);
+    recon_rt(mu, dir, acc, uh);
+  }
+}
+
+// acc += couplings to the neighbouring domains from their face buffers (see face_hop_mu).
+template <typename MT>
+__device__ inline void face_hops_rt(const Geom& g, int d, const int n[4], const int l[4], unsigned fwd, unsigned bwd,
+                                    int r_self, const float4* faces, const MatBlock<MT>& M, Spinor<float>& acc) {
+  int fidx[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) fidx[mu] = face_index(g, l, mu);
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) {
+    const int mu = k >> 1;
+    const int dir = (k & 1) ? -1 : 1;
+    if ((((dir > 0 ? fwd : bwd) >> mu) & 1u)) continue;   // neighbour inside: not a face hop
+    long long dn;
+    int fi;
+    switch (mu) {   // register arrays are only indexed with constants
+      case 0: dn = neighbour_domain(g, d, n, 0, dir); fi = fidx[0]; break;
+      case 1: dn = neighbour_domain(g, d, n, 1, dir); fi = fidx[1]; break;
+      case 2: dn = neighbour_domain(g, d, n, 2, dir); fi = fidx[2]; break;
+      default: dn = neighbour_domain(g, d, n, 3, dir); fi = fidx[3]; break;
+    }
+    const float4* q = faces + (dn * g.face_block + g.face_off[2 * mu + (dir > 0 ? 0 : 1)] + fi) * 3;
+    Half<float> h, uh;
+    ld_half(q, h);
+    if (dir > 0) {
+      Link<float> U;
+      M.link(mu, r_self, U);
+      su3_mul(U, h, uh);
+    } else {
+      uh = h;
+    }
+    recon_rt(mu, dir, acc, uh);
+  }
+}
+
+// Projected half-spinors of dl on this site's faces (see face_write_mu).
+template <typename MT>
+__device__ inline void face_write_rt(const Geom& g, long long d, const int l[4], unsigned fwd, unsigned bwd,
+                                     int r_self, float4* faces, const MatBlock<MT>& M, const Spinor<float>& dl) {
+  int fidx[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) fidx[mu] = face_index(g, l, mu);
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) {
+    const int mu = k >> 1;
+    const int side = k & 1;          // 0: -mu face (l_mu = 0), 1: +mu face (l_mu = b_mu - 1)
+    if (side == 0 ? ((bwd >> mu) & 1u) : ((fwd >> mu) & 1u)) continue;
+    int fi;
+    switch (mu) {
+      case 0: fi = fidx[0]; break;
+      case 1: fi = fidx[1]; break;
+      case 2: fi = fidx[2]; break;
+      default: fi = fidx[3]; break;
+    }
+    Half<float> h, uh;
+    // -mu face: P^-_mu dl for the neighbour's forward hop; +mu face: U^dag P^+_mu dl
+    project_rt(mu, side == 0 ? 1 : -1, dl, h);
+    if (side == 1) {
+      Link<float> U;
+      link_rt(M, mu, r_self, -1, U);
+      su3_mul(U, h, uh);
+    } else {
+      uh = h;
+    }
+    st_half(faces + (d * g.face_block + g.face_off[2 * mu + side] + fi) * 3, uh);
+  }
+}
+
+// Clover block h of site r applied to x (block index at run time).
+template <typename MT> struct BlockLoadRt;
+template <> struct BlockLoadRt<__half> {
+  __device__ static void load(const MatBlock<__half>& M, int r, int h, float m[36]) {
+    float t[40];
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+      uint4 v = M.cm[(4 * h + u) * M.Vd + r];
+      uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { float2 f = h2f(w[e]); t[8 * u + 2 * e] = f.x; t[8 * u + 2 * e + 1] = f.y; }
+    }
+#pragma unroll
+    for (int k = 0; k < 36; ++k) m[k] = h ? t[k + 4] : t[k];
+  }
+};
+template <> struct BlockLoadRt<float> {
+  __device__ static void load(const MatBlock<float>& M, int r, int h, float m[36]) {
+#pragma unroll
+    for (int u = 0; u < 9; ++u) {
+      float4 v = M.cm[(9 * h + u) * M.Vd + r];
+      m[4 * u] = v.x; m[4 * u + 1] = v.y; m[4 * u + 2] = v.z; m[4 * u + 3] = v.w;
+    }
+  }
+};
+template <typename MT>
+__device__ inline void block_apply_rt(const MatBlock<MT>& M, int r, int h, const Half<float>& x, Half<float>& y) {
+  float m[36];
+  BlockLoadRt<MT>::load(M, r, h, m);
+  cx<float> v[6], w[6];
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[3 * s + c] = x.c[s][c];
+  clover_block_mul(m, v, w);
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y.c[s][c] = w[3 * s + c];
+}
+
+// Hops of one direction with the inside-the-domain test taken from bit masks, so the
+// phase loop carries four small integers instead of two coordinate arrays.
+template <int MU, typename MT>
+__device__ inline void hop_mask_mu(const Geom& g, unsigned fwd, unsigned bwd, int lex, int p, int r_self,
+                                   const float4* src, const MatBlock<MT>& M, Spinor<float>& acc) {
+  Spinor<float> psi;
+  Half<float> h, uh;
+  Link<float> L;
+  if ((fwd >> MU) & 1u) {
+    int j = (lex + g.bstride[MU]) >> 1;
+    ld_buf(src, g.Hd, j, psi);
+    project<MU, -1>(psi, h);
+    M.link(MU, r_self, L);
+    su3_mul(L, h, uh);
+    accum_recon<MU, -1>(acc, uh);
+  }
+  if ((bwd >> MU) & 1u) {
+    int j = (lex - g.bstride[MU]) >> 1;
+    ld_buf(src, g.Hd, j, psi);
+    project<MU, +1>(psi, h);
+    M.link(MU, (1 - p) * g.Hd + j, L);
+    su3_dag_mul(L, h, uh);
+    accum_recon<MU, +1>(acc, uh);
+  }
+}
+
+template <typename MT>
+__device__ inline void hops_half_mask(int h, const Geom& g, unsigned fwd, unsigned bwd, int lex, int p, int r_self,
+                                      const float4* src, const MatBlock<MT>& M, Spinor<float>& acc) {
+  if (h == 0) {
+    hop_mask_mu<0>(g, fwd, bwd, lex, p, r_self, src, M, acc);
+    hop_mask_mu<1>(g, fwd, bwd, lex, p, r_self, src, M, acc);
+  } else {
+    hop_mask_mu<2>(g, fwd, bwd, lex, p, r_self, src, M, acc);
+    hop_mask_mu<3>(g, fwd, bwd, lex, p, r_self, src, M, acc);
+  }
+}
+
+// Two threads per site, compact code.  The MR iteration is a loop over hop phases:
+//   phase 0:          even sites, src = t_o      -> rho = r_e + 1/2 H t_o, x = 0
+//   phase 2k+1:       odd sites,  src = rho      -> t = A_oo^{-1} H rho
+//   phase 2k+2:       even sites, src = t        -> p = A_ee rho - 1/4 H t, MR step
+//   phase 2 I_d + 1:  odd sites,  src = x        -> delta_o = A_oo^{-1} (r_o + 1/2 H x)
+template <typename MT, typename VT, bool MSMEM>
+__global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArgs a) {
+  const Geom& g = a.g;
+  extern __shared__ float4 smem[];
+  __shared__ uint64_t mbar;
+  __shared__ float4 red[2 * SAP_MAX_THREADS / 32];
+  __shared__ float nrm[2 * SAP_MAX_THREADS];
+  const int tid = threadIdx.x;
+  const int Hd = g.Hd, Vd = g.Vd;
+  const int h = tid >= Hd;          // MR phases: chirality half and hop directions; ends: parity
+  const int i = tid - h * Hd;
+
+  int n[4];
+  {
+    int hx = g.N[0] >> 1;
+    int j = blockIdx.x % hx;
+    int row = blockIdx.x / hx;
+    n[1] = row % g.N[1];
+    n[2] = (row / g.N[1]) % g.N[2];
+    n[3] = row / (g.N[1] * g.N[2]);
+    n[0] = 2 * j + ((a.colour + n[1] + n[2] + n[3]) & 1);
+  }
+  const long long d = n[0] + (long long)g.dstride[1] * n[1] + (long long)g.dstride[2] * n[2] +
+                      (long long)g.dstride[3] * n[3];
+  const size_t lk_elems = (size_t)4 * 9 * Vd;
+  const size_t lk_bytes = (size_t)MatBlock<MT>::link_bytes_per_site * Vd;
+  const size_t cm_bytes = (size_t)MatBlock<MT>::mat_bytes_per_site * Vd;
+  char* sbase = reinterpret_cast<char*>(smem);
+  MatBlock<MT> M;
+  M.Vd = Vd;
+  typedef typename std::remove_const<typename std::remove_pointer<decltype(M.lk)>::type>::type LkT;
+  typedef typename std::remove_const<typename std::remove_pointer<decltype(M.cm)>::type>::type CmT;
+  const LkT* glk = reinterpret_cast<const LkT*>(a.links) + d * lk_elems;
+  const CmT* gcm = reinterpret_cast<const CmT*>(a.smat) + d * (cm_bytes / sizeof(CmT));
+  float4* sE;
+  if (MSMEM) {
+    M.lk = reinterpret_cast<const LkT*>(sbase);
+    M.cm = reinterpret_cast<const CmT*>(sbase + lk_bytes);
+    sE = reinterpret_cast<float4*>(sbase + lk_bytes + cm_bytes);
+    if (tid == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes) + a.extra_tx);
+      bulk_g2s(sbase, glk, (uint32_t)lk_bytes, &mbar);
+      bulk_g2s(sbase + lk_bytes, gcm, (uint32_t)cm_bytes, &mbar);
+    }
+  } else {
+    M.lk = glk;
+    M.cm = gcm;
+    sE = smem;
+  }
+  float4* sO = sE + 6 * Hd;
+
+  int le[4], lo[4];
+  local_coords(g, 0, i, le);
+  local_coords(g, 1, i, lo);
+  const int lex_e = le[0] + g.bstride[1] * le[1] + g.bstride[2] * le[2] + g.bstride[3] * le[3];
+  const int lex_o = lo[0] + g.bstride[1] * lo[1] + g.bstride[2] * lo[2] + g.bstride[3] * lo[3];
+  unsigned fe, be, fo, bo;
+  inside_masks(g, le, fe, be);
+  inside_masks(g, lo, fo, bo);
+  const int r_e = i, r_o = Hd + i;
+  const long long s_site = (d << g.lgVd) + h * Hd + i;
+  const int r_site = h * Hd + i;
+  const unsigned fs = h ? fo : fe, bs = h ? bo : be;
+
+  // 1. residual of site (parity h, index i), with the couplings to the other colour
+  EvenStore<VT> rst{reinterpret_cast<decltype(EvenStore<VT>::p)>(a.r_store), a.r_norm};
+  {
+    Spinor<float> r;
+    const SpinorPtr<float> vin{const_cast<float4*>(a.v)};
+    if (a.first) vin.load(g, s_site, r);
+    else if (h == 0) rst.load(d, Hd, i, r);
+    else zero(r);
+    if (MSMEM) {
+      bool ok = mbar_wait(&mbar, 0, a.wait_ns);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(a.err, 1);
+        mbar_wait(&mbar, 0, a.wait_ns);
+        return;
+      }
+    }
+    if (a.use_faces) {
+      Spinor<float> acc;
+      zero(acc);
+      if (h) face_hops_rt(g, (int)d, n, lo, fs, bs, r_site, a.faces, M, acc);
+      else face_hops_rt(g, (int)d, n, le, fs, bs, r_site, a.faces, M, acc);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r.c[s][c] = r.c[s][c] + 0.5f * acc.c[s][c];
+    }
+    st_buf(h ? sO : sE, Hd, i, r);
+  }
+  __syncthreads();
+  Half<float> roh, t, own, rho, x;
+  ld_hbuf(sE, Hd, i, h, rho);              // rho starts as r_e; phase 0 adds 1/2 H t_o
+  ld_hbuf(sO, Hd, i, h, roh);
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x.c[s][c] = mk(0.f, 0.f);
+  block_apply_rt(M, r_o, h, roh, t);       // t_o = A_oo^{-1} r_o
+  st_hbuf(sO, Hd, i, h, t);
+  __syncthreads();
+
+  // 2.-4. preparation, MR steps and odd reconstruction as one loop over hop phases
+  const int nph = 2 * a.i_domain + 2;
+  const int nwarp = (2 * Hd + 31) >> 5;
+#pragma unroll 1
+  for (int ph = 0; ph < nph; ++ph) {
+    const int odd = ph & 1;
+    Spinor<float> acc;
+    zero(acc);
+    // the hop code is specialised per direction pair (h) but appears once in the loop
+    hops_half_mask(h, g, odd ? fo : fe, odd ? bo : be, odd ? lex_o : lex_e, odd, odd ? r_o : r_e, odd ? sE : sO, M,
+                   acc);
+    exchange(acc, h, odd ? sO : sE, Hd, i, own);
+    if (ph == 0) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rho.c[s][c] = rho.c[s][c] + 0.5f * own.c[s][c];
+      st_hbuf(sE, Hd, i, h, rho);
+    } else {
+      // one clover-block application per phase: A_oo^{-1} on odd phases, A_ee rho on even
+      Half<float> bin;
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          bin.c[s][c] = !odd ? rho.c[s][c] : (ph == nph - 1 ? roh.c[s][c] + 0.5f * own.c[s][c] : own.c[s][c]);
+      block_apply(M, odd ? r_o : r_e, h, bin, t);
+      if (odd) st_hbuf(sO, Hd, i, h, t);
+    }
+    if (ph != 0 && !odd) {
+      Half<float> pv = t;
+      float pr_re = 0.f, pr_im = 0.f, pp = 0.f;
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          pv.c[s][c] = pv.c[s][c] - 0.25f * own.c[s][c];
+          cx<float> q = cjmul(pv.c[s][c], rho.c[s][c]);
+          pr_re += q.re;
+          pr_im += q.im;
+          pp += pv.c[s][c].re * pv.c[s][c].re + pv.c[s][c].im * pv.c[s][c].im;
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        pr_re += __shfl_xor_sync(0xffffffffu, pr_re, o);
+        pr_im += __shfl_xor_sync(0xffffffffu, pr_im, o);
+        pp += __shfl_xor_sync(0xffffffffu, pp, o);
+      }
+      if ((tid & 31) == 0) red[tid >> 5] = make_float4(pr_re, pr_im, pp, 0.f);
+      __syncthreads();
+      float sr = 0.f, si = 0.f, sp = 0.f;
+      for (int w = 0; w < nwarp; ++w) {
+        float4 q = red[w];
+        sr += q.x;
+        si += q.y;
+        sp += q.z;
+      }
+      cx<float> alpha = sp > 0.f ? mk(sr / sp, si / sp) : mk(0.f, 0.f);
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          x.c[s][c] = x.c[s][c] + cmul(alpha, rho.c[s][c]);
+          rho.c[s][c] = rho.c[s][c] - cmul(alpha, pv.c[s][c]);
+        }
+      // the last MR step hands x to the reconstruction phase instead of rho
+      st_hbuf(sE, Hd, i, h, ph == nph - 2 ? x : rho);
+    }
+    __syncthreads();
+  }
+  if (!a.last) {
+    EvenHalfStore<VT>::store(rst, nrm, d, Hd, i, h, rho);
+    __syncthreads();
+  }
+
+  // 5. site (h, i): u += delta, faces of delta
+  Spinor<float> dl;
+  ld_buf(h ? sO : sE, Hd, i, dl);
+  typename VecPtr<VT>::type ust = VecPtr<VT>::make(a.u_store, a.u_norm);
+  Spinor<float> u;
+  if (a.first) {
+    u = dl;
+  } else {
+    ust.load(g, s_site, u);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u.c[s][c] = u.c[s][c] + dl.c[s][c];
+  }
+  if (a.last) {
+    SpinorPtr<float> zo{a.z};
+    zo.store(g, s_site, u);
+  } else {
+    ust.store(g, s_site, u);
+  }
+  if (!(a.last && a.colour == 1)) {
+    if (h) face_write_rt(g, d, lo, fs, bs, r_site, a.faces, M, dl);
+    else face_write_rt(g, d, le, fs, bs, r_site, a.faces, M, dl);
+  }
 }
 
 size_t sap_smem_bytes(const Geom& g, int mat_prec, bool mat_in_smem) {
