@@ -16,6 +16,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <array>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -33,8 +35,20 @@ struct SapBuffers {
   float4* faces = nullptr;
 };
 
+// A launch sequence of the outer solver captured as a CUDA graph: key = (part, basis
+// buffer, step j, I_Schwarz, I_domain, storage precision, threads per site, m).
+typedef std::array<int, 8> GraphKey;
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;     // kernels per replay
+  int seen = 0;
+};
+
 struct SolverBuffers {
   int m = 0;                 // capacity (basis size)
+  cudaStream_t stream = nullptr;       // private stream of dd_solve (capturable)
+  cudaEvent_t ev_in = nullptr;
+  std::map<GraphKey, GraphEntry> graphs;
   float4* V[2] = {nullptr, nullptr};   // (m+1) vectors each, double-buffered for restarts
   float4* Z[2] = {nullptr, nullptr};   // m vectors each
   float4* w = nullptr;
@@ -68,6 +82,7 @@ struct dd_ctx {
   // data is made to run out (it expects 16 bytes nobody sends, limit 50 ms), to exercise
   // the DD_ERR_TIMEOUT path without any fault
   bool inject_wait_timeout = false;
+  bool use_graphs = true;   // DD_NO_GRAPHS=1: launch the outer solver's kernels directly
   // gauge
   double* Ucanon = nullptr;
   double2* U64 = nullptr;
@@ -197,6 +212,8 @@ extern "C" dd_status dd_create(dd_ctx** out, const int dims[4], const int domain
   c->trace = tr && tr[0] && tr[0] != '0';
   const char* inj = getenv("DD_INJECT_WAIT_TIMEOUT");
   c->inject_wait_timeout = inj && inj[0] && inj[0] != '0';
+  const char* ng = getenv("DD_NO_GRAPHS");
+  c->use_graphs = !(ng && ng[0] && ng[0] != '0');
   if (dalloc(c, &c->dstatus, 64) != DD_OK || dalloc(c, &c->sap_err, 64) != DD_OK) {
     for (void* p : c->allocs) cudaFree(p);
     delete c;
@@ -501,6 +518,10 @@ static void release_solver(dd_ctx* c) {
                   (void*)s.h_cn, (void*)s.h_theta})
     if (p) cudaFreeHost(p);
   delete s.h_dw;
+  for (auto& kv : s.graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  if (s.stream) cudaStreamDestroy(s.stream);
+  if (s.ev_in) cudaEventDestroy(s.ev_in);
   s = SolverBuffers();
 }
 
@@ -541,6 +562,9 @@ static dd_status ensure_solver(dd_ctx* c, int m) {
   for (zd** p : {&s.h_c0, &s.h_y, &s.h_cn, &s.h_theta})
     if (cudaMallocHost(p, (m + 2) * sizeof(zd)) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned deflation buffers");
   s.h_dw = new DeflateWork();
+  if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s.ev_in, cudaEventDisableTiming) != cudaSuccess)
+    return fail(c, DD_ERR_CUDA, "solver stream");
   s.m = m;
   return DD_OK;
 }
@@ -550,6 +574,46 @@ struct Timer {
   Timer() { cudaEventCreate(&a); cudaEventCreate(&b); }
   ~Timer() { cudaEventDestroy(a); cudaEventDestroy(b); }
 };
+
+// Run a launch sequence of the outer solver: directly on its first use, captured into a
+// CUDA graph on its second (so one-time set-up inside the sequence stays out of the
+// capture), replayed from the graph afterwards.  If capture is not possible the
+// sequence keeps running directly.
+template <typename F>
+static dd_status graphed(dd_ctx* c, const GraphKey& key, F&& fn) {
+  SolverBuffers& s = c->sv;
+  GraphEntry& e = s.graphs[key];
+  if (e.exec) {
+    TRY(cuda_check(c, cudaGraphLaunch(e.exec, c->st), "graph launch"));
+    c->launches += e.kernels;
+    return DD_OK;
+  }
+  if (!c->use_graphs || e.seen == 0 || c->st != s.stream) {
+    e.seen++;
+    return fn();
+  }
+  cudaGraph_t gr = nullptr;
+  TRY(cuda_check(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal), "begin capture"));
+  long long l0 = c->launches;
+  dd_status st = fn();
+  cudaError_t ce = cudaStreamEndCapture(c->st, &gr);
+  long long kernels = c->launches - l0;
+  c->launches = l0;
+  cudaGraphExec_t ex = nullptr;
+  if (st == DD_OK && ce == cudaSuccess && gr && cudaGraphInstantiate(&ex, gr, 0) == cudaSuccess) {
+    cudaGraphDestroy(gr);
+    e.exec = ex;
+    e.kernels = kernels;
+    TRY(cuda_check(c, cudaGraphLaunch(ex, c->st), "graph launch"));
+    c->launches += kernels;
+    return DD_OK;
+  }
+  if (gr) cudaGraphDestroy(gr);
+  cudaGetLastError();
+  c->use_graphs = false;   // capture unavailable: stay with direct launches
+  if (st != DD_OK) return st;
+  return fn();
+}
 
 static dd_status read_status(dd_ctx* c, int n = 4) {
   SolverBuffers& s = c->sv;
@@ -607,29 +671,38 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
     int mm = m;
     double rho_cycle = sqrt(rho2);
     for (int j = j0; j < m; ++j) {
+      // one Arnoldi step = three device-only launch sequences, each replayed from a CUDA
+      // graph once it has been captured (keyed by basis buffer, step and parameters)
+      const GraphKey kbase = {0, cur, j, p->sap.i_schwarz, p->sap.i_domain, p->sap.storage_prec,
+                              p->sap.threads_per_site, m};
+      GraphKey k0 = kbase, k1 = kbase, k2 = kbase;
+      k1[0] = 1;
+      k2[0] = 2;
       cudaEventRecord(e0, c->st);
-      TRY(sap_run(c, Vv(j), Zv(j), &p->sap));
+      TRY(graphed(c, k0, [&]() { return sap_run(c, Vv(j), Zv(j), &p->sap); }));
       cudaEventRecord(e1, c->st);
-      TRY(apply_internal(c, Zv(j), s.w, P32));
+      TRY(graphed(c, k1, [&]() { return apply_internal(c, Zv(j), s.w, P32); }));
       cudaEventRecord(e2, c->st);
-      // Gram-Schmidt: classical projection with the exact norm of the result, repeated
-      // once when it cancels more than half of |w| (Daniel-Gragg-Kaufman-Stewart test)
-      float4* vn = Vv(j + 1);
-      double2* nrm_a = s.nrm2 + 1;
-      double2* nrm_b = s.nrm2 + 2;
-      int nk = launch_gs_dot(Vv(0), j + 1, n4, s.w, s.partial, nullptr, 0, c->st);
-      launch_gs_reduce(s.partial, j + 1, (double2*)s.hA, nullptr, 0, c->st);
-      launch_gs_project(vn, s.w, Vv(0), j + 1, n4, (const double2*)s.hA, s.partial2, nullptr, 0, c->st);
-      launch_gs_reduce(s.partial2, 0, nrm_a, nullptr, 0, c->st);
-      gs_decide_kernel<<<1, 1, 0, c->st>>>(s.hA, j + 1, nrm_a, s.hB, s.flag, s.nu2);
-      nk += launch_gs_dot(Vv(0), j + 1, n4, vn, s.partial, s.flag, 1, c->st);
-      launch_gs_reduce(s.partial, j + 1, (double2*)s.hB, s.flag, 1, c->st);
-      launch_gs_project(vn, vn, Vv(0), j + 1, n4, (const double2*)s.hB, s.partial2, s.flag, 1, c->st);
-      launch_gs_reduce(s.partial2, 0, nrm_b, s.flag, 1, c->st);
-      gs_decide2_kernel<<<1, 1, 0, c->st>>>(s.flag, nrm_b, s.nu2);
-      launch_scale_inplace(vn, n4, s.nu2, c->st);
-      arnoldi_finish_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, j, s.hA, s.hB, s.nu2, s.lsq, s.g, s.status);
-      TRY(launched(c, nk + 11));
+      TRY(graphed(c, k2, [&]() {
+        // Gram-Schmidt: classical projection with the exact norm of the result, repeated
+        // once when it cancels more than half of |w| (Daniel-Gragg-Kaufman-Stewart test)
+        float4* vn = Vv(j + 1);
+        double2* nrm_a = s.nrm2 + 1;
+        double2* nrm_b = s.nrm2 + 2;
+        int nk = launch_gs_dot(Vv(0), j + 1, n4, s.w, s.partial, nullptr, 0, c->st);
+        launch_gs_reduce(s.partial, j + 1, (double2*)s.hA, nullptr, 0, c->st);
+        launch_gs_project(vn, s.w, Vv(0), j + 1, n4, (const double2*)s.hA, s.partial2, nullptr, 0, c->st);
+        launch_gs_reduce(s.partial2, 0, nrm_a, nullptr, 0, c->st);
+        gs_decide_kernel<<<1, 1, 0, c->st>>>(s.hA, j + 1, nrm_a, s.hB, s.flag, s.nu2);
+        nk += launch_gs_dot(Vv(0), j + 1, n4, vn, s.partial, s.flag, 1, c->st);
+        launch_gs_reduce(s.partial, j + 1, (double2*)s.hB, s.flag, 1, c->st);
+        launch_gs_project(vn, vn, Vv(0), j + 1, n4, (const double2*)s.hB, s.partial2, s.flag, 1, c->st);
+        launch_gs_reduce(s.partial2, 0, nrm_b, s.flag, 1, c->st);
+        gs_decide2_kernel<<<1, 1, 0, c->st>>>(s.flag, nrm_b, s.nu2);
+        launch_scale_inplace(vn, n4, s.nu2, c->st);
+        arnoldi_finish_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, j, s.hA, s.hB, s.nu2, s.lsq, s.g, s.status);
+        return launched(c, nk + 11);
+      }));
       cudaEventRecord(e3, c->st);
       TRY(read_status(c));
       float ms;
@@ -753,6 +826,21 @@ extern "C" dd_status dd_solve(dd_ctx* c, const double* f, double* x, int nrhs, i
   TRY(ensure_solver(c, p->m));
   if (info) memset(info, 0, sizeof(*info));
   SolverBuffers& s = c->sv;
+  // Run on the solver's own stream (capturable into CUDA graphs even when the caller
+  // uses the legacy default stream), ordered after the caller's stream; the call is
+  // synchronous, so the caller's stream needs no event back.
+  struct StreamSwap {
+    dd_ctx* c;
+    cudaStream_t user;
+    ~StreamSwap() {
+      cudaStreamSynchronize(c->st);
+      c->st = user;
+    }
+  };
+  cudaEventRecord(s.ev_in, c->st);
+  cudaStreamWaitEvent(s.stream, s.ev_in, 0);
+  StreamSwap swap{c, c->st};
+  c->st = s.stream;
   const Geom& g = c->g;
   size_t cb = (size_t)g.V * 24 * 8;
   cudaMemcpyKind in_kind = where == DD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;

@@ -613,18 +613,6 @@ __device__ inline void block_apply(const MatBlock<MT>& M, int r, int h, const Ha
     for (int c = 0; c < 3; ++c) y.c[s][c] = w[3 * s + c];
 }
 
-template <typename MT>
-__device__ inline void hops_half(int h, const Geom& g, const int l[4], int lex, int p, int r_self, const float4* src,
-                                 const MatBlock<MT>& M, Spinor<float>& acc) {
-  if (h == 0) {
-    inside_hop_mu<0>(g, l, lex, p, r_self, src, M, acc);
-    inside_hop_mu<1>(g, l, lex, p, r_self, src, M, acc);
-  } else {
-    inside_hop_mu<2>(g, l, lex, p, r_self, src, M, acc);
-    inside_hop_mu<3>(g, l, lex, p, r_self, src, M, acc);
-  }
-}
-
 // acc: this thread's partial sum over its two directions.  The other thread of the site
 // holds the rest.  Returns the full sum of chirality half h.  buf is scratch here.
 __device__ inline void exchange(const Spinor<float>& acc, int h, float4* buf, int Hd, int i, Half<float>& own) {
@@ -675,215 +663,10 @@ template <> struct EvenHalfStore<__half> {
   }
 };
 
-template <typename MT, typename VT, bool MSMEM>
-__global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair_unrolled(SapArgs a) {
-  const Geom& g = a.g;
-  extern __shared__ float4 smem[];
-  __shared__ uint64_t mbar;
-  __shared__ float4 red[2 * SAP_MAX_THREADS / 32];
-  __shared__ float nrm[2 * SAP_MAX_THREADS];
-  const int tid = threadIdx.x;
-  const int Hd = g.Hd, Vd = g.Vd;
-  const int h = tid >= Hd;          // MR phases: chirality half and hop directions; ends: parity
-  const int i = tid - h * Hd;
-
-  int n[4];
-  {
-    int hx = g.N[0] >> 1;
-    int j = blockIdx.x % hx;
-    int row = blockIdx.x / hx;
-    n[1] = row % g.N[1];
-    n[2] = (row / g.N[1]) % g.N[2];
-    n[3] = row / (g.N[1] * g.N[2]);
-    n[0] = 2 * j + ((a.colour + n[1] + n[2] + n[3]) & 1);
-  }
-  const long long d = n[0] + (long long)g.dstride[1] * n[1] + (long long)g.dstride[2] * n[2] +
-                      (long long)g.dstride[3] * n[3];
-  const size_t lk_elems = (size_t)4 * 9 * Vd;
-  const size_t lk_bytes = (size_t)MatBlock<MT>::link_bytes_per_site * Vd;
-  const size_t cm_bytes = (size_t)MatBlock<MT>::mat_bytes_per_site * Vd;
-  char* sbase = reinterpret_cast<char*>(smem);
-  MatBlock<MT> M;
-  M.Vd = Vd;
-  typedef typename std::remove_const<typename std::remove_pointer<decltype(M.lk)>::type>::type LkT;
-  typedef typename std::remove_const<typename std::remove_pointer<decltype(M.cm)>::type>::type CmT;
-  const LkT* glk = reinterpret_cast<const LkT*>(a.links) + d * lk_elems;
-  const CmT* gcm = reinterpret_cast<const CmT*>(a.smat) + d * (cm_bytes / sizeof(CmT));
-  float4* sE;
-  if (MSMEM) {
-    M.lk = reinterpret_cast<const LkT*>(sbase);
-    M.cm = reinterpret_cast<const CmT*>(sbase + lk_bytes);
-    sE = reinterpret_cast<float4*>(sbase + lk_bytes + cm_bytes);
-    if (tid == 0) mbar_init(&mbar, 1);
-    __syncthreads();
-    if (tid == 0) {
-      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes) + a.extra_tx);
-      bulk_g2s(sbase, glk, (uint32_t)lk_bytes, &mbar);
-      bulk_g2s(sbase + lk_bytes, gcm, (uint32_t)cm_bytes, &mbar);
-    }
-  } else {
-    M.lk = glk;
-    M.cm = gcm;
-    sE = smem;
-  }
-  float4* sO = sE + 6 * Hd;
-
-  int le[4], lo[4];
-  local_coords(g, 0, i, le);
-  local_coords(g, 1, i, lo);
-  const int lex_e = le[0] + g.bstride[1] * le[1] + g.bstride[2] * le[2] + g.bstride[3] * le[3];
-  const int lex_o = lo[0] + g.bstride[1] * lo[1] + g.bstride[2] * lo[2] + g.bstride[3] * lo[3];
-  const int r_e = i, r_o = Hd + i;
-  const int* lsite = h ? lo : le;            // prologue / epilogue: site (parity h, index i)
-  const long long s_site = (d << g.lgVd) + h * Hd + i;
-  const int r_site = h * Hd + i;
-
-  // 1. residual of site (h, i), with the couplings to the other colour
-  EvenStore<VT> rst{reinterpret_cast<decltype(EvenStore<VT>::p)>(a.r_store), a.r_norm};
-  {
-    Spinor<float> r;
-    const SpinorPtr<float> vin{const_cast<float4*>(a.v)};
-    if (a.first) vin.load(g, s_site, r);
-    else if (h == 0) rst.load(d, Hd, i, r);
-    else zero(r);
-    if (MSMEM) {
-      bool ok = mbar_wait(&mbar, 0, a.wait_ns);
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicExch(a.err, 1);
-        mbar_wait(&mbar, 0, a.wait_ns);
-        return;
-      }
-    }
-    if (a.use_faces) {
-      Spinor<float> acc;
-      zero(acc);
-      face_hops(g, (int)d, n, lsite, r_site, a.faces, M, acc);
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) r.c[s][c] = r.c[s][c] + 0.5f * acc.c[s][c];
-    }
-    st_buf(h ? sO : sE, Hd, i, r);
-  }
-  __syncthreads();
-  Half<float> reh, roh, t, own, rho, x;
-  ld_hbuf(sE, Hd, i, h, reh);
-  ld_hbuf(sO, Hd, i, h, roh);
-  __syncthreads();
-
-  // 2. even-odd preparation: t_o = A_oo^{-1} r_o (per chirality), f_e = r_e + 1/2 H_eo t_o
-  block_apply(M, r_o, h, roh, t);
-  st_hbuf(sO, Hd, i, h, t);
-  __syncthreads();
-  Spinor<float> acc;
-  zero(acc);
-  hops_half(h, g, le, lex_e, 0, r_e, sO, M, acc);
-  exchange(acc, h, sE, Hd, i, own);
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      rho.c[s][c] = reh.c[s][c] + 0.5f * own.c[s][c];
-      x.c[s][c] = mk(0.f, 0.f);
-    }
-  st_hbuf(sE, Hd, i, h, rho);
-  __syncthreads();
-
-  // 3. MR on the Schur complement
-  const int nwarp = (2 * Hd + 31) >> 5;
-  for (int it = 0; it < a.i_domain; ++it) {
-    zero(acc);
-    hops_half(h, g, lo, lex_o, 1, r_o, sE, M, acc);
-    exchange(acc, h, sO, Hd, i, own);
-    block_apply(M, r_o, h, own, t);
-    st_hbuf(sO, Hd, i, h, t);
-    __syncthreads();
-    zero(acc);
-    hops_half(h, g, le, lex_e, 0, r_e, sO, M, acc);
-    exchange(acc, h, sE, Hd, i, own);
-    Half<float> pv;
-    block_apply(M, r_e, h, rho, pv);
-    float pr_re = 0.f, pr_im = 0.f, pp = 0.f;
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        pv.c[s][c] = pv.c[s][c] - 0.25f * own.c[s][c];
-        cx<float> q = cjmul(pv.c[s][c], rho.c[s][c]);
-        pr_re += q.re;
-        pr_im += q.im;
-        pp += pv.c[s][c].re * pv.c[s][c].re + pv.c[s][c].im * pv.c[s][c].im;
-      }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      pr_re += __shfl_xor_sync(0xffffffffu, pr_re, o);
-      pr_im += __shfl_xor_sync(0xffffffffu, pr_im, o);
-      pp += __shfl_xor_sync(0xffffffffu, pp, o);
-    }
-    if ((tid & 31) == 0) red[tid >> 5] = make_float4(pr_re, pr_im, pp, 0.f);
-    __syncthreads();
-    float sr = 0.f, si = 0.f, sp = 0.f;
-    for (int w = 0; w < nwarp; ++w) {
-      float4 q = red[w];
-      sr += q.x;
-      si += q.y;
-      sp += q.z;
-    }
-    cx<float> alpha = sp > 0.f ? mk(sr / sp, si / sp) : mk(0.f, 0.f);
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        x.c[s][c] = x.c[s][c] + cmul(alpha, rho.c[s][c]);
-        rho.c[s][c] = rho.c[s][c] - cmul(alpha, pv.c[s][c]);
-      }
-    st_hbuf(sE, Hd, i, h, rho);
-    __syncthreads();
-  }
-
-  // 4. odd reconstruction delta_o = A_oo^{-1} (r_o + 1/2 H_oe x); store the MR residual
-  st_hbuf(sE, Hd, i, h, x);
-  __syncthreads();
-  zero(acc);
-  hops_half(h, g, lo, lex_o, 1, r_o, sE, M, acc);
-  exchange(acc, h, sO, Hd, i, own);
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) own.c[s][c] = roh.c[s][c] + 0.5f * own.c[s][c];
-  block_apply(M, r_o, h, own, t);
-  st_hbuf(sO, Hd, i, h, t);
-  if (!a.last) EvenHalfStore<VT>::store(rst, nrm, d, Hd, i, h, rho);
-  __syncthreads();
-
-  // 5. site (h, i): u += delta, faces of delta
-  Spinor<float> dl;
-  ld_buf(h ? sO : sE, Hd, i, dl);
-  typename VecPtr<VT>::type ust = VecPtr<VT>::make(a.u_store, a.u_norm);
-  Spinor<float> u;
-  if (a.first) {
-    u = dl;
-  } else {
-    ust.load(g, s_site, u);
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) u.c[s][c] = u.c[s][c] + dl.c[s][c];
-  }
-  if (a.last) {
-    SpinorPtr<float> zo{a.z};
-    zo.store(g, s_site, u);
-  } else {
-    ust.store(g, s_site, u);
-  }
-  if (!(a.last && a.colour == 1)) face_write(g, d, lsite, r_site, a.faces, M, dl);
-}
-
-// ------------------------------------------------------------------ compact hop code
-// The domain solve runs ~2 + 2 I_domain hop phases per visit; written out for every
-// direction and phase the kernel outgrows the instruction cache.  Here a hop has one
-// body: the direction is a loop variable and only the few additions of the spin
-// projection and reconstruction are selected per direction (warp-uniform switches).
+// ------------------------------------------------------------------ face code, run-time direction
+// Face coupling and face output run once per visit; with the direction as a loop variable
+// (only the spin projection and reconstruction are selected per direction, warp-uniform)
+// their code stays small.
 __device__ inline void project_rt(int mu, int dir, const Spinor<float>& p, Half<float>& h) {
   // forward hop uses (1 - gamma_mu), backward (1 + gamma_mu)
   switch (2 * mu + (dir < 0)) {
@@ -932,27 +715,6 @@ __device__ inline void inside_masks(const Geom& g, const int l[4], unsigned& fwd
   for (int mu = 0; mu < 4; ++mu) {
     fwd |= (l[mu] + 1 < g.b[mu] ? 1u : 0u) << mu;
     bwd |= (l[mu] > 0 ? 1u : 0u) << mu;
-  }
-}
-
-// acc += hops inside the domain along mu = mu0, mu0 + 1 (both senses), no -1/2 factor.
-template <typename MT>
-__device__ inline void hops_rt(const Geom& g, int mu0, unsigned fwd, unsigned bwd, int lex, int p, int r_self,
-                               const float4* src, const MatBlock<MT>& M, Spinor<float>& acc) {
-#pragma unroll 1
-  for (int k = 0; k < 4; ++k) {
-    const int mu = mu0 + (k >> 1);
-    const int dir = (k & 1) ? -1 : 1;
-    if (!(((dir > 0 ? fwd : bwd) >> mu) & 1u)) continue;
-    const int j = (lex + dir * g.bstride[mu]) >> 1;
-    Spinor<float> psi;
-    ld_buf(src, g.Hd, j, psi);
-    Half<float> h, uh;
-    project_rt(mu, dir, psi, h);
-    Link<float> U;
-    link_rt(M, mu, dir > 0 ? r_self : (1 - p) * g.Hd + j, dir, U);
-    su3_mul(U, h, uh);
-    recon_rt(mu, dir, acc, uh);
   }
 }
 
@@ -1023,47 +785,6 @@ __device__ inline void face_write_rt(const Geom& g, long long d, const int l[4],
   }
 }
 
-// Clover block h of site r applied to x (block index at run time).
-template <typename MT> struct BlockLoadRt;
-template <> struct BlockLoadRt<__half> {
-  __device__ static void load(const MatBlock<__half>& M, int r, int h, float m[36]) {
-    float t[40];
-#pragma unroll
-    for (int u = 0; u < 5; ++u) {
-      uint4 v = M.cm[(4 * h + u) * M.Vd + r];
-      uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) { float2 f = h2f(w[e]); t[8 * u + 2 * e] = f.x; t[8 * u + 2 * e + 1] = f.y; }
-    }
-#pragma unroll
-    for (int k = 0; k < 36; ++k) m[k] = h ? t[k + 4] : t[k];
-  }
-};
-template <> struct BlockLoadRt<float> {
-  __device__ static void load(const MatBlock<float>& M, int r, int h, float m[36]) {
-#pragma unroll
-    for (int u = 0; u < 9; ++u) {
-      float4 v = M.cm[(9 * h + u) * M.Vd + r];
-      m[4 * u] = v.x; m[4 * u + 1] = v.y; m[4 * u + 2] = v.z; m[4 * u + 3] = v.w;
-    }
-  }
-};
-template <typename MT>
-__device__ inline void block_apply_rt(const MatBlock<MT>& M, int r, int h, const Half<float>& x, Half<float>& y) {
-  float m[36];
-  BlockLoadRt<MT>::load(M, r, h, m);
-  cx<float> v[6], w[6];
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) v[3 * s + c] = x.c[s][c];
-  clover_block_mul(m, v, w);
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) y.c[s][c] = w[3 * s + c];
-}
-
 // Hops of one direction with the inside-the-domain test taken from bit masks, so the
 // phase loop carries four small integers instead of two coordinate arrays.
 template <int MU, typename MT>
@@ -1102,7 +823,8 @@ __device__ inline void hops_half_mask(int h, const Geom& g, unsigned fwd, unsign
   }
 }
 
-// Two threads per site, compact code.  The MR iteration is a loop over hop phases:
+// Two threads per site.  The MR iteration is a loop over hop phases, so the hop and
+// clover code appears once (the whole kernel then fits the instruction cache):
 //   phase 0:          even sites, src = t_o      -> rho = r_e + 1/2 H t_o, x = 0
 //   phase 2k+1:       odd sites,  src = rho      -> t = A_oo^{-1} H rho
 //   phase 2k+2:       even sites, src = t        -> p = A_ee rho - 1/4 H t, MR step
@@ -1210,7 +932,7 @@ __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArg
   for (int s = 0; s < 2; ++s)
 #pragma unroll
     for (int c = 0; c < 3; ++c) x.c[s][c] = mk(0.f, 0.f);
-  block_apply_rt(M, r_o, h, roh, t);       // t_o = A_oo^{-1} r_o
+  block_apply(M, r_o, h, roh, t);          // t_o = A_oo^{-1} r_o
   st_hbuf(sO, Hd, i, h, t);
   __syncthreads();
 

@@ -58,3 +58,26 @@ def test_initial_guess_and_zero_source():
     xz = np.ones_like(f)
     c.dd_solve(z, xz, tol=1e-10, m=16, k=0, i_schwarz=16, i_domain=4)
     assert np.abs(xz).max() == 0
+
+
+def test_graph_replay_matches_direct_launches(monkeypatch):
+    """Arnoldi steps replayed from captured CUDA graphs (from the second occurrence of a
+    step on) give bit-for-bit the solution of direct launches (DD_NO_GRAPHS=1)."""
+    dims, dom = (16, 8, 8, 8), (8, 4, 4, 4)
+    U = gauge(dims, 0.5, 31, ape=2)
+    f = synth.gaussian_source(dims, 32)
+    kw = dict(tol=1e-10, m=8, k=2, i_schwarz=2, i_domain=3, storage_prec=dd.DD_PREC_FP16)
+    c = ctx_for(dims, dom, U, 0.1250, 1.5)
+    xs = []
+    for _ in range(3):
+        x = np.zeros_like(f)
+        info = c.dd_solve(f, x, **kw)
+        xs.append(x)
+    assert info.restarts >= 1
+    assert np.array_equal(xs[0], xs[1]) and np.array_equal(xs[1], xs[2])
+    monkeypatch.setenv("DD_NO_GRAPHS", "1")
+    c2 = ctx_for(dims, dom, U, 0.1250, 1.5)
+    xd = np.zeros_like(f)
+    c2.dd_solve(f, xd, **kw)
+    assert np.array_equal(xd, xs[0])
+    assert S.true_residual(U, xd, f, 0.1250, 1.5) <= 1e-10
