@@ -41,9 +41,9 @@ WORKLOADS = {
     "8^4": Workload("8^4", (8, 8, 8, 8), 0.6, 0, 0.1300, 1.0, (4, 4, 4, 4), 16, 4, 16, 0, 11, 21),
     # kappa = 0.136 lies above the critical kappa (~0.125) of these smooth synthetic
     # fields (plaquette 0.997), where 16 multiplicative Schwarz sweeps amplify the
-    # residual; I_Schwarz = 2, I_domain = 4, (m, k) = (32, 8) were picked by measuring
+    # residual; I_Schwarz = 2, I_domain = 4, (m, k) = (40, 8) were picked by measuring
     # time-to-solution on the GPU.
-    "32^3x64": Workload("32^3x64", (32, 32, 32, 64), 0.5, 5, 0.1360, 1.5, (8, 4, 4, 4), 2, 4, 32, 8, 12, 22),
+    "32^3x64": Workload("32^3x64", (32, 32, 32, 64), 0.5, 5, 0.1360, 1.5, (8, 4, 4, 4), 2, 4, 40, 8, 12, 22),
     "24^3x48": Workload("24^3x48", (24, 24, 24, 48), 0.5, 5, 0.1360, 1.5, (4, 4, 4, 4), 16, 5, 16, 6, 14, 24),
     "16^3x32": Workload("16^3x32", (16, 16, 16, 32), 0.5, 5, 0.1340, 1.5, (4, 4, 4, 4), 16, 5, 16, 6, 151, 25),
 }
