@@ -32,7 +32,7 @@ METRIC = "time-to-solution to 1e-10 true residual, mixed FP16/FP32/FP64 SAP-FGMR
 FLOP_HOP, FLOP_CLOVER, FLOP_A = 168, 504, 1848      # Sec. II-B: 1344 = 8 x 168, 504, 1848
 # Outer iterations the 32^3x64 solve takes (measured on the GPU, mixed and FP32 alike);
 # only used to scale the oracle's sampled cost to a whole solve.
-ORACLE_ITERS_32x64 = 888
+ORACLE_ITERS_32x64 = 696
 
 
 # ------------------------------------------------------------------ flop / byte model
