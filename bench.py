@@ -222,6 +222,7 @@ def main():
                     help="sap / dslash: time one kernel alone on --lattice (kernel studies, ncu captures)")
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--tps", type=int, default=0, help="Schwarz kernel threads per site (0: library default)")
+    ap.add_argument("--nrhs", type=int, default=1, help="kernel studies: right-hand sides per launch")
     args = ap.parse_args()
     if not args.only_mixed:
         args.warmup = max(args.warmup, 3)   # profiling runs (--only-mixed) may skip the warm-up
@@ -394,15 +395,24 @@ def kernel_case(args, local):
     del U
     V = int(np.prod(dims))
     src = torch.view_as_real(torch.from_numpy(f)).to(torch.float32).cuda().contiguous()
-    a = torch.empty(ctx.dd_spinor_bytes(dd.DD_PREC_FP32, dd.DD_LAYOUT_INTERNAL), dtype=torch.uint8, device="cuda")
+    nb = ctx.dd_spinor_bytes(dd.DD_PREC_FP32, dd.DD_LAYOUT_INTERNAL)
+    nr = args.nrhs
+    a = torch.empty(nr * nb, dtype=torch.uint8, device="cuda")
     b = torch.empty_like(a)
-    ctx.dd_pack_spinor(src, dd.DD_PREC_FP32, a, dd.DD_PREC_FP32)
+    for r in range(nr):
+        ctx.dd_pack_spinor(src, dd.DD_PREC_FP32, a[r * nb:(r + 1) * nb], dd.DD_PREC_FP32)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = args.steps
-    if args.case == "sap":
+    if args.case == "sap" and nr > 1:
+        run = lambda: ctx.dd_sap_precondition_batch(a, b, nr, w.i_schwarz, w.i_domain, dd.DD_PREC_FP16)
+        launches = 2 * w.i_schwarz
+    elif args.case == "sap":
         run = lambda: ctx.dd_sap_precondition(a, b, w.i_schwarz, w.i_domain, dd.DD_PREC_FP16, dd.DD_LAYOUT_INTERNAL,
                                               threads_per_site=args.tps)
         launches = 2 * w.i_schwarz
+    elif nr > 1:
+        run = lambda: ctx.dd_apply_D_batch(a, b, nr, dd.DD_PREC_FP32)
+        launches = 1
     else:
         run = lambda: ctx.dd_apply_D(a, b, dd.DD_PREC_FP32, dd.DD_LAYOUT_INTERNAL)
         launches = 1
@@ -417,11 +427,16 @@ def kernel_case(args, local):
     launch_s = e0.elapsed_time(e1) / 1e3 / (reps * launches)
     if args.case == "sap":
         useful, nominal = sap_visit_flops(w.domain, w.i_domain)
-        out = {"case": "sap_kernel", "threads_per_site": args.tps or 2, "lattice": dims, "launch_ms": 1e3 * launch_s,
-               "tflops_useful": useful * V / 2 / launch_s / 1e12, "gflops_nominal": nominal * V / 2 / launch_s / 1e9}
+        out = {"case": "sap_kernel", "threads_per_site": args.tps or 2, "nrhs": nr, "lattice": dims,
+               "launch_ms": 1e3 * launch_s, "tflops_useful": nr * useful * V / 2 / launch_s / 1e12,
+               "gflops_nominal": nr * nominal * V / 2 / launch_s / 1e9}
     else:
-        out = {"case": "apply_A_kernel<float>", "lattice": dims, "launch_ms": 1e3 * launch_s,
-               "gbs_algorithmic": dslash_bytes_per_site("fp32") * V / launch_s / 1e9}
+        # per right-hand side the batch reads the links and clover once per pair
+        per_site = dslash_bytes_per_site("fp32") if nr == 1 else (72 + 72) * 4 / 2 + 48 * 4
+        out = {"case": "apply_A_kernel<float>" if nr == 1 else "apply_A_multi_kernel<float,2>", "nrhs": nr,
+               "lattice": dims, "launch_ms": 1e3 * launch_s,
+               "ms_per_rhs": 1e3 * launch_s / nr,
+               "gbs_algorithmic": per_site * V * nr / launch_s / 1e9}
     print(json.dumps(out))
 
 

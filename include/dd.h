@@ -118,6 +118,17 @@ dd_status dd_apply_D(dd_ctx* ctx, const void* in, void* out, int prec, int layou
  * buffers in `layout`; they may not overlap. */
 dd_status dd_sap_precondition(dd_ctx* ctx, const float* in, float* out, const dd_sap_params* p, int layout);
 
+/* Several right-hand sides in one launch (batching of the many solves of an analysis,
+ * Sec. IV-C).  in/out hold nrhs fields in the internal layout, one after another
+ * (stride dd_spinor_bytes(ctx, prec, DD_LAYOUT_INTERNAL)); they may not overlap.
+ * dd_sap_precondition_batch: out_r = M in_r, FP32 fields; each domain's links and Schwarz
+ * matrices are staged into shared memory once and used for all right-hand sides
+ * (threads_per_site must be 0 or 2).  dd_apply_D_batch: out_r = A in_r for FP32 or FP16
+ * fields, two right-hand sides per thread, so each link and clover block is loaded once
+ * per pair. */
+dd_status dd_sap_precondition_batch(dd_ctx* ctx, const float* in, float* out, int nrhs, const dd_sap_params* p);
+dd_status dd_apply_D_batch(dd_ctx* ctx, const void* in, void* out, int nrhs, int prec);
+
 /* out = M in like dd_sap_precondition, but without allocating: the paper has no
  * counterpart to this entry point.  It is for callers that cannot call cudaMalloc when
  * they apply the preconditioner: code running under CUDA stream capture (a cudaMalloc

@@ -33,6 +33,8 @@ struct SapBuffers {
   void* u_store = nullptr;
   float* u_norm = nullptr;
   float4* faces = nullptr;
+  int cap = 0;                 // right-hand sides the buffers hold
+  long long r_bytes = 0, u_bytes = 0;
 };
 
 // A launch sequence of the outer solver captured as a CUDA graph: key = (part, basis
@@ -352,29 +354,45 @@ extern "C" dd_status dd_unpack_spinor(dd_ctx* c, const void* internal, int iprec
 }
 
 // ------------------------------------------------------------------ Schwarz preconditioner
-static dd_status ensure_sap(dd_ctx* c, int prec) {
+static void release(dd_ctx* c, void* p);
+
+// Schwarz state (residual, solution, faces) for nrhs right-hand sides, one after another.
+static dd_status ensure_sap(dd_ctx* c, int prec, int nrhs = 1) {
   SapBuffers& b = c->sap[prec];
-  if (b.faces) return DD_OK;
-  const Geom& g = c->g;
-  size_t half_sites = (size_t)g.V / 2;
-  if (prec == P16) {
-    TRY(dalloc(c, &b.r_store, half_sites * 48));
-    TRY(dalloc(c, &b.r_norm, half_sites * 4));
-    TRY(dalloc(c, &b.u_store, (size_t)g.V * 48));
-    TRY(dalloc(c, &b.u_norm, (size_t)g.V * 4));
-  } else {
-    TRY(dalloc(c, &b.r_store, half_sites * 96));
-    TRY(dalloc(c, &b.u_store, (size_t)g.V * 96));
+  if (b.faces && b.cap >= nrhs) return DD_OK;
+  if (b.faces) {
+    cudaStreamSynchronize(c->st);
+    for (void* q : {(void*)b.r_store, (void*)b.r_norm, (void*)b.u_store, (void*)b.u_norm, (void*)b.faces}) release(c, q);
+    b = SapBuffers();
   }
-  TRY(dalloc(c, &b.faces, (size_t)g.ND * g.face_block * 48));
+  const Geom& g = c->g;
+  size_t half_sites = (size_t)g.V / 2, n = (size_t)nrhs;
+  if (prec == P16) {
+    TRY(dalloc(c, &b.r_store, n * half_sites * 48));
+    TRY(dalloc(c, &b.r_norm, n * half_sites * 4));
+    TRY(dalloc(c, &b.u_store, n * (size_t)g.V * 48));
+    TRY(dalloc(c, &b.u_norm, n * (size_t)g.V * 4));
+    b.r_bytes = (long long)half_sites * 48;
+    b.u_bytes = (long long)g.V * 48;
+  } else {
+    TRY(dalloc(c, &b.r_store, n * half_sites * 96));
+    TRY(dalloc(c, &b.u_store, n * (size_t)g.V * 96));
+    b.r_bytes = (long long)half_sites * 96;
+    b.u_bytes = (long long)g.V * 96;
+  }
+  TRY(dalloc(c, &b.faces, n * (size_t)g.ND * g.face_block * 48));
+  b.cap = nrhs;
   return DD_OK;
 }
 
-static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_params* p) {
+static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_params* p, int nrhs = 1) {
   int prec = p->storage_prec == DD_PREC_FP16 ? P16 : P32;
-  TRY(ensure_sap(c, prec));
+  TRY(ensure_sap(c, prec, nrhs));
   SapBuffers& b = c->sap[prec];
   SapState S;
+  S.nrhs = nrhs;
+  S.r_bytes = b.r_bytes;
+  S.u_bytes = b.u_bytes;
   S.mat_prec = prec;
   S.vec_prec = prec;
   S.links = prec == P16 ? (const void*)c->U16 : (const void*)c->U32;
@@ -432,6 +450,27 @@ extern "C" dd_status dd_sap_precondition(dd_ctx* c, const float* in, float* out,
     TRY(launched(c));
   }
   return sap_error_flag(c);
+}
+
+// ------------------------------------------------------------------ several right-hand sides
+extern "C" dd_status dd_sap_precondition_batch(dd_ctx* c, const float* in, float* out, int nrhs,
+                                               const dd_sap_params* p) {
+  if (!c || !in || !out || nrhs < 1) return DD_ERR_INVALID;
+  TRY(check_sap_params(c, p));
+  if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
+  if (p->i_domain == 0) return fail(c, DD_ERR_INVALID, "i_domain must be >= 1");
+  if (p->threads_per_site == 1 && nrhs > 1) return fail(c, DD_ERR_INVALID, "batches need threads_per_site 2");
+  TRY(sap_run(c, (const float4*)in, (float4*)out, p, nrhs));
+  return sap_error_flag(c);
+}
+
+extern "C" dd_status dd_apply_D_batch(dd_ctx* c, const void* in, void* out, int nrhs, int prec) {
+  if (!c || !in || !out || nrhs < 1 || (prec != DD_PREC_FP32 && prec != DD_PREC_FP16)) return DD_ERR_INVALID;
+  if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
+  launch_apply_A_multi(c->g, gauge_view(c, prec), clover_view(c, prec), view(c->g, (void*)in, prec),
+                       view(c->g, out, prec), nrhs, c->st);
+  TRY(launched(c));
+  return cuda_check(c, cudaStreamSynchronize(c->st), "apply_D_batch");
 }
 
 // ------------------------------------------------------------------ small dense kernels

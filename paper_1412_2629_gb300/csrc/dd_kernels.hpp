@@ -35,6 +35,10 @@ void launch_build_clover(const Geom& g, const double* canon, double kappa, doubl
                          float4* c32, uint4* c16, float4* s32, uint4* s16, int* status, cudaStream_t st);
 
 // ---- Wilson-clover operator (dslash.cu)
+// Several right-hand sides per thread (nrhs fields of one precision, one after another,
+// stride = one field): each link and clover block is loaded once per site.
+void launch_apply_A_multi(const Geom& g, GaugeView U, CloverView C, FieldView in, FieldView out, int nrhs,
+                          cudaStream_t st);
 // out = A in, or out = f - A in when f != nullptr.  FP64 and FP32 fields use the matching
 // gauge/clover precision; FP16 fields use FP16 gauge/clover and FP32 arithmetic.
 void launch_apply_A(const Geom& g, GaugeView U, CloverView C, FieldView in, FieldView out, const FieldView* f,
@@ -55,6 +59,9 @@ struct SapState {
   bool mat_in_smem;    // stage links and Schwarz matrices in shared memory
   int threads_per_site = 2;   // 1: one thread per site; 2: hop directions and chirality split
   bool inject_wait_timeout = false;   // test hook: make the bounded wait run out (no fault)
+  int nrhs = 1;                // right-hand sides in one launch (their buffers follow each other)
+  long long r_bytes = 0;       // bytes of one right-hand side's residual / solution storage
+  long long u_bytes = 0;
 };
 // One half-sweep: all domains of `colour`.  first: the residual is the input v (both
 // parities) and u = 0; use_faces: subtract the couplings to the other colour from the

@@ -94,3 +94,102 @@ void launch_apply_A(const Geom& g, GaugeView U, CloverView C, FieldView in, Fiel
 }
 
 }  // namespace dd
+
+namespace dd {
+
+// ------------------------------------------------------------------ several right-hand sides
+__device__ inline void shift_norm(SpinorPtr<float>&, long long) {}
+__device__ inline void shift_norm(SpinorPtr<__half>& p, long long d) { p.norm += d; }
+
+// Thread per site, NR right-hand sides per thread: every link and the clover block are
+// loaded once and applied to NR spinors, so per right-hand side the operator moves
+// (4 links + clover) / NR + in + out bytes instead of all 192 reals.
+template <int MU, typename T, int NR>
+__device__ inline void hop_pair_multi(const Geom& g, const Site& st, long long s, const SpinorPtr<T>* in,
+                                      const LinkPtr<T>& U, Spinor<typename Arith<T>::type>* acc) {
+  typedef typename Arith<T>::type R;
+  Spinor<R> psi;
+  Half<R> h, uh;
+  Link<R> L;
+  long long sf = neighbour(g, st, MU, +1);
+  U.load(g, s, MU, L);
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    in[r].load(g, sf, psi);
+    project<MU, -1>(psi, h);
+    su3_mul(L, h, uh);
+    accum_recon<MU, -1>(acc[r], uh);
+  }
+  long long sb = neighbour(g, st, MU, -1);
+  U.load(g, sb, MU, L);
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    in[r].load(g, sb, psi);
+    project<MU, +1>(psi, h);
+    su3_dag_mul(L, h, uh);
+    accum_recon<MU, +1>(acc[r], uh);
+  }
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(128) apply_A_multi_kernel(Geom g, LinkPtr<T> U, CloverPtr<T> C, SpinorPtr<T> in0,
+                                                             SpinorPtr<T> out0, long long unit_stride,
+                                                             long long norm_stride, int nrhs) {
+  typedef typename Arith<T>::type R;
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const int r0 = blockIdx.y * NR;
+  SpinorPtr<T> in[NR], out[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    int rr = r0 + r < nrhs ? r0 + r : nrhs - 1;   // a short last group repeats the last field
+    in[r] = in0;
+    out[r] = out0;
+    in[r].p += rr * unit_stride;
+    out[r].p += rr * unit_stride;
+    shift_norm(in[r], rr * norm_stride);
+    shift_norm(out[r], rr * norm_stride);
+  }
+  Site st = decode(g, s);
+  Spinor<R> acc[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) zero(acc[r]);
+  hop_pair_multi<0, T, NR>(g, st, s, in, U, acc);
+  hop_pair_multi<1, T, NR>(g, st, s, in, U, acc);
+  hop_pair_multi<2, T, NR>(g, st, s, in, U, acc);
+  hop_pair_multi<3, T, NR>(g, st, s, in, U, acc);
+  R m[72];
+  C.load(g, s, m);
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (r0 + r >= nrhs) break;
+    Spinor<R> x, y;
+    in[r].load(g, s, x);
+    clover_mul(m, x, y);
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+      for (int b2 = 0; b2 < 3; ++b2) y.c[a2][b2] = y.c[a2][b2] - R(0.5) * acc[r].c[a2][b2];
+    out[r].store(g, s, y);
+  }
+}
+
+void launch_apply_A_multi(const Geom& g, GaugeView U, CloverView C, FieldView in, FieldView out, int nrhs,
+                          cudaStream_t st) {
+  const int NR = 2;
+  dim3 grid((unsigned)((g.V + 127) / 128), (unsigned)((nrhs + NR - 1) / NR));
+  if (in.prec == P32) {
+    apply_A_multi_kernel<float, NR><<<grid, 128, 0, st>>>(
+        g, LinkPtr<float>{(const float2*)U.links}, CloverPtr<float>{(const float4*)C.m},
+        SpinorPtr<float>{(float4*)in.data}, SpinorPtr<float>{(float4*)out.data}, g.V * 6, 0, nrhs);
+  } else {
+    // FP16 fields are V * 52 bytes each (values, then the per-site norms) and follow each
+    // other: 13 V / 4 uint4 units or 13 V floats apart (V is a multiple of 64)
+    apply_A_multi_kernel<__half, NR><<<grid, 128, 0, st>>>(
+        g, LinkPtr<__half>{(const uint32_t*)U.links}, CloverPtr<__half>{(const uint4*)C.m},
+        SpinorPtr<__half>{(uint4*)in.data, in.norm}, SpinorPtr<__half>{(uint4*)out.data, out.norm}, 13 * g.V / 4,
+        13 * g.V, nrhs);
+  }
+}
+
+}  // namespace dd

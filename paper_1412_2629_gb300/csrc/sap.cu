@@ -315,6 +315,11 @@ struct SapArgs {
   // expect: 0 normally; a test sets it so the wait runs out and the error path is taken.
   unsigned long long wait_ns;
   unsigned extra_tx;
+  // several right-hand sides per launch (two-threads-per-site kernel): strides between
+  // consecutive right-hand sides of v / z (float4), faces (float4), residual and solution
+  // storage (bytes) and their FP16 norms (floats)
+  int nrhs;
+  long long v_stride, f_stride, r_bytes, u_bytes, rn_stride, un_stride;
 };
 
 constexpr int SAP_MAX_THREADS = 256;
@@ -895,15 +900,21 @@ __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArg
   const int r_site = h * Hd + i;
   const unsigned fs = h ? fo : fe, bs = h ? bo : be;
 
+  // Right-hand sides share the staged matrices; each has its own input, output and state.
+#pragma unroll 1
+  for (int rhs = 0; rhs < a.nrhs; ++rhs) {
+  float4* const fr = a.faces + rhs * a.f_stride;
+  float* const rnr = a.r_norm ? a.r_norm + rhs * a.rn_stride : nullptr;
+  float* const unr = a.u_norm ? a.u_norm + rhs * a.un_stride : nullptr;
   // 1. residual of site (parity h, index i), with the couplings to the other colour
-  EvenStore<VT> rst{reinterpret_cast<decltype(EvenStore<VT>::p)>(a.r_store), a.r_norm};
+  EvenStore<VT> rst{reinterpret_cast<decltype(EvenStore<VT>::p)>((char*)a.r_store + rhs * a.r_bytes), rnr};
   {
     Spinor<float> r;
-    const SpinorPtr<float> vin{const_cast<float4*>(a.v)};
+    const SpinorPtr<float> vin{const_cast<float4*>(a.v) + rhs * a.v_stride};
     if (a.first) vin.load(g, s_site, r);
     else if (h == 0) rst.load(d, Hd, i, r);
     else zero(r);
-    if (MSMEM) {
+    if (MSMEM && rhs == 0) {
       bool ok = mbar_wait(&mbar, 0, a.wait_ns);
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicExch(a.err, 1);
@@ -914,8 +925,8 @@ __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArg
     if (a.use_faces) {
       Spinor<float> acc;
       zero(acc);
-      if (h) face_hops_rt(g, (int)d, n, lo, fs, bs, r_site, a.faces, M, acc);
-      else face_hops_rt(g, (int)d, n, le, fs, bs, r_site, a.faces, M, acc);
+      if (h) face_hops_rt(g, (int)d, n, lo, fs, bs, r_site, fr, M, acc);
+      else face_hops_rt(g, (int)d, n, le, fs, bs, r_site, fr, M, acc);
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -1014,7 +1025,7 @@ __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArg
   // 5. site (h, i): u += delta, faces of delta
   Spinor<float> dl;
   ld_buf(h ? sO : sE, Hd, i, dl);
-  typename VecPtr<VT>::type ust = VecPtr<VT>::make(a.u_store, a.u_norm);
+  typename VecPtr<VT>::type ust = VecPtr<VT>::make((char*)a.u_store + rhs * a.u_bytes, unr);
   Spinor<float> u;
   if (a.first) {
     u = dl;
@@ -1026,14 +1037,16 @@ __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArg
       for (int c = 0; c < 3; ++c) u.c[s][c] = u.c[s][c] + dl.c[s][c];
   }
   if (a.last) {
-    SpinorPtr<float> zo{a.z};
+    SpinorPtr<float> zo{a.z + rhs * a.v_stride};
     zo.store(g, s_site, u);
   } else {
     ust.store(g, s_site, u);
   }
   if (!(a.last && a.colour == 1)) {
-    if (h) face_write_rt(g, d, lo, fs, bs, r_site, a.faces, M, dl);
-    else face_write_rt(g, d, le, fs, bs, r_site, a.faces, M, dl);
+    if (h) face_write_rt(g, d, lo, fs, bs, r_site, fr, M, dl);
+    else face_write_rt(g, d, le, fs, bs, r_site, fr, M, dl);
+  }
+  __syncthreads();   // the work buffers are reused by the next right-hand side
   }
 }
 
@@ -1105,6 +1118,14 @@ int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int 
   a.v = v;
   a.z = z;
   a.err = S.err;
+  a.nrhs = S.nrhs;
+  a.v_stride = g.V * 6;
+  a.f_stride = (long long)g.ND * g.face_block * 3;
+  a.r_bytes = S.r_bytes;
+  a.u_bytes = S.u_bytes;
+  a.rn_stride = g.V / 2;
+  a.un_stride = g.V;
+  if (S.nrhs > 1 && S.threads_per_site != 2) return -1;   // only the pair kernel loops over right-hand sides
   a.extra_tx = S.inject_wait_timeout ? 16u : 0u;
   a.wait_ns = S.inject_wait_timeout ? 50000000ull : 2000000000ull;
   int grid = g.ND / 2;

@@ -68,6 +68,8 @@ def lib():
             "dd_apply_D": (I, [P, P, P, I, I]),
             "dd_sap_precondition": (I, [P, P, P, C.POINTER(dd_sap_params), I]),
             "dd_sap_precondition_noalloc": (I, [P, P, P, C.POINTER(dd_sap_params)]),
+            "dd_sap_precondition_batch": (I, [P, P, P, I, C.POINTER(dd_sap_params)]),
+            "dd_apply_D_batch": (I, [P, P, P, I, I]),
             "dd_solve": (I, [P, P, P, I, I, C.POINTER(dd_solve_params), C.POINTER(dd_solve_info)]),
             "dd_spinor_bytes": (C.c_size_t, [P, I, I]),
             "dd_pack_spinor": (I, [P, P, I, P, I]),
@@ -139,6 +141,15 @@ class Context:
                             threads_per_site=0):
         p = dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site)
         return self._check(lib().dd_sap_precondition(self._h, _ptr(inp), _ptr(out), C.byref(p), layout))
+
+    def dd_sap_precondition_batch(self, inp, out, nrhs, i_schwarz, i_domain, storage_prec, threads_per_site=0):
+        """nrhs internal-layout FP32 fields one after another; one launch per half-sweep."""
+        p = dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site)
+        return self._check(lib().dd_sap_precondition_batch(self._h, _ptr(inp), _ptr(out), nrhs, C.byref(p)))
+
+    def dd_apply_D_batch(self, inp, out, nrhs, prec):
+        """nrhs internal-layout fields (FP32 or FP16) one after another."""
+        return self._check(lib().dd_apply_D_batch(self._h, _ptr(inp), _ptr(out), nrhs, prec))
 
     def dd_sap_precondition_noalloc(self, inp, out, i_schwarz, i_domain, storage_prec, check=True,
                                     threads_per_site=0):

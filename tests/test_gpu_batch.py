@@ -1,0 +1,64 @@
+"""Several right-hand sides per launch: dd_apply_D_batch and dd_sap_precondition_batch
+against one-at-a-time calls and against the oracle (same bars as the single-field tests)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import wilson as W
+from paper_1412_2629_gb300 import dd
+
+from gpu_helpers import ctx_for, dev, gauge, host, rel
+
+pytestmark = pytest.mark.gpu
+
+DIMS, DOM = (16, 8, 8, 8), (8, 4, 4, 4)
+
+
+def _pack(c, fields, prec):
+    nb = c.dd_spinor_bytes(prec, dd.DD_LAYOUT_INTERNAL)
+    buf = torch.empty(len(fields) * nb, dtype=torch.uint8, device="cuda")
+    for r, f in enumerate(fields):
+        c.dd_pack_spinor(dev(f), dd.DD_PREC_FP64, buf[r * nb:(r + 1) * nb], prec)
+    return buf, nb
+
+
+def _unpack(c, buf, nb, n, prec):
+    out = []
+    for r in range(n):
+        t = torch.empty(DIMS[3], DIMS[2], DIMS[1], DIMS[0], 4, 3, 2, dtype=torch.float64, device="cuda")
+        c.dd_unpack_spinor(buf[r * nb:(r + 1) * nb], prec, t, dd.DD_PREC_FP64)
+        out.append(host(t))
+    return out
+
+
+@pytest.mark.parametrize("prec,tol", [(dd.DD_PREC_FP32, 1e-6), (dd.DD_PREC_FP16, 3e-3)], ids=["fp32", "fp16"])
+def test_apply_batch(prec, tol):
+    U = gauge(DIMS, 0.5, 5)
+    c = ctx_for(DIMS, DOM, U, 0.1360, 1.5)
+    fs = [synth.gaussian_source(DIMS, 200 + r) for r in range(3)]     # odd count: short last pair
+    src, nb = _pack(c, fs, prec)
+    out = torch.empty_like(src)
+    c.dd_apply_D_batch(src, out, len(fs), prec)
+    got = _unpack(c, out, nb, len(fs), prec)
+    for r, f in enumerate(fs):
+        assert rel(got[r], W.apply_A(U, f, 0.1360, 1.5)) <= tol
+        one = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        c.dd_apply_D(src[r * nb:(r + 1) * nb], one, prec, dd.DD_LAYOUT_INTERNAL)
+        assert rel(got[r], _unpack(c, one, nb, 1, prec)[0]) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", [dd.DD_PREC_FP32, dd.DD_PREC_FP16], ids=["fp32", "fp16"])
+def test_sap_batch_equals_single(prec):
+    U = gauge(DIMS, 0.5, 6)
+    c = ctx_for(DIMS, DOM, U, 0.1300, 1.5)
+    fs = [synth.gaussian_source(DIMS, 300 + r) for r in range(3)]
+    src, nb = _pack(c, fs, dd.DD_PREC_FP32)
+    out = torch.empty_like(src)
+    c.dd_sap_precondition_batch(src, out, len(fs), 3, 4, prec)
+    for r in range(len(fs)):
+        one = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        c.dd_sap_precondition(src[r * nb:(r + 1) * nb], one, 3, 4, prec, dd.DD_LAYOUT_INTERNAL)
+        a = out[r * nb:(r + 1) * nb].view(torch.float32).double()
+        b = one.view(torch.float32).double()
+        assert float((a - b).norm() / b.norm()) <= 1e-6
