@@ -221,6 +221,7 @@ def main():
     ap.add_argument("--case", default="solve", choices=["solve", "sap", "dslash"],
                     help="sap / dslash: time one kernel alone on --lattice (kernel studies, ncu captures)")
     ap.add_argument("--lattice", default="32,32,32,64")
+    ap.add_argument("--domain", default="", help="kernel studies: domain shape (default: the workload's)")
     ap.add_argument("--tps", type=int, default=0, help="Schwarz kernel threads per site (0: library default)")
     ap.add_argument("--nrhs", type=int, default=1, help="kernel studies: right-hand sides per launch")
     args = ap.parse_args()
@@ -385,7 +386,8 @@ def kernel_case(args, local):
     from paper_1412_2629_gb300 import dd
     base = synth.WORKLOADS[WORKLOAD]
     dims = tuple(int(v) for v in args.lattice.split(","))
-    w = synth.Workload("case", dims, base.width, base.ape_steps, base.kappa, base.csw, base.domain, base.i_schwarz,
+    dom = tuple(int(v) for v in args.domain.split(",")) if args.domain else base.domain
+    w = synth.Workload("case", dims, base.width, base.ape_steps, base.kappa, base.csw, dom, base.i_schwarz,
                        base.i_domain, base.m, base.k, base.gauge_seed, base.source_seed)
     st = torch.cuda.current_stream()
     U, f = make_inputs(w, "cuda")
