@@ -127,6 +127,12 @@ dd_status dd_sap_precondition(dd_ctx* ctx, const float* in, float* out, const dd
  * fields, two right-hand sides per thread, so each link and clover block is loaded once
  * per pair. */
 dd_status dd_sap_precondition_batch(dd_ctx* ctx, const float* in, float* out, int nrhs, const dd_sap_params* p);
+/* Lattices of different volume in one launch per half-sweep: out_l = M_l in_l for the
+ * nlat <= 4 contexts ctxs[l] (their own gauge fields, clover and kappa), all with the same
+ * domain volume, FP16 storage and two threads per site.  in[l] / out[l]: FP32 internal
+ * fields of lattice l.  Work is issued on ctxs[0]'s stream. */
+dd_status dd_sap_precondition_lattices(dd_ctx** ctxs, const float* const* in, float* const* out, int nlat,
+                                       const dd_sap_params* p);
 dd_status dd_apply_D_batch(dd_ctx* ctx, const void* in, void* out, int nrhs, int prec);
 
 /* out = M in like dd_sap_precondition, but without allocating: the paper has no

@@ -385,6 +385,28 @@ static dd_status ensure_sap(dd_ctx* c, int prec, int nrhs = 1) {
   return DD_OK;
 }
 
+static SapState sap_state(dd_ctx* c, int prec, const dd_sap_params* p, int nrhs) {
+  SapBuffers& b = c->sap[prec];
+  SapState S;
+  S.nrhs = nrhs;
+  S.r_bytes = b.r_bytes;
+  S.u_bytes = b.u_bytes;
+  S.mat_prec = prec;
+  S.vec_prec = prec;
+  S.links = prec == P16 ? (const void*)c->U16 : (const void*)c->U32;
+  S.smat = prec == P16 ? (const void*)c->S16 : (const void*)c->S32;
+  S.r_store = b.r_store;
+  S.r_norm = b.r_norm;
+  S.u_store = b.u_store;
+  S.u_norm = b.u_norm;
+  S.faces = b.faces;
+  S.err = c->sap_err;
+  S.mat_in_smem = sap_mat_fits_smem(c->g, prec);
+  S.threads_per_site = p->threads_per_site ? p->threads_per_site : 2;
+  S.inject_wait_timeout = c->inject_wait_timeout;
+  return S;
+}
+
 static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_params* p, int nrhs = 1) {
   int prec = p->storage_prec == DD_PREC_FP16 ? P16 : P32;
   TRY(ensure_sap(c, prec, nrhs));
@@ -462,6 +484,41 @@ extern "C" dd_status dd_sap_precondition_batch(dd_ctx* c, const float* in, float
   if (p->threads_per_site == 1 && nrhs > 1) return fail(c, DD_ERR_INVALID, "batches need threads_per_site 2");
   TRY(sap_run(c, (const float4*)in, (float4*)out, p, nrhs));
   return sap_error_flag(c);
+}
+
+extern "C" dd_status dd_sap_precondition_lattices(dd_ctx** ctxs, const float* const* in, float* const* out, int nlat,
+                                                  const dd_sap_params* p) {
+  if (!ctxs || !in || !out || nlat < 1 || nlat > 4) return DD_ERR_INVALID;
+  dd_ctx* c0 = ctxs[0];
+  if (!c0) return DD_ERR_INVALID;
+  TRY(check_sap_params(c0, p));
+  if (p->storage_prec != DD_PREC_FP16 || p->threads_per_site == 1 || p->i_domain < 1)
+    return fail(c0, DD_ERR_INVALID, "lattice batches need FP16 storage, two threads per site and i_domain >= 1");
+  Geom gs[4];
+  SapState Ss[4];
+  for (int l = 0; l < nlat; ++l) {
+    dd_ctx* c = ctxs[l];
+    if (!c || !in[l] || !out[l]) return DD_ERR_INVALID;
+    if (!c->have_clover) return fail(c0, DD_ERR_NO_CLOVER, "clover not built on lattice " + std::to_string(l));
+    if (c->g.Vd != c0->g.Vd || c->g.Hd != c0->g.Hd)
+      return fail(c0, DD_ERR_DIMS, "lattices of one launch need the same domain volume");
+    TRY(ensure_sap(c, P16, 1));
+    gs[l] = c->g;
+    Ss[l] = sap_state(c, P16, p, 1);
+    if (Ss[l].mat_in_smem != Ss[0].mat_in_smem) return fail(c0, DD_ERR_DIMS, "mixed domain shapes");
+  }
+  for (int l = 0; l < nlat; ++l) cudaStreamSynchronize(ctxs[l]->st);   // inputs written on the lattices' streams
+  for (int s = 0; s < p->i_schwarz; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      int first = s == 0, use_faces = !(s == 0 && colour == 0), last = s == p->i_schwarz - 1;
+      if (sap_half_sweep_lattices(gs, Ss, nlat, colour, first, use_faces, last, (const float4* const*)in,
+                                  (float4* const*)out, p->i_domain, c0->st))
+        return fail(c0, DD_ERR_CUDA, std::string("Schwarz launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+      TRY(launched(c0));
+    }
+  TRY(cuda_check(c0, cudaStreamSynchronize(c0->st), "sap_lattices"));
+  for (int l = 0; l < nlat; ++l) TRY(sap_error_flag(ctxs[l]));
+  return DD_OK;
 }
 
 extern "C" dd_status dd_apply_D_batch(dd_ctx* c, const void* in, void* out, int nrhs, int prec) {

@@ -68,6 +68,9 @@ struct SapState {
 // face buffers; last: write u (FP32) into z.
 int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int use_faces, int last,
                    const float4* v, float4* z, int i_domain, cudaStream_t st);
+// Several lattices (same domain shape, FP16 storage) in one launch per half-sweep.
+int sap_half_sweep_lattices(const Geom* gs, const SapState* Ss, int nlat, int colour, int first, int use_faces,
+                            int last, const float4* const* v, float4* const* z, int i_domain, cudaStream_t st);
 size_t sap_smem_bytes(const Geom& g, int mat_prec, bool mat_in_smem);
 bool sap_mat_fits_smem(const Geom& g, int mat_prec);
 int sap_max_domain_sites();

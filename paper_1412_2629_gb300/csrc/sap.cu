@@ -834,8 +834,9 @@ __device__ inline void hops_half_mask(int h, const Geom& g, unsigned fwd, unsign
 //   phase 2k+1:       odd sites,  src = rho      -> t = A_oo^{-1} H rho
 //   phase 2k+2:       even sites, src = t        -> p = A_ee rho - 1/4 H t, MR step
 //   phase 2 I_d + 1:  odd sites,  src = x        -> delta_o = A_oo^{-1} (r_o + 1/2 H x)
+// cta: index of the domain among the domains of the given colour.
 template <typename MT, typename VT, bool MSMEM>
-__global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArgs a) {
+__device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   const Geom& g = a.g;
   extern __shared__ float4 smem[];
   __shared__ uint64_t mbar;
@@ -849,8 +850,8 @@ __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArg
   int n[4];
   {
     int hx = g.N[0] >> 1;
-    int j = blockIdx.x % hx;
-    int row = blockIdx.x / hx;
+    int j = cta % hx;
+    int row = cta / hx;
     n[1] = row % g.N[1];
     n[2] = (row / g.N[1]) % g.N[2];
     n[3] = row / (g.N[1] * g.N[2]);
@@ -1050,6 +1051,32 @@ __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArg
   }
 }
 
+template <typename MT, typename VT, bool MSMEM>
+__global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArgs a) {
+  sap_pair_body<MT, VT, MSMEM>(a, blockIdx.x);
+}
+
+// Several lattices of the same domain shape in one launch: the grid is the concatenation
+// of every lattice's domains of the colour; lattice l owns CTAs first[l] .. first[l+1]-1.
+constexpr int SAP_MAX_LATTICES = 4;
+struct SapLattices {
+  SapArgs lat[SAP_MAX_LATTICES];
+  int first[SAP_MAX_LATTICES + 1];
+  int nlat;
+};
+
+template <typename MT, typename VT, bool MSMEM>
+__global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair_lattices(SapLattices m) {
+  int l = 0;
+  while (l + 1 < m.nlat && (int)blockIdx.x >= m.first[l + 1]) ++l;
+  switch (l) {   // constant indices keep the arguments in the parameter space
+    case 0: sap_pair_body<MT, VT, MSMEM>(m.lat[0], blockIdx.x - m.first[0]); break;
+    case 1: sap_pair_body<MT, VT, MSMEM>(m.lat[1], blockIdx.x - m.first[1]); break;
+    case 2: sap_pair_body<MT, VT, MSMEM>(m.lat[2], blockIdx.x - m.first[2]); break;
+    default: sap_pair_body<MT, VT, MSMEM>(m.lat[3], blockIdx.x - m.first[3]); break;
+  }
+}
+
 size_t sap_smem_bytes(const Geom& g, int mat_prec, bool mat_in_smem) {
   size_t vec = (size_t)2 * 6 * g.Hd * 16;
   if (!mat_in_smem) return vec;
@@ -1098,9 +1125,63 @@ static int launch_one(const SapArgs& a, int grid, int pair, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
+static SapArgs make_args(const Geom& g, const SapState& S, int colour, int first, int use_faces, int last,
+                         const float4* v, float4* z, int i_domain);
+
+// All lattices' domains of one colour in one launch (FP16 storage, two threads per site,
+// same domain shape everywhere).
+int sap_half_sweep_lattices(const Geom* gs, const SapState* Ss, int nlat, int colour, int first, int use_faces,
+                            int last, const float4* const* v, float4* const* z, int i_domain, cudaStream_t st) {
+  if (nlat < 1 || nlat > SAP_MAX_LATTICES) return -1;
+  SapLattices m;
+  m.nlat = nlat;
+  int total = 0;
+  for (int l = 0; l < nlat; ++l) {
+    const Geom& g = gs[l];
+    if (g.Hd != gs[0].Hd || g.Hd > SAP_MAX_THREADS || (g.Hd & 31) || Ss[l].mat_prec != P16 || Ss[l].vec_prec != P16 ||
+        Ss[l].mat_in_smem != Ss[0].mat_in_smem)
+      return -1;
+    m.lat[l] = make_args(g, Ss[l], colour, first, use_faces, last, v[l], z[l], i_domain);
+    m.first[l] = total;
+    total += g.ND / 2;
+  }
+  m.first[nlat] = total;
+  const bool ms = Ss[0].mat_in_smem;
+  size_t smem = sap_smem_bytes(gs[0], P16, ms);
+  if (ms) {
+    static int configured = 0;
+    if (!configured) {
+      cudaFuncSetAttribute(sap_kernel_pair_lattices<__half, __half, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem_optin() - 4096);
+      configured = 1;
+    }
+    sap_kernel_pair_lattices<__half, __half, true><<<total, 2 * gs[0].Hd, smem, st>>>(m);
+  } else {
+    sap_kernel_pair_lattices<__half, __half, false><<<total, 2 * gs[0].Hd, smem, st>>>(m);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
 int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int use_faces, int last,
                    const float4* v, float4* z, int i_domain, cudaStream_t st) {
   if (g.Hd > SAP_MAX_THREADS || (g.Hd & 31)) return -1;
+  if (S.nrhs > 1 && S.threads_per_site != 2) return -1;   // only the pair kernel loops over right-hand sides
+  SapArgs a = make_args(g, S, colour, first, use_faces, last, v, z, i_domain);
+  int grid = g.ND / 2;
+  bool ms = S.mat_in_smem;
+  int pr = S.threads_per_site == 2;
+  if (S.mat_prec == P16) {
+    if (S.vec_prec == P16)
+      return ms ? launch_one<__half, __half, true>(a, grid, pr, st) : launch_one<__half, __half, false>(a, grid, pr, st);
+    return ms ? launch_one<__half, float, true>(a, grid, pr, st) : launch_one<__half, float, false>(a, grid, pr, st);
+  }
+  if (S.vec_prec == P16)
+    return ms ? launch_one<float, __half, true>(a, grid, pr, st) : launch_one<float, __half, false>(a, grid, pr, st);
+  return ms ? launch_one<float, float, true>(a, grid, pr, st) : launch_one<float, float, false>(a, grid, pr, st);
+}
+
+static SapArgs make_args(const Geom& g, const SapState& S, int colour, int first, int use_faces, int last,
+                         const float4* v, float4* z, int i_domain) {
   SapArgs a;
   a.g = g;
   a.colour = colour;
@@ -1125,20 +1206,9 @@ int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int 
   a.u_bytes = S.u_bytes;
   a.rn_stride = g.V / 2;
   a.un_stride = g.V;
-  if (S.nrhs > 1 && S.threads_per_site != 2) return -1;   // only the pair kernel loops over right-hand sides
   a.extra_tx = S.inject_wait_timeout ? 16u : 0u;
   a.wait_ns = S.inject_wait_timeout ? 50000000ull : 2000000000ull;
-  int grid = g.ND / 2;
-  bool ms = S.mat_in_smem;
-  int pr = S.threads_per_site == 2;
-  if (S.mat_prec == P16) {
-    if (S.vec_prec == P16)
-      return ms ? launch_one<__half, __half, true>(a, grid, pr, st) : launch_one<__half, __half, false>(a, grid, pr, st);
-    return ms ? launch_one<__half, float, true>(a, grid, pr, st) : launch_one<__half, float, false>(a, grid, pr, st);
-  }
-  if (S.vec_prec == P16)
-    return ms ? launch_one<float, __half, true>(a, grid, pr, st) : launch_one<float, __half, false>(a, grid, pr, st);
-  return ms ? launch_one<float, float, true>(a, grid, pr, st) : launch_one<float, float, false>(a, grid, pr, st);
+  return a;
 }
 
 }  // namespace dd

@@ -70,6 +70,8 @@ def lib():
             "dd_sap_precondition_noalloc": (I, [P, P, P, C.POINTER(dd_sap_params)]),
             "dd_sap_precondition_batch": (I, [P, P, P, I, C.POINTER(dd_sap_params)]),
             "dd_apply_D_batch": (I, [P, P, P, I, I]),
+            "dd_sap_precondition_lattices": (I, [C.POINTER(P), C.POINTER(P), C.POINTER(P), I,
+                                                 C.POINTER(dd_sap_params)]),
             "dd_solve": (I, [P, P, P, I, I, C.POINTER(dd_solve_params), C.POINTER(dd_solve_info)]),
             "dd_spinor_bytes": (C.c_size_t, [P, I, I]),
             "dd_pack_spinor": (I, [P, P, I, P, I]),
@@ -184,6 +186,18 @@ class Context:
         p = dd_sap_params(i_schwarz, 0, storage_prec)
         self._check(lib().dd_autotune(self._h, storage_prec, dom, C.byref(p)))
         return tuple(dom), (p.i_schwarz, p.i_domain, p.storage_prec, p.threads_per_site)
+
+
+def dd_sap_precondition_lattices(ctxs, ins, outs, i_schwarz, i_domain, storage_prec=DD_PREC_FP16):
+    """One Schwarz launch per half-sweep over several lattices (internal FP32 fields)."""
+    n = len(ctxs)
+    hs = (C.c_void_p * n)(*[c._h.value for c in ctxs])
+    pi = (C.c_void_p * n)(*[_ptr(x) for x in ins])
+    po = (C.c_void_p * n)(*[_ptr(x) for x in outs])
+    p = dd_sap_params(i_schwarz, i_domain, storage_prec, 0)
+    s = lib().dd_sap_precondition_lattices(hs, pi, po, n, C.byref(p))
+    if s != DD_OK:
+        raise DDError(s, lib().dd_last_error(ctxs[0]._h).decode())
 
 
 def dd_load_model(n_domains_per_colour, slots):

@@ -62,3 +62,27 @@ def test_sap_batch_equals_single(prec):
         a = out[r * nb:(r + 1) * nb].view(torch.float32).double()
         b = one.view(torch.float32).double()
         assert float((a - b).norm() / b.norm()) <= 1e-6
+
+
+def test_sap_lattices_in_one_launch_equal_single():
+    """Three lattices of different volume (own gauge field, clover and kappa) in one launch
+    per half-sweep give what each lattice gives alone."""
+    shapes = [((8, 8, 8, 8), 0.1250, 41), ((8, 8, 8, 16), 0.1300, 42), ((16, 8, 8, 8), 0.1350, 43)]
+    ctxs, ins, outs, refs = [], [], [], []
+    for dims, kappa, seed in shapes:
+        U = gauge(dims, 0.5, seed)
+        c = ctx_for(dims, (4, 4, 4, 4), U, kappa, 1.5)
+        f = synth.gaussian_source(dims, seed + 1)
+        nb = c.dd_spinor_bytes(dd.DD_PREC_FP32, dd.DD_LAYOUT_INTERNAL)
+        src = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        c.dd_pack_spinor(dev(f), dd.DD_PREC_FP64, src, dd.DD_PREC_FP32)
+        ref = torch.empty_like(src)
+        c.dd_sap_precondition(src, ref, 3, 4, dd.DD_PREC_FP16, dd.DD_LAYOUT_INTERNAL)
+        ctxs.append(c)
+        ins.append(src)
+        outs.append(torch.empty_like(src))
+        refs.append(ref)
+    dd.dd_sap_precondition_lattices(ctxs, ins, outs, 3, 4)
+    for o, r in zip(outs, refs):
+        a, b = o.view(torch.float32).double(), r.view(torch.float32).double()
+        assert float((a - b).norm() / b.norm()) <= 1e-6
