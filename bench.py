@@ -218,7 +218,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-mixed", action="store_true", help="time the mixed solve only (profiling runs)")
-    ap.add_argument("--case", default="solve", choices=["solve", "sap", "dslash"],
+    ap.add_argument("--case", default="solve", choices=["solve", "sap", "dslash", "sap_lattices"],
                     help="sap / dslash: time one kernel alone on --lattice (kernel studies, ncu captures)")
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--domain", default="", help="kernel studies: domain shape (default: the workload's)")
@@ -246,6 +246,8 @@ def main():
     from paper_1412_2629_gb300 import build as B
     B.build()
     from paper_1412_2629_gb300 import dd
+    if args.case == "sap_lattices":
+        return lattices_case(args)
     if args.case != "solve":
         return kernel_case(args, local)
 
@@ -440,6 +442,53 @@ def kernel_case(args, local):
                "ms_per_rhs": 1e3 * launch_s / nr,
                "gbs_algorithmic": per_site * V * nr / launch_s / 1e9}
     print(json.dumps(out))
+
+
+def lattices_case(args):
+    """The uneven batch of the fifth workload: 16^3x32, 24^3x48 and 32^3x64 (kappa 0.134,
+    0.135, 0.1355, c_sw 1.5, 4^4 domains), one Schwarz application each, timed as one
+    launch per half-sweep over all three lattices and as three separate calls."""
+    import torch
+
+    import synth
+    from paper_1412_2629_gb300 import dd
+    base = synth.WORKLOADS[WORKLOAD]
+    st = torch.cuda.current_stream()
+    specs = [((16, 16, 16, 32), 0.1340, 151), ((24, 24, 24, 48), 0.1350, 152), ((32, 32, 32, 64), 0.1355, 153)]
+    ctxs, ins, outs, vols = [], [], [], []
+    for dims, kappa, seed in specs:
+        w = synth.Workload("lat", dims, base.width, base.ape_steps, kappa, 1.5, (4, 4, 4, 4), base.i_schwarz,
+                           base.i_domain, base.m, base.k, seed, seed + 10)
+        U, f = make_inputs(w, "cuda")
+        c = dd.Context(dims, (4, 4, 4, 4), True, st.cuda_stream)
+        c.dd_load_gauge(torch.view_as_real(U).contiguous(), dd.DD_DEVICE)
+        c.dd_build_clover(kappa, 1.5)
+        del U
+        nb = c.dd_spinor_bytes(dd.DD_PREC_FP32, dd.DD_LAYOUT_INTERNAL)
+        a = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        c.dd_pack_spinor(torch.view_as_real(torch.from_numpy(f)).float().cuda().contiguous(), dd.DD_PREC_FP32, a,
+                         dd.DD_PREC_FP32)
+        ctxs.append(c); ins.append(a); outs.append(torch.empty_like(a)); vols.append(int(np.prod(dims)))
+    i_s, i_d = base.i_schwarz, base.i_domain
+    one = lambda: dd.dd_sap_precondition_lattices(ctxs, ins, outs, i_s, i_d)
+    sep = lambda: [c.dd_sap_precondition(a, o, i_s, i_d, dd.DD_PREC_FP16, dd.DD_LAYOUT_INTERNAL)
+                   for c, a, o in zip(ctxs, ins, outs)]
+    res = {}
+    for name, fn in (("one_launch", one), ("separate", sep)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        res[name + "_ms"] = e0.elapsed_time(e1) / args.steps
+    useful, _ = sap_visit_flops((4, 4, 4, 4), i_d)
+    res["tflops_one_launch"] = useful * sum(vols) * i_s / (res["one_launch_ms"] / 1e3) / 1e12
+    res["case"] = "sap_lattices 16^3x32 + 24^3x48 + 32^3x64"
+    print(json.dumps(res))
 
 
 if __name__ == "__main__":

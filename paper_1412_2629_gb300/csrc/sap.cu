@@ -1170,13 +1170,10 @@ int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int 
   int grid = g.ND / 2;
   bool ms = S.mat_in_smem;
   int pr = S.threads_per_site == 2;
-  if (S.mat_prec == P16) {
-    if (S.vec_prec == P16)
-      return ms ? launch_one<__half, __half, true>(a, grid, pr, st) : launch_one<__half, __half, false>(a, grid, pr, st);
-    return ms ? launch_one<__half, float, true>(a, grid, pr, st) : launch_one<__half, float, false>(a, grid, pr, st);
-  }
-  if (S.vec_prec == P16)
-    return ms ? launch_one<float, __half, true>(a, grid, pr, st) : launch_one<float, __half, false>(a, grid, pr, st);
+  // matrices and vectors are stored in the same precision (FP16 or FP32)
+  if (S.mat_prec != S.vec_prec) return -1;
+  if (S.mat_prec == P16)
+    return ms ? launch_one<__half, __half, true>(a, grid, pr, st) : launch_one<__half, __half, false>(a, grid, pr, st);
   return ms ? launch_one<float, float, true>(a, grid, pr, st) : launch_one<float, float, false>(a, grid, pr, st);
 }
 
