@@ -72,7 +72,7 @@ typedef struct {
 /* Outer solver parameters (flexible GMRES with deflated restarts, Table I). */
 typedef struct {
   double tol;         /* target |f - A x| / |f|, recomputed in FP64 (paper: 1e-10) */
-  int m;              /* basis size, 1 <= m <= 64 */
+  int m;              /* basis size, 1 <= m <= 63 (else DD_ERR_INVALID) */
   int k;              /* deflation vectors kept at a restart, 0 <= k < m */
   int max_iter;       /* total Arnoldi steps allowed */
   dd_sap_params sap;

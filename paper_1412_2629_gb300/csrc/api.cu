@@ -50,6 +50,8 @@ struct SolverBuffers {
   int m = 0;                 // capacity (basis size)
   cudaStream_t stream = nullptr;       // private stream of dd_solve (capturable)
   cudaEvent_t ev_in = nullptr;
+  cudaStream_t side = nullptr;         // second branch of an Arnoldi step (small dense work)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::map<GraphKey, GraphEntry> graphs;
   float4* V[2] = {nullptr, nullptr};   // (m+1) vectors each, double-buffered for restarts
   float4* Z[2] = {nullptr, nullptr};   // m vectors each
@@ -617,7 +619,9 @@ static void release_solver(dd_ctx* c) {
   for (auto& kv : s.graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   if (s.stream) cudaStreamDestroy(s.stream);
-  if (s.ev_in) cudaEventDestroy(s.ev_in);
+  if (s.side) cudaStreamDestroy(s.side);
+  for (cudaEvent_t e : {s.ev_in, s.ev_fork, s.ev_join})
+    if (e) cudaEventDestroy(e);
   s = SolverBuffers();
 }
 
@@ -659,7 +663,10 @@ static dd_status ensure_solver(dd_ctx* c, int m) {
     if (cudaMallocHost(p, (m + 2) * sizeof(zd)) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned deflation buffers");
   s.h_dw = new DeflateWork();
   if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s.ev_in, cudaEventDisableTiming) != cudaSuccess)
+      cudaStreamCreateWithFlags(&s.side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s.ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s.ev_join, cudaEventDisableTiming) != cudaSuccess)
     return fail(c, DD_ERR_CUDA, "solver stream");
   s.m = m;
   return DD_OK;
@@ -795,9 +802,15 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
         launch_gs_project(vn, vn, Vv(0), j + 1, n4, (const double2*)s.hB, s.partial2, s.flag, 1, c->st);
         launch_gs_reduce(s.partial2, 0, nrm_b, s.flag, 1, c->st);
         gs_decide2_kernel<<<1, 1, 0, c->st>>>(s.flag, nrm_b, s.nu2);
+        // the Hessenberg column and its Givens update (one thread) run beside the
+        // normalisation of the new basis vector; both only read nu2
+        cudaEventRecord(s.ev_fork, c->st);
+        cudaStreamWaitEvent(s.side, s.ev_fork, 0);
+        arnoldi_finish_kernel<<<1, 1, 0, s.side>>>(s.H, s.R, ldh, j, s.hA, s.hB, s.nu2, s.lsq, s.g, s.status);
+        cudaEventRecord(s.ev_join, s.side);
         launch_scale_inplace(vn, n4, s.nu2, c->st);
-        arnoldi_finish_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, j, s.hA, s.hB, s.nu2, s.lsq, s.g, s.status);
-        return launched(c, nk + 11);
+        cudaStreamWaitEvent(c->st, s.ev_join, 0);
+        return launched(c, nk + 10);
       }));
       cudaEventRecord(e3, c->st);
       TRY(read_status(c));

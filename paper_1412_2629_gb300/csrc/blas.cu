@@ -215,42 +215,63 @@ void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2*
   r64_to_v32_kernel<<<blas_partials_blocks(), BT, 0, st>>>(v, r, n4, nrm2);
 }
 
-// out_l = sum_i P[i + l ldp] V_i for l < nout (P complex FP64, column-major).
+// out_l = sum_i P[i + l ldp] V_i for l < nout (P complex FP64, column-major).  One pass
+// produces up to NO outputs, so a deflated restart of k <= 15 reads each basis once; the
+// loop over inputs takes two at a time to keep two loads in flight per thread.
 template <int NO>
-__global__ void __launch_bounds__(BT) recombine_kernel(float4* out, const float4* V, int nv, int l0, int nout, long long n4,
-                                                       const double2* P, int ldp) {
+__global__ void __launch_bounds__(BT) recombine_kernel(float4* out, const float4* __restrict__ V, int nv, int l0,
+                                                       int nout, long long n4, const double2* P, int ldp) {
   __shared__ float2 ps[64][NO];
+  const int nl = min(NO, nout - l0);
   for (int t = threadIdx.x; t < nv * NO; t += BT) {
     int i = t / NO, l = t % NO;
-    ps[i][l] = l0 + l < nout ? make_float2((float)P[i + (long long)(l0 + l) * ldp].x, (float)P[i + (long long)(l0 + l) * ldp].y)
-                             : make_float2(0.f, 0.f);
+    ps[i][l] = l < nl ? make_float2((float)P[i + (long long)(l0 + l) * ldp].x, (float)P[i + (long long)(l0 + l) * ldp].y)
+                      : make_float2(0.f, 0.f);
   }
   __syncthreads();
   for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n4; q += (long long)gridDim.x * BT) {
     float4 a[NO];
 #pragma unroll
     for (int l = 0; l < NO; ++l) a[l] = make_float4(0, 0, 0, 0);
-    for (int i = 0; i < nv; ++i) {
-      float4 v = V[(long long)i * n4 + q];
+    auto fma_in = [&](int i, float4 v) {
 #pragma unroll
       for (int l = 0; l < NO; ++l) {
-        float2 c = ps[i][l];
-        a[l].x += c.x * v.x - c.y * v.y;
-        a[l].y += c.x * v.y + c.y * v.x;
-        a[l].z += c.x * v.z - c.y * v.w;
-        a[l].w += c.x * v.w + c.y * v.z;
+        if (l < nl) {
+          float2 c = ps[i][l];
+          a[l].x += c.x * v.x - c.y * v.y;
+          a[l].y += c.x * v.y + c.y * v.x;
+          a[l].z += c.x * v.z - c.y * v.w;
+          a[l].w += c.x * v.w + c.y * v.z;
+        }
       }
+    };
+    int i = 0;
+    for (; i + 1 < nv; i += 2) {
+      float4 v0 = V[(long long)i * n4 + q], v1 = V[(long long)(i + 1) * n4 + q];
+      fma_in(i, v0);
+      fma_in(i + 1, v1);
     }
+    if (i < nv) fma_in(i, V[(long long)i * n4 + q]);
 #pragma unroll
     for (int l = 0; l < NO; ++l)
-      if (l0 + l < nout) out[(long long)(l0 + l) * n4 + q] = a[l];
+      if (l < nl) out[(long long)(l0 + l) * n4 + q] = a[l];
   }
 }
 int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n4, const double2* P, int ldp,
                      cudaStream_t st) {
   int n = 0;
-  for (int l0 = 0; l0 < nout; l0 += 8, ++n)
-    recombine_kernel<8><<<blas_partials_blocks(), BT, 0, st>>>(out, V, nv, l0, nout, n4, P, ldp);
+  const int nb = blas_partials_blocks();
+  for (int l0 = 0; l0 < nout; l0 += 16, ++n) {
+    const int nl = nout - l0 < 16 ? nout - l0 : 16;
+    if (nl <= 4)
+      recombine_kernel<4><<<nb, BT, 0, st>>>(out, V, nv, l0, nout, n4, P, ldp);
+    else if (nl <= 8)
+      recombine_kernel<8><<<nb, BT, 0, st>>>(out, V, nv, l0, nout, n4, P, ldp);
+    else if (nl <= 12)
+      recombine_kernel<12><<<nb, BT, 0, st>>>(out, V, nv, l0, nout, n4, P, ldp);
+    else
+      recombine_kernel<16><<<nb, BT, 0, st>>>(out, V, nv, l0, nout, n4, P, ldp);
+  }
   return n;
 }
 
@@ -278,32 +299,62 @@ void launch_axpy_64(double2* x, const double2* y, double a, long long n2, cudaSt
 
 namespace dd {
 
-// ------------------------------------------------------------------ single-pass Gram-Schmidt
+// ------------------------------------------------------------------ Gram-Schmidt passes
 // Classical Gram-Schmidt with selective reorthogonalisation, gated on the device so no
-// host round trip is needed.  Pass 1 forms h = V^H w and |w|^2 in one read of the basis.
-// The norm of the projected vector follows from Pythagoras, nu^2 = |w|^2 - |h|^2; when
-// that cancels by less than half (nu^2 >= |w|^2 / 2) one projection is accurate to FP32
-// rounding and the new basis vector (w - V h) / nu is written in a single fused pass.
-// Otherwise the projection is repeated once (the classical "twice is enough" rule).
-template <int NV>
-__global__ void __launch_bounds__(BT) gs_dot_kernel(const float4* V, int v0, int nv, long long n4, const float4* w,
-                                                    double2* partial, int ldp, const int* gate, int want) {
+// host round trip is needed.  Pass 1 forms h = V^H w and |w|^2 in one read of the basis;
+// the projection pass writes w - V h and its exact squared norm; a second projection runs
+// only when the first cancelled more than half of |w|^2.
+//
+// One launch covers every basis vector.  Block b takes the chunk b % nch of NV vectors
+// and the q-slice b / nch, so blocks that read the same elements of w are adjacent in
+// launch order and all but the first find them in L2.  Each loop trip handles U elements
+// per vector, (NV + 1) * U independent 16-byte loads per thread, which keeps enough bytes
+// in flight for HBM even for the short last chunk.
+template <int NV, int U>
+__global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const float4* __restrict__ V, int nv, int nch, long long n4,
+                                                       const float4* __restrict__ w, double2* partial, int ldp,
+                                                       const int* gate, int want) {
   if (gate && *gate != want) return;
+  const int chunk = blockIdx.x % nch, qb = blockIdx.x / nch, nqb = gridDim.x / nch;
+  const int v0 = chunk * NV, nvc = min(NV, nv - v0);
+  const bool self = chunk == 0;
   float re[NV], im[NV], ww = 0.f;
 #pragma unroll
   for (int i = 0; i < NV; ++i) re[i] = im[i] = 0.f;
-  const bool self = v0 == 0;
-  for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n4; q += (long long)gridDim.x * BT) {
+  const long long stride = (long long)nqb * BT;
+  const float4* Vc = V + (long long)v0 * n4;
+  long long q = (long long)qb * BT + threadIdx.x;
+  for (; q + (U - 1) * stride < n4; q += U * stride) {
+    float4 wq[U], vq[NV][U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) wq[u] = w[q + u * stride];
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (i < nvc)
+#pragma unroll
+        for (int u = 0; u < U; ++u) vq[i][u] = Vc[(long long)i * n4 + q + u * stride];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (self) ww += wq[u].x * wq[u].x + wq[u].y * wq[u].y + wq[u].z * wq[u].z + wq[u].w * wq[u].w;
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (i < nvc) {
+          cx<float> d = dot4(vq[i][u], wq[u]);
+          re[i] += d.re;
+          im[i] += d.im;
+        }
+    }
+  }
+  for (; q < n4; q += stride) {
     float4 wq = w[q];
     if (self) ww += wq.x * wq.x + wq.y * wq.y + wq.z * wq.z + wq.w * wq.w;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      if (v0 + i < nv) {
-        cx<float> d = dot4(V[(long long)(v0 + i) * n4 + q], wq);
+    for (int i = 0; i < NV; ++i)
+      if (i < nvc) {
+        cx<float> d = dot4(Vc[(long long)i * n4 + q], wq);
         re[i] += d.re;
         im[i] += d.im;
       }
-    }
   }
   double2 acc[NV + 1];
 #pragma unroll
@@ -311,18 +362,16 @@ __global__ void __launch_bounds__(BT) gs_dot_kernel(const float4* V, int v0, int
   acc[NV] = make_double2(ww, 0.0);
   __shared__ double2 out[NV + 1];
   block_reduce<NV + 1>(acc, out);
-  if (threadIdx.x < NV && v0 + (int)threadIdx.x < nv) partial[(long long)blockIdx.x * ldp + v0 + threadIdx.x] = out[threadIdx.x];
-  if (self && threadIdx.x == 0) partial[(long long)blockIdx.x * ldp + nv] = out[NV];
+  if ((int)threadIdx.x < nvc) partial[(long long)qb * ldp + v0 + threadIdx.x] = out[threadIdx.x];
+  if (self && threadIdx.x == 0) partial[(long long)qb * ldp + nv] = out[NV];
 }
 
-// partial layout [block][nv + 1]: entries 0..nv-1 are V^H w, entry nv is |w|^2.
+// partial layout [q-slice][nv + 1]: entries 0..nv-1 are V^H w, entry nv is |w|^2.
 int launch_gs_dot(const float4* V, int nv, long long n4, const float4* w, double2* partial, const int* gate, int want,
                   cudaStream_t st) {
-  int nb = blas_partials_blocks(), n = 0;
-  // 8 basis vectors per pass: 16 per pass needs 124 registers and halves the bandwidth
-  for (int v0 = 0; v0 < (nv > 0 ? nv : 1); v0 += 8, ++n)
-    gs_dot_kernel<8><<<nb, BT, 0, st>>>(V, v0, nv, n4, w, partial, nv + 1, gate, want);
-  return n;
+  const int nch = nv > 0 ? (nv + 7) / 8 : 1;
+  gs_dot_kernel<8, 2><<<blas_partials_blocks() * nch, BT, 0, st>>>(V, nv, nch, n4, w, partial, nv + 1, gate, want);
+  return 1;
 }
 
 __global__ void gs_reduce_kernel(const double2* partial, int nb, int ld, double2* out, const int* gate, int want) {
@@ -344,38 +393,6 @@ __global__ void gs_reduce_kernel(const double2* partial, int nb, int ld, double2
 void launch_gs_reduce(const double2* partial, int nv, double2* out, const int* gate, int want, cudaStream_t st) {
   gs_reduce_kernel<<<nv + 1, 256, 0, st>>>(partial, blas_partials_blocks(), nv + 1, out, gate, want);
 }
-
-// nu2 == nullptr: w -= V h in place.  Otherwise out = (w - V h) / sqrt(*nu2).
-__global__ void __launch_bounds__(BT) gs_axpy_kernel(float4* out, float4* w, const float4* V, int nv, long long n4,
-                                                     const double2* h, const double* nu2, const int* gate, int want) {
-  if (gate && *gate != want) return;
-  __shared__ float2 hs[64];
-  for (int i = threadIdx.x; i < nv; i += BT) hs[i] = make_float2((float)h[i].x, (float)h[i].y);
-  __syncthreads();
-  const float s = nu2 ? (float)(1.0 / sqrt(*nu2)) : 1.f;
-  float4* dst = nu2 ? out : w;
-  for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n4; q += (long long)gridDim.x * BT) {
-    float4 a = w[q];
-    for (int i = 0; i < nv; ++i) {
-      float4 v = V[(long long)i * n4 + q];
-      float2 c = hs[i];
-      a.x -= c.x * v.x - c.y * v.y;
-      a.y -= c.x * v.y + c.y * v.x;
-      a.z -= c.x * v.z - c.y * v.w;
-      a.w -= c.x * v.w + c.y * v.z;
-    }
-    dst[q] = make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
-  }
-}
-
-void launch_gs_axpy(float4* out, float4* w, const float4* V, int nv, long long n4, const double2* h, const double* nu2,
-                    const int* gate, int want, cudaStream_t st) {
-  gs_axpy_kernel<<<blas_partials_blocks(), BT, 0, st>>>(out, w, V, nv, n4, h, nu2, gate, want);
-}
-
-}  // namespace dd
-
-namespace dd {
 
 // out = w - V h with |out|^2 partials per block (exact norm of the projected vector).
 // in_place: out aliases w.

@@ -95,13 +95,11 @@ int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n
 void launch_copy64_to32(float4* out, const double2* in, long long n4, cudaStream_t st);
 void launch_axpy_64(double2* x, const double2* y, double a, long long n2, cudaStream_t st);
 
-// Single-pass Gram-Schmidt with device-gated reorthogonalisation (blas.cu).  A kernel
+// Classical Gram-Schmidt passes with device-gated reorthogonalisation (blas.cu).  A kernel
 // given a gate runs only when *gate == want.
 int launch_gs_dot(const float4* V, int nv, long long n4, const float4* w, double2* partial, const int* gate, int want,
                   cudaStream_t st);
 void launch_gs_reduce(const double2* partial, int nv, double2* out, const int* gate, int want, cudaStream_t st);
-void launch_gs_axpy(float4* out, float4* w, const float4* V, int nv, long long n4, const double2* h, const double* nu2,
-                    const int* gate, int want, cudaStream_t st);
 void launch_gs_project(float4* out, const float4* w, const float4* V, int nv, long long n4, const double2* h,
                        double2* norm_partial, const int* gate, int want, cudaStream_t st);
 void launch_scale_inplace(float4* v, long long n4, const double* nu2, cudaStream_t st);
