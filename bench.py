@@ -218,12 +218,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-mixed", action="store_true", help="time the mixed solve only (profiling runs)")
-    ap.add_argument("--case", default="solve", choices=["solve", "sap", "dslash", "sap_lattices"],
+    ap.add_argument("--case", default="solve", choices=["solve", "sap", "dslash", "sap_lattices", "workload_solve"],
                     help="sap / dslash: time one kernel alone on --lattice (kernel studies, ncu captures)")
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--domain", default="", help="kernel studies: domain shape (default: the workload's)")
     ap.add_argument("--tps", type=int, default=0, help="Schwarz kernel threads per site (0: library default)")
     ap.add_argument("--nrhs", type=int, default=1, help="kernel studies: right-hand sides per launch")
+    ap.add_argument("--workload", default="48^3x96", help="workload_solve: the workload to solve once")
+    ap.add_argument("--m", type=int, default=0, help="workload_solve: basis size (0: the workload's)")
     args = ap.parse_args()
     if not args.only_mixed:
         args.warmup = max(args.warmup, 3)   # profiling runs (--only-mixed) may skip the warm-up
@@ -248,6 +250,8 @@ def main():
     from paper_1412_2629_gb300 import dd
     if args.case == "sap_lattices":
         return lattices_case(args)
+    if args.case == "workload_solve":
+        return workload_case(args)
     if args.case != "solve":
         return kernel_case(args, local)
 
@@ -489,6 +493,50 @@ def lattices_case(args):
     res["tflops_one_launch"] = useful * sum(vols) * i_s / (res["one_launch_ms"] / 1e3) / 1e12
     res["case"] = "sap_lattices 16^3x32 + 24^3x48 + 32^3x64"
     print(json.dumps(res))
+
+
+def workload_case(args):
+    """One mixed-precision solve of a named workload (the larger lattices: 48^3x96,
+    64^3x128), device-resident f and x, with the times of input generation, set-up and
+    solve; the true residual is the library's FP64 recomputation."""
+    import torch
+
+    import synth
+    from paper_1412_2629_gb300 import dd
+    w = synth.WORKLOADS[args.workload]
+    st = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    U = synth.random_su3_field(w.dims, w.width, w.gauge_seed, device="cuda")
+    torch.cuda.synchronize()
+    t_rand = time.perf_counter() - t0
+    if w.ape_steps:
+        U = synth.ape_smear(U, 0.5, w.ape_steps)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    f = synth.make_sources(w)[0]
+    ctx = dd.Context(w.dims, w.domain, True, st.cuda_stream)
+    t1 = time.perf_counter()
+    ctx.dd_load_gauge(torch.view_as_real(U).contiguous(), dd.DD_DEVICE)
+    ctx.dd_build_clover(w.kappa, w.csw)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t1
+    del U
+    torch.cuda.empty_cache()   # the generator's temporaries, before the solver allocates its basis
+    f_dev = torch.view_as_real(torch.from_numpy(f)).cuda().contiguous()
+    del f
+    x_dev = torch.zeros_like(f_dev)
+    m = args.m or w.m
+    kw = dict(tol=w.tol, m=m, k=w.k, max_iter=20000, i_schwarz=w.i_schwarz, i_domain=w.i_domain)
+    t2 = time.perf_counter()
+    info = ctx.dd_solve(f_dev, x_dev, where=dd.DD_DEVICE, **kw)
+    t_solve = time.perf_counter() - t2
+    print(json.dumps({"case": "workload_solve", "workload": w.name, "lattice": list(w.dims), "kappa": w.kappa,
+                      "csw": w.csw, "domain": list(w.domain), "i_schwarz": w.i_schwarz, "i_domain": w.i_domain,
+                      "m": m, "k": w.k, "iterations": info.iterations, "restarts": info.restarts,
+                      "true_rel_residual": info.true_rel_residual, "solve_s": info.t_total, "wall_s": t_solve,
+                      "split_s": {"A": info.t_A, "M": info.t_M, "GS": info.t_GS, "other": info.t_other},
+                      "gen_random_s": t_rand, "gen_total_s": t_gen, "setup_s": t_setup,
+                      "device_gb_in_use": (lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info())}))
 
 
 if __name__ == "__main__":

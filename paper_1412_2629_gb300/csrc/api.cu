@@ -37,9 +37,9 @@ struct SapBuffers {
   long long r_bytes = 0, u_bytes = 0;
 };
 
-// A launch sequence of the outer solver captured as a CUDA graph: key = (part, basis
-// buffer, step j, I_Schwarz, I_domain, storage precision, threads per site, m).
-typedef std::array<int, 8> GraphKey;
+// A launch sequence of the outer solver captured as a CUDA graph: key = (part, step j,
+// I_Schwarz, I_domain, storage precision, threads per site, m).
+typedef std::array<int, 7> GraphKey;
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   long long kernels = 0;     // kernels per replay
@@ -53,8 +53,8 @@ struct SolverBuffers {
   cudaStream_t side = nullptr;         // second branch of an Arnoldi step (small dense work)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::map<GraphKey, GraphEntry> graphs;
-  float4* V[2] = {nullptr, nullptr};   // (m+1) vectors each, double-buffered for restarts
-  float4* Z[2] = {nullptr, nullptr};   // m vectors each
+  float4* V = nullptr;                 // m+1 basis vectors (recombined in place at a restart)
+  float4* Z = nullptr;                 // m preconditioned vectors
   float4* w = nullptr;
   double2 *x64 = nullptr, *f64 = nullptr, *r64 = nullptr;
   double2* canon64 = nullptr;          // canonical FP64 staging (one field)
@@ -606,7 +606,7 @@ static void release(dd_ctx* c, void* p) {
 static void release_solver(dd_ctx* c) {
   SolverBuffers& s = c->sv;
   cudaStreamSynchronize(c->st);
-  for (void* p : {(void*)s.V[0], (void*)s.V[1], (void*)s.Z[0], (void*)s.Z[1], (void*)s.w, (void*)s.x64,
+  for (void* p : {(void*)s.V, (void*)s.Z, (void*)s.w, (void*)s.x64,
                   (void*)s.f64, (void*)s.r64, (void*)s.canon64, (void*)s.H, (void*)s.R, (void*)s.P, (void*)s.Hn,
                   (void*)s.g, (void*)s.c0, (void*)s.y, (void*)s.hA, (void*)s.hB, (void*)s.cn, (void*)s.theta,
                   (void*)s.cp, (void*)s.partial, (void*)s.partial2, (void*)s.nrm2, (void*)s.status, (void*)s.lsq,
@@ -632,10 +632,8 @@ static dd_status ensure_solver(dd_ctx* c, int m) {
   const Geom& g = c->g;
   long long n4 = g.V * 6;
   size_t vb = (size_t)n4 * 16;
-  for (int b = 0; b < 2; ++b) {
-    TRY(dalloc(c, &s.V[b], vb * (m + 1)));
-    TRY(dalloc(c, &s.Z[b], vb * m));
-  }
+  TRY(dalloc(c, &s.V, vb * (m + 1)));
+  TRY(dalloc(c, &s.Z, vb * m));
   TRY(dalloc(c, &s.w, vb));
   TRY(dalloc(c, &s.x64, field_bytes(g, P64)));
   TRY(dalloc(c, &s.f64, field_bytes(g, P64)));
@@ -755,9 +753,8 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
   int iters = 0, restarts = 0, reliable = 0, deflated = 0;
   dd_status rc = DD_OK;
   double rho2 = 0;
-  int cur = 0;
-  auto Vv = [&](int i) { return s.V[cur] + (long long)i * n4; };
-  auto Zv = [&](int i) { return s.Z[cur] + (long long)i * n4; };
+  auto Vv = [&](int i) { return s.V + (long long)i * n4; };
+  auto Zv = [&](int i) { return s.Z + (long long)i * n4; };
 
   TRY(true_residual(c, &rho2));
   reliable++;
@@ -775,8 +772,8 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
     double rho_cycle = sqrt(rho2);
     for (int j = j0; j < m; ++j) {
       // one Arnoldi step = three device-only launch sequences, each replayed from a CUDA
-      // graph once it has been captured (keyed by basis buffer, step and parameters)
-      const GraphKey kbase = {0, cur, j, p->sap.i_schwarz, p->sap.i_domain, p->sap.storage_prec,
+      // graph once it has been captured (keyed by step and parameters)
+      const GraphKey kbase = {0, j, p->sap.i_schwarz, p->sap.i_domain, p->sap.storage_prec,
                               p->sap.threads_per_site, m};
       GraphKey k0 = kbase, k1 = kbase, k2 = kbase;
       k1[0] = 1;
@@ -864,12 +861,10 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
       if (drc == 0) {
         TRY(cuda_check(c, cudaMemcpyAsync(s.P, s.h_P, hb, cudaMemcpyHostToDevice, c->st), "P"));
         TRY(cuda_check(c, cudaMemcpyAsync(s.Hn, s.h_Hn, hb, cudaMemcpyHostToDevice, c->st), "Hn"));
-        int nxt = 1 - cur;
-        float4* Vn = s.V[nxt];
-        float4* Zn = s.Z[nxt];
-        int nk = launch_recombine(Vn, s.V[cur], mm + 1, k + 1, n4, (const double2*)s.P, ldh, c->st);
-        nk += launch_recombine(Zn, s.Z[cur], mm, k, n4, (const double2*)s.P, ldh, c->st);
-        cur = nxt;
+        // V <- V P_{k+1}, Z <- Z P_k in place: every output element depends only on the
+        // inputs at the same position, which its thread reads before writing
+        int nk = launch_recombine(s.V, s.V, mm + 1, k + 1, n4, (const double2*)s.P, ldh, c->st);
+        nk += launch_recombine(s.Z, s.Z, mm, k, n4, (const double2*)s.P, ldh, c->st);
         // project the FP64 residual onto the new basis
         launch_r64_to_v32(s.w, s.r64, n4, s.nrm2, c->st);
         nk += launch_multi_dot(Vv(0), k + 1, n4, s.w, s.partial, c->st);

@@ -216,62 +216,64 @@ void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2*
 }
 
 // out_l = sum_i P[i + l ldp] V_i for l < nout (P complex FP64, column-major).  One pass
-// produces up to NO outputs, so a deflated restart of k <= 15 reads each basis once; the
-// loop over inputs takes two at a time to keep two loads in flight per thread.
+// produces NO outputs (instantiated for every count up to 16, so a deflated restart with
+// k <= 15 reads each basis once and holds no unused accumulators); each loop trip issues
+// RU independent input loads per thread, which is what keeps HBM busy here.  out may be
+// V itself (in-place recombination): a thread reads all inputs at q before it writes
+// the outputs at q, and no other thread touches q.
+constexpr int RBT = 128, RU = 8;
 template <int NO>
-__global__ void __launch_bounds__(BT) recombine_kernel(float4* out, const float4* __restrict__ V, int nv, int l0,
-                                                       int nout, long long n4, const double2* P, int ldp) {
+__global__ void __launch_bounds__(RBT) recombine_kernel(float4* out, const float4* V, int nv, int l0,
+                                                        long long n4, const double2* P, int ldp) {
   __shared__ float2 ps[64][NO];
-  const int nl = min(NO, nout - l0);
-  for (int t = threadIdx.x; t < nv * NO; t += BT) {
+  for (int t = threadIdx.x; t < nv * NO; t += RBT) {
     int i = t / NO, l = t % NO;
-    ps[i][l] = l < nl ? make_float2((float)P[i + (long long)(l0 + l) * ldp].x, (float)P[i + (long long)(l0 + l) * ldp].y)
-                      : make_float2(0.f, 0.f);
+    const double2 c = P[i + (long long)(l0 + l) * ldp];
+    ps[i][l] = make_float2((float)c.x, (float)c.y);
   }
   __syncthreads();
-  for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n4; q += (long long)gridDim.x * BT) {
+  for (long long q = blockIdx.x * (long long)RBT + threadIdx.x; q < n4; q += (long long)gridDim.x * RBT) {
     float4 a[NO];
 #pragma unroll
     for (int l = 0; l < NO; ++l) a[l] = make_float4(0, 0, 0, 0);
     auto fma_in = [&](int i, float4 v) {
 #pragma unroll
       for (int l = 0; l < NO; ++l) {
-        if (l < nl) {
-          float2 c = ps[i][l];
-          a[l].x += c.x * v.x - c.y * v.y;
-          a[l].y += c.x * v.y + c.y * v.x;
-          a[l].z += c.x * v.z - c.y * v.w;
-          a[l].w += c.x * v.w + c.y * v.z;
-        }
+        float2 c = ps[i][l];
+        a[l].x += c.x * v.x - c.y * v.y;
+        a[l].y += c.x * v.y + c.y * v.x;
+        a[l].z += c.x * v.z - c.y * v.w;
+        a[l].w += c.x * v.w + c.y * v.z;
       }
     };
     int i = 0;
-    for (; i + 1 < nv; i += 2) {
-      float4 v0 = V[(long long)i * n4 + q], v1 = V[(long long)(i + 1) * n4 + q];
-      fma_in(i, v0);
-      fma_in(i + 1, v1);
-    }
-    if (i < nv) fma_in(i, V[(long long)i * n4 + q]);
+    for (; i + RU <= nv; i += RU) {
+      float4 v[RU];
 #pragma unroll
-    for (int l = 0; l < NO; ++l)
-      if (l < nl) out[(long long)(l0 + l) * n4 + q] = a[l];
+      for (int u = 0; u < RU; ++u) v[u] = V[(long long)(i + u) * n4 + q];
+#pragma unroll
+      for (int u = 0; u < RU; ++u) fma_in(i + u, v[u]);
+    }
+    for (; i < nv; ++i) fma_in(i, V[(long long)i * n4 + q]);
+#pragma unroll
+    for (int l = 0; l < NO; ++l) out[(long long)(l0 + l) * n4 + q] = a[l];
   }
 }
+
+template <int NO>
+static void recombine_launch(int nl, float4* out, const float4* V, int nv, int l0, long long n4, const double2* P,
+                             int ldp, cudaStream_t st) {
+  if constexpr (NO > 1) {
+    if (nl < NO) return recombine_launch<NO - 1>(nl, out, V, nv, l0, n4, P, ldp, st);
+  }
+  recombine_kernel<NO><<<2 * blas_partials_blocks(), RBT, 0, st>>>(out, V, nv, l0, n4, P, ldp);
+}
+
 int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n4, const double2* P, int ldp,
                      cudaStream_t st) {
   int n = 0;
-  const int nb = blas_partials_blocks();
-  for (int l0 = 0; l0 < nout; l0 += 16, ++n) {
-    const int nl = nout - l0 < 16 ? nout - l0 : 16;
-    if (nl <= 4)
-      recombine_kernel<4><<<nb, BT, 0, st>>>(out, V, nv, l0, nout, n4, P, ldp);
-    else if (nl <= 8)
-      recombine_kernel<8><<<nb, BT, 0, st>>>(out, V, nv, l0, nout, n4, P, ldp);
-    else if (nl <= 12)
-      recombine_kernel<12><<<nb, BT, 0, st>>>(out, V, nv, l0, nout, n4, P, ldp);
-    else
-      recombine_kernel<16><<<nb, BT, 0, st>>>(out, V, nv, l0, nout, n4, P, ldp);
-  }
+  for (int l0 = 0; l0 < nout; l0 += 16, ++n)
+    recombine_launch<16>(nout - l0 < 16 ? nout - l0 : 16, out, V, nv, l0, n4, P, ldp, st);
   return n;
 }
 

@@ -49,6 +49,15 @@ WORKLOADS = {
     # Schwarz settings apply (24 / 8 is odd, so the domains are 4^4)
     "24^3x48": Workload("24^3x48", (24, 24, 24, 48), 0.5, 5, 0.1240, 1.5, (4, 4, 4, 4), 16, 5, 16, 6, 14, 24),
     "16^3x32": Workload("16^3x32", (16, 16, 16, 32), 0.5, 5, 0.1340, 1.5, (4, 4, 4, 4), 16, 5, 16, 6, 151, 25),
+    # near-critical: the smallest |eigenvalue| of gamma5 A cannot fall to 1e-3 on these
+    # almost-free fields with antiperiodic time over 96 slices (the free-field bound is
+    # sin(pi / 96) = 0.033 at the critical mass), so kappa sits at the field's critical
+    # value, just below 1 / (8 u0) = 0.12509 (u0 = plaquette^(1/4) = 0.99925), where it is smallest
+    "48^3x96": Workload("48^3x96", (48, 48, 48, 96), 0.5, 5, 0.1250, 1.7, (8, 4, 4, 4), 4, 4, 32, 8, 13, 23),
+    # the large single lattice; its kappa is not given: 0.124 as for the batched workload.
+    # Basis sized to HBM: the fields take ~4.6 KB per site, each basis vector 96 B per
+    # site, so m = 12 (2m + 1 = 25 vectors, 80 GB) keeps the whole solve near 250 GB
+    "64^3x128": Workload("64^3x128", (64, 64, 64, 128), 0.5, 5, 0.1240, 1.5, (8, 4, 4, 4), 16, 5, 12, 6, 15, 25),
 }
 
 

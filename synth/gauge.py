@@ -62,6 +62,17 @@ def reunitarize(M: torch.Tensor) -> torch.Tensor:
     return torch.stack([r0, r1, r2], dim=-2)
 
 
+def mm3(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+    """Products of [..., 3, 3] matrices as one broadcast multiply and a sum over the inner
+    index: elementwise kernels, which run at memory speed for millions of 3x3 matrices
+    where a batched GEMM of that shape is two orders of magnitude slower."""
+    return (A.unsqueeze(-1) * B.unsqueeze(-3)).sum(-2)
+
+
+def _dag(M: torch.Tensor) -> torch.Tensor:
+    return M.conj().transpose(-1, -2)
+
+
 def _expi_hermitian(Hm: torch.Tensor, terms: int = 18) -> torch.Tensor:
     """exp(i H) for Hermitian [..., 3, 3] H by scaling and squaring: X = i H / 2^s with
     |X|_F <= 1/2, a Taylor polynomial of X (Horner form, remainder < 1e-20), then s
@@ -72,9 +83,9 @@ def _expi_hermitian(Hm: torch.Tensor, terms: int = 18) -> torch.Tensor:
     eye = torch.eye(3, dtype=Hm.dtype, device=Hm.device).expand_as(Hm)
     E = eye.clone()
     for n in range(terms, 0, -1):
-        E = eye + (X @ E) / n
+        E = eye + mm3(X, E) / n
     for _ in range(s):
-        E = E @ E
+        E = mm3(E, E)
     return E
 
 
@@ -125,10 +136,10 @@ def ape_smear(U: torch.Tensor, alpha: float = 0.5, steps: int = 5) -> torch.Tens
                     continue
                 Unu = U[..., nu, :, :]
                 # upper staple U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
-                S = S + Unu @ _sh(Umu, nu, 1) @ _sh(Unu, mu, 1).conj().transpose(-1, -2)
+                S = S + mm3(mm3(Unu, _sh(Umu, nu, 1)), _dag(_sh(Unu, mu, 1)))
                 # lower staple U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
                 Unm = _sh(Unu, nu, -1)
-                S = S + Unm.conj().transpose(-1, -2) @ _sh(Umu, nu, -1) @ _sh(_sh(Unu, nu, -1), mu, 1)
+                S = S + mm3(mm3(_dag(Unm), _sh(Umu, nu, -1)), _sh(Unm, mu, 1))
             new[..., mu, :, :] = reunitarize((1 - alpha) * Umu + (alpha / 6.0) * S)
         U = new
     return U
