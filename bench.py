@@ -28,6 +28,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "32^3x64"
+SAP_DTYPE = {"fp16": "f16-storage/f32-arith/f64-residual",
+             "half2": "f16-storage/f16x2-products+f32-arith/f64-residual"}
+SAP_KERNEL = {"fp16": "sap_kernel (Schwarz half-sweep, FP16 storage)",
+              "half2": "sap_kernel (Schwarz half-sweep, FP16 storage, packed FP16 products)"}
 METRIC = "time-to-solution to 1e-10 true residual, mixed FP16/FP32/FP64 SAP-FGMRES-DR"
 FLOP_HOP, FLOP_CLOVER, FLOP_A = 168, 504, 1848      # Sec. II-B: 1344 = 8 x 168, 504, 1848
 # Outer iterations the 32^3x64 solve takes (measured on the GPU, mixed and FP32 alike);
@@ -225,6 +229,8 @@ def main():
     ap.add_argument("--tps", type=int, default=0, help="Schwarz kernel threads per site (0: library default)")
     ap.add_argument("--nrhs", type=int, default=1, help="kernel studies: right-hand sides per launch")
     ap.add_argument("--workload", default="48^3x96", help="workload_solve: the workload to solve once")
+    ap.add_argument("--sap-prec", default="fp16", choices=["fp16", "half2"],
+                    help="mixed form: FP16 storage with FP32 arithmetic, or with packed FP16 products")
     ap.add_argument("--m", type=int, default=0, help="workload_solve: basis size (0: the workload's)")
     args = ap.parse_args()
     if not args.only_mixed:
@@ -303,15 +309,20 @@ def main():
 
     clk = ClockSampler(local)
     clk.start()
-    ms_mixed, infos, launches = timed(dd.DD_PREC_FP16, dd.DD_DEVICE, args.steps, args.warmup, "timed_mixed")
+    mixed = dd.DD_PREC_FP16_H2 if args.sap_prec == "half2" else dd.DD_PREC_FP16
+    ms_mixed, infos, launches = timed(mixed, dd.DD_DEVICE, args.steps, args.warmup, "timed_mixed")
     clocks = clk.stop()
     if args.only_mixed:
         ms_e2e, ms_fp32, infos32 = float("nan"), float("nan"), infos
+        ms_alt, infos_alt = float("nan"), infos
     else:
-        ms_e2e, infos_e2e, _ = timed(dd.DD_PREC_FP16, dd.DD_HOST, args.steps, 1, "timed_e2e")
+        ms_e2e, infos_e2e, _ = timed(mixed, dd.DD_HOST, args.steps, 1, "timed_e2e")
         ms_fp32, infos32, _ = timed(dd.DD_PREC_FP32, dd.DD_DEVICE, max(2, args.steps // 2), 1, "timed_fp32")
+        # the other mixed form: FP16 storage with packed FP16 products (or FP32 arithmetic)
+        alt = dd.DD_PREC_FP16 if args.sap_prec == "half2" else dd.DD_PREC_FP16_H2
+        ms_alt, infos_alt, _ = timed(alt, dd.DD_DEVICE, max(2, args.steps // 2), 1, "timed_alt")
 
-    ms_mixed, ms_e2e, ms_fp32 = max_over_ranks([ms_mixed, ms_e2e, ms_fp32], "cuda")
+    ms_mixed, ms_e2e, ms_fp32, ms_alt = max_over_ranks([ms_mixed, ms_e2e, ms_fp32, ms_alt], "cuda")
 
     V = int(np.prod(w.dims))
     mean = lambda key, L: statistics.mean(i[key] for i in L)
@@ -349,11 +360,11 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f16-storage/f32-arith/f64-residual", "data": "synthetic",
+        "vs_baseline": None, "dtype": SAP_DTYPE[args.sap_prec], "data": "synthetic",
         "config": config_dict(w),
         "e2e": {"value": ms_e2e / 1e3, "unit": "s", "h2d_bytes_per_step": 2 * V * 24 * 8,
                 "d2h_bytes_per_step": V * 24 * 8},
-        "roofline": {"kernel": "sap_kernel (Schwarz half-sweep, FP16 storage)", "bound": "alu",
+        "roofline": {"kernel": SAP_KERNEL[args.sap_prec], "bound": "alu",
                      "achieved": sap_tflops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": sap_tflops / fp32_peak,
                      "traffic": sap_traffic,
                      "peak_note": f"FP32 CUDA cores: {props.multi_processor_count} SMs x 128 lanes x 2 flop x "
@@ -362,6 +373,11 @@ def main():
         "dslash": {"kernel": "apply_A_kernel<float>", "bound": "hbm", "achieved": dsl_gbs, "peak": hbm,
                    "unit": "GB/s", "frac": dsl_gbs / hbm, "traffic": dsl_traffic, "launch_ms": 1e3 * a_launch_s,
                    "bytes_per_launch": dslash_bytes_per_site("fp32") * V, "peak_note": "of measured (MEASURED_PEAKS hbm_gbs)"},
+        ("fp16_f32arith_form" if args.sap_prec == "half2" else "half2_form"): {
+            "value": ms_alt / 1e3, "unit": "s", "dtype": SAP_DTYPE["fp16" if args.sap_prec == "half2" else "half2"],
+            "iterations": mean("iterations", infos_alt),
+            "true_rel_residual": max(i["true_rel_residual"] for i in infos_alt),
+            "schwarz_launch_ms": 1e3 * mean("t_M", infos_alt) / (mean("iterations", infos_alt) * 2 * w.i_schwarz)},
         "fp32_form": {"value": ms_fp32 / 1e3, "unit": "s", "iterations": mean("iterations", infos32),
                       "true_rel_residual": max(i["true_rel_residual"] for i in infos32),
                       "speedup_mixed_over_fp32": ms_fp32 / ms_mixed},
@@ -390,6 +406,7 @@ def kernel_case(args, local):
 
     import synth
     from paper_1412_2629_gb300 import dd
+    SAP_PREC = {"fp16": dd.DD_PREC_FP16, "half2": dd.DD_PREC_FP16_H2}
     base = synth.WORKLOADS[WORKLOAD]
     dims = tuple(int(v) for v in args.lattice.split(","))
     dom = tuple(int(v) for v in args.domain.split(",")) if args.domain else base.domain
@@ -412,10 +429,10 @@ def kernel_case(args, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = args.steps
     if args.case == "sap" and nr > 1:
-        run = lambda: ctx.dd_sap_precondition_batch(a, b, nr, w.i_schwarz, w.i_domain, dd.DD_PREC_FP16)
+        run = lambda: ctx.dd_sap_precondition_batch(a, b, nr, w.i_schwarz, w.i_domain, SAP_PREC[args.sap_prec])
         launches = 2 * w.i_schwarz
     elif args.case == "sap":
-        run = lambda: ctx.dd_sap_precondition(a, b, w.i_schwarz, w.i_domain, dd.DD_PREC_FP16, dd.DD_LAYOUT_INTERNAL,
+        run = lambda: ctx.dd_sap_precondition(a, b, w.i_schwarz, w.i_domain, SAP_PREC[args.sap_prec], dd.DD_LAYOUT_INTERNAL,
                                               threads_per_site=args.tps)
         launches = 2 * w.i_schwarz
     elif nr > 1:

@@ -56,7 +56,7 @@ enum {
   DD_ERR_CUDA = 10             /* other CUDA runtime error */
 };
 
-enum { DD_PREC_FP64 = 0, DD_PREC_FP32 = 1, DD_PREC_FP16 = 2 };
+enum { DD_PREC_FP64 = 0, DD_PREC_FP32 = 1, DD_PREC_FP16 = 2, DD_PREC_FP16_H2 = 3 };
 enum { DD_HOST = 0, DD_DEVICE = 1 };
 enum { DD_LAYOUT_CANONICAL = 0, DD_LAYOUT_INTERNAL = 1 };
 
@@ -65,6 +65,11 @@ typedef struct {
   int i_schwarz;      /* Schwarz iterations; one iteration = black then white half-sweep (paper: 16) */
   int i_domain;       /* MR steps per domain solve (paper: 4-5) */
   int storage_prec;   /* DD_PREC_FP16: FP16 links, Schwarz matrices and spinors (FP32 arithmetic);
+                         DD_PREC_FP16_H2: FP16 storage as above, and the domain solve's SU(3) and
+                           clover-block products in packed FP16 arithmetic (half2), each domain's
+                           residual scaled into FP16 range by a power of two; hop sums, MR
+                           reductions and updates stay FP32.  Not part of the paper (which keeps
+                           single-precision arithmetic); needs threads_per_site 0 or 2;
                          DD_PREC_FP32: everything FP32 */
   int threads_per_site; /* 1 or 2 GPU threads per lattice site in the domain solve; 0 = default (2) */
 } dd_sap_params;

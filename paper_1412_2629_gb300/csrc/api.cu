@@ -387,6 +387,9 @@ static dd_status ensure_sap(dd_ctx* c, int prec, int nrhs = 1) {
   return DD_OK;
 }
 
+// Storage precision of the Schwarz state for a dd_sap_params::storage_prec value.
+static int sap_prec(int storage_prec) { return storage_prec == DD_PREC_FP32 ? P32 : P16; }
+
 static SapState sap_state(dd_ctx* c, int prec, const dd_sap_params* p, int nrhs) {
   SapBuffers& b = c->sap[prec];
   SapState S;
@@ -406,30 +409,14 @@ static SapState sap_state(dd_ctx* c, int prec, const dd_sap_params* p, int nrhs)
   S.mat_in_smem = sap_mat_fits_smem(c->g, prec);
   S.threads_per_site = p->threads_per_site ? p->threads_per_site : 2;
   S.inject_wait_timeout = c->inject_wait_timeout;
+  S.half_arith = p->storage_prec == DD_PREC_FP16_H2;
   return S;
 }
 
 static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_params* p, int nrhs = 1) {
-  int prec = p->storage_prec == DD_PREC_FP16 ? P16 : P32;
+  int prec = sap_prec(p->storage_prec);
   TRY(ensure_sap(c, prec, nrhs));
-  SapBuffers& b = c->sap[prec];
-  SapState S;
-  S.nrhs = nrhs;
-  S.r_bytes = b.r_bytes;
-  S.u_bytes = b.u_bytes;
-  S.mat_prec = prec;
-  S.vec_prec = prec;
-  S.links = prec == P16 ? (const void*)c->U16 : (const void*)c->U32;
-  S.smat = prec == P16 ? (const void*)c->S16 : (const void*)c->S32;
-  S.r_store = b.r_store;
-  S.r_norm = b.r_norm;
-  S.u_store = b.u_store;
-  S.u_norm = b.u_norm;
-  S.faces = b.faces;
-  S.err = c->sap_err;
-  S.mat_in_smem = sap_mat_fits_smem(c->g, prec);
-  S.threads_per_site = p->threads_per_site ? p->threads_per_site : 2;
-  S.inject_wait_timeout = c->inject_wait_timeout;
+  SapState S = sap_state(c, prec, p, nrhs);
   for (int s = 0; s < p->i_schwarz; ++s)
     for (int colour = 0; colour < 2; ++colour) {
       int first = s == 0, use_faces = !(s == 0 && colour == 0), last = s == p->i_schwarz - 1;
@@ -441,9 +428,12 @@ static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_par
 }
 
 static dd_status check_sap_params(dd_ctx* c, const dd_sap_params* p) {
-  if (!p || p->i_schwarz < 1 || p->i_domain < 0 || (p->storage_prec != DD_PREC_FP16 && p->storage_prec != DD_PREC_FP32) ||
+  if (!p || p->i_schwarz < 1 || p->i_domain < 0 ||
+      (p->storage_prec != DD_PREC_FP16 && p->storage_prec != DD_PREC_FP32 && p->storage_prec != DD_PREC_FP16_H2) ||
       p->threads_per_site < 0 || p->threads_per_site > 2)
     return fail(c, DD_ERR_INVALID, "bad Schwarz parameters");
+  if (p->storage_prec == DD_PREC_FP16_H2 && p->threads_per_site == 1)
+    return fail(c, DD_ERR_INVALID, "packed FP16 arithmetic needs two threads per site");
   return DD_OK;
 }
 
@@ -1074,8 +1064,8 @@ extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4],
           if (s == DD_OK) {
             fill_random_kernel<<<blas_partials_blocks(), 256, 0, c->st>>>(v, n4, 12345);
             // slots: CTAs resident at once, for the load model
-            double load = dd_load_model(t->g.ND / 2, sms * (sap_smem_bytes(t->g, storage_prec == DD_PREC_FP16 ? P16 : P32,
-                                                                          sap_mat_fits_smem(t->g, storage_prec == DD_PREC_FP16 ? P16 : P32)) > 116 * 1024 ? 1 : 2));
+            double load = dd_load_model(t->g.ND / 2, sms * (sap_smem_bytes(t->g, sap_prec(storage_prec),
+                                                                          sap_mat_fits_smem(t->g, sap_prec(storage_prec))) > 116 * 1024 ? 1 : 2));
             for (int cand = 0; cand < 10; ++cand) {
               const int id = 2 + cand / 2, tps = 1 + cand % 2;
               dd_sap_params sp = {i_schwarz, id, storage_prec, tps};
@@ -1126,7 +1116,7 @@ extern "C" dd_status dd_sap_precondition_noalloc(dd_ctx* c, const float* in, flo
   TRY(check_sap_params(c, p));
   if (p->i_domain == 0) return fail(c, DD_ERR_INVALID, "i_domain must be >= 1");
   const Geom& g = c->g;
-  int prec = p->storage_prec == DD_PREC_FP16 ? P16 : P32;
+  int prec = sap_prec(p->storage_prec);
   // carve the fixed array: residual (even sites), solution, faces, error word
   size_t half_sites = (size_t)g.V / 2;
   size_t r_bytes = prec == P16 ? half_sites * 48 : half_sites * 96;
@@ -1157,6 +1147,7 @@ extern "C" dd_status dd_sap_precondition_noalloc(dd_ctx* c, const float* in, flo
   S.err = (int*)(base + off);
   S.mat_in_smem = sap_mat_fits_smem(g, prec);
   S.threads_per_site = p->threads_per_site ? p->threads_per_site : 2;
+  S.half_arith = p->storage_prec == DD_PREC_FP16_H2;
   // the error word must start at zero; residual, solution and faces are written before
   // they are read within one call
   TRY(cuda_check(c, cudaMemsetAsync(S.err, 0, sizeof(int), c->st), "clear error word"));

@@ -60,6 +60,7 @@ struct SapState {
   int threads_per_site = 2;   // 1: one thread per site; 2: hop directions and chirality split
   bool inject_wait_timeout = false;   // test hook: make the bounded wait run out (no fault)
   int nrhs = 1;                // right-hand sides in one launch (their buffers follow each other)
+  bool half_arith = false;     // FP16 storage with packed FP16 hop and clover products
   long long r_bytes = 0;       // bytes of one right-hand side's residual / solution storage
   long long u_bytes = 0;
 };

@@ -790,41 +790,176 @@ __device__ inline void face_write_rt(const Geom& g, long long d, const int l[4],
   }
 }
 
+// ------------------------------------------------------------------ packed FP16 arithmetic
+// Optional form of the domain solve's two products, in half2 arithmetic (two FP16 lanes
+// per instruction) straight from the FP16 links and Schwarz matrices in shared memory.
+//  - SU(3) times a half-spinor is spin-vectorised: the two spin rows of one colour share
+//    a half2 (re = (s0.re, s1.re), im = (s0.im, s1.im)), so each link element, broadcast
+//    to both lanes, enters four fused multiply-adds that cover both spins.
+//  - A Hermitian 6x6 block times a 6-vector keeps (re, im) in a half2 and a copy of i x
+//    per input entry, (-im, re); an entry L enters y_i += Lr x_j + Li (i x_j) and, as
+//    conj(L), y_j += Lr x_i - Li (i x_i).
+// Hop sums, MR reductions and vector updates stay FP32; values are scaled per domain into
+// FP16's range before they meet these products (sap_pair_body).
+struct HalfH2 {
+  __half2 re[3], im[3];   // colour c: (spin 0, spin 1) of the real and imaginary parts
+};
+
+__device__ inline __half2 as_h2(uint32_t w) { return *reinterpret_cast<__half2*>(&w); }
+
+__device__ inline void pack_h2(const Half<float>& h, HalfH2& o) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    o.re[c] = __floats2half2_rn(h.c[0][c].re, h.c[1][c].re);
+    o.im[c] = __floats2half2_rn(h.c[0][c].im, h.c[1][c].im);
+  }
+}
+__device__ inline void unpack_h2(const HalfH2& o, Half<float>& h) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float2 r = __half22float2(o.re[c]), i = __half22float2(o.im[c]);
+    h.c[0][c] = mk(r.x, i.x);
+    h.c[1][c] = mk(r.y, i.y);
+  }
+}
+
+// o = U h (DAG false) or U^dag h (DAG true); u: the 9 (re, im) words of U, stride Vd.
+template <bool DAG>
+__device__ inline void su3_h2(const __half2* u, int Vd, const HalfH2& h, HalfH2& o) {
+  __half2 U[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) U[e] = u[e * Vd];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    __half2 re, im;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const __half2 e = DAG ? U[3 * b + a] : U[3 * a + b];
+      const __half2 er = __low2half2(e), ei = __high2half2(e);
+      // U h:     re += er h.re - ei h.im,  im += er h.im + ei h.re
+      // U^dag h: re += er h.re + ei h.im,  im += er h.im - ei h.re
+      if (b == 0) {
+        re = __hmul2(er, h.re[b]);
+        im = __hmul2(er, h.im[b]);
+      } else {
+        re = __hfma2(er, h.re[b], re);
+        im = __hfma2(er, h.im[b], im);
+      }
+      re = __hfma2(DAG ? ei : __hneg2(ei), h.im[b], re);
+      im = __hfma2(DAG ? __hneg2(ei) : ei, h.re[b], im);
+    }
+    o.re[a] = re;
+    o.im[a] = im;
+  }
+}
+
+// y = H x for block H of site r; the block's 18 words are 3 pairs of diagonal entries
+// and the 15 lower entries (re, im) in the order of tri(i, j).
+template <int H>
+__device__ inline void clover_block_h2(const MatBlock<__half>& M, int r, const __half2 x[6], __half2 y[6]) {
+  uint32_t w[20];   // units 4H .. 4H+4 of the site; block word k is w[2H + k]
+#pragma unroll
+  for (int u = 0; u < 5; ++u) {
+    uint4 v = M.cm[(4 * H + u) * M.Vd + r];
+    w[4 * u] = v.x;
+    w[4 * u + 1] = v.y;
+    w[4 * u + 2] = v.z;
+    w[4 * u + 3] = v.w;
+  }
+  const __half2 sgn = __floats2half2_rn(-1.f, 1.f);
+  __half2 xs[6];   // i x = (-im, re)
+#pragma unroll
+  for (int j = 0; j < 6; ++j) xs[j] = __hmul2(__lowhigh2highlow(x[j]), sgn);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const __half2 d = as_h2(w[2 * H + i / 2]);
+    y[i] = __hmul2((i & 1) ? __high2half2(d) : __low2half2(d), x[i]);
+  }
+#pragma unroll
+  for (int i = 1; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      const __half2 L = as_h2(w[2 * H + 3 + tri(i, j)]);
+      const __half2 lr = __low2half2(L), li = __high2half2(L);
+      y[i] = __hfma2(lr, x[j], y[i]);
+      y[i] = __hfma2(li, xs[j], y[i]);
+      y[j] = __hfma2(lr, x[i], y[j]);
+      y[j] = __hfma2(__hneg2(li), xs[i], y[j]);
+    }
+}
+
+template <typename MT, bool H2>
+__device__ inline void block_apply_pair(const MatBlock<MT>& M, int r, int h, const Half<float>& x, Half<float>& y) {
+  if constexpr (H2) {
+    __half2 xv[6], yv[6];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) xv[3 * s + c] = __floats2half2_rn(x.c[s][c].re, x.c[s][c].im);
+    if (h == 0) clover_block_h2<0>(M, r, xv, yv);
+    else clover_block_h2<1>(M, r, xv, yv);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float2 f = __half22float2(yv[3 * s + c]);
+        y.c[s][c] = mk(f.x, f.y);
+      }
+  } else {
+    block_apply(M, r, h, x, y);
+  }
+}
+
 // Hops of one direction with the inside-the-domain test taken from bit masks, so the
 // phase loop carries four small integers instead of two coordinate arrays.
-template <int MU, typename MT>
+template <int MU, typename MT, bool H2>
 __device__ inline void hop_mask_mu(const Geom& g, unsigned fwd, unsigned bwd, int lex, int p, int r_self,
                                    const float4* src, const MatBlock<MT>& M, Spinor<float>& acc) {
   Spinor<float> psi;
   Half<float> h, uh;
-  Link<float> L;
   if ((fwd >> MU) & 1u) {
     int j = (lex + g.bstride[MU]) >> 1;
     ld_buf(src, g.Hd, j, psi);
     project<MU, -1>(psi, h);
-    M.link(MU, r_self, L);
-    su3_mul(L, h, uh);
+    if constexpr (H2) {
+      HalfH2 hh, oh;
+      pack_h2(h, hh);
+      su3_h2<false>(reinterpret_cast<const __half2*>(M.lk) + MU * 9 * g.Vd + r_self, g.Vd, hh, oh);
+      unpack_h2(oh, uh);
+    } else {
+      Link<float> L;
+      M.link(MU, r_self, L);
+      su3_mul(L, h, uh);
+    }
     accum_recon<MU, -1>(acc, uh);
   }
   if ((bwd >> MU) & 1u) {
     int j = (lex - g.bstride[MU]) >> 1;
     ld_buf(src, g.Hd, j, psi);
     project<MU, +1>(psi, h);
-    M.link(MU, (1 - p) * g.Hd + j, L);
-    su3_dag_mul(L, h, uh);
+    if constexpr (H2) {
+      HalfH2 hh, oh;
+      pack_h2(h, hh);
+      su3_h2<true>(reinterpret_cast<const __half2*>(M.lk) + MU * 9 * g.Vd + (1 - p) * g.Hd + j, g.Vd, hh, oh);
+      unpack_h2(oh, uh);
+    } else {
+      Link<float> L;
+      M.link(MU, (1 - p) * g.Hd + j, L);
+      su3_dag_mul(L, h, uh);
+    }
     accum_recon<MU, +1>(acc, uh);
   }
 }
 
-template <typename MT>
+template <typename MT, bool H2>
 __device__ inline void hops_half_mask(int h, const Geom& g, unsigned fwd, unsigned bwd, int lex, int p, int r_self,
                                       const float4* src, const MatBlock<MT>& M, Spinor<float>& acc) {
   if (h == 0) {
-    hop_mask_mu<0>(g, fwd, bwd, lex, p, r_self, src, M, acc);
-    hop_mask_mu<1>(g, fwd, bwd, lex, p, r_self, src, M, acc);
+    hop_mask_mu<0, MT, H2>(g, fwd, bwd, lex, p, r_self, src, M, acc);
+    hop_mask_mu<1, MT, H2>(g, fwd, bwd, lex, p, r_self, src, M, acc);
   } else {
-    hop_mask_mu<2>(g, fwd, bwd, lex, p, r_self, src, M, acc);
-    hop_mask_mu<3>(g, fwd, bwd, lex, p, r_self, src, M, acc);
+    hop_mask_mu<2, MT, H2>(g, fwd, bwd, lex, p, r_self, src, M, acc);
+    hop_mask_mu<3, MT, H2>(g, fwd, bwd, lex, p, r_self, src, M, acc);
   }
 }
 
@@ -835,7 +970,11 @@ __device__ inline void hops_half_mask(int h, const Geom& g, unsigned fwd, unsign
 //   phase 2k+2:       even sites, src = t        -> p = A_ee rho - 1/4 H t, MR step
 //   phase 2 I_d + 1:  odd sites,  src = x        -> delta_o = A_oo^{-1} (r_o + 1/2 H x)
 // cta: index of the domain among the domains of the given colour.
-template <typename MT, typename VT, bool MSMEM>
+// H2: hop and clover products in packed FP16 (see su3_h2); the domain's residual is then
+// scaled by a power of two, 16 / 2^ceil(log2 max|r|), before it enters the work buffers,
+// and everything that leaves them (the new residual, delta) is scaled back.  The MR
+// iteration is invariant under that scaling and powers of two are exact in FP32.
+template <typename MT, typename VT, bool MSMEM, bool H2>
 __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   const Geom& g = a.g;
   extern __shared__ float4 smem[];
@@ -907,6 +1046,7 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   float4* const fr = a.faces + rhs * a.f_stride;
   float* const rnr = a.r_norm ? a.r_norm + rhs * a.rn_stride : nullptr;
   float* const unr = a.u_norm ? a.u_norm + rhs * a.un_stride : nullptr;
+  float inv_sc = 1.f;   // H2: undoes the domain's scaling on the way out
   // 1. residual of site (parity h, index i), with the couplings to the other colour
   EvenStore<VT> rst{reinterpret_cast<decltype(EvenStore<VT>::p)>((char*)a.r_store + rhs * a.r_bytes), rnr};
   {
@@ -933,6 +1073,27 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) r.c[s][c] = r.c[s][c] + 0.5f * acc.c[s][c];
     }
+    if constexpr (H2) {
+      float m = 0.f;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) m = fmaxf(m, fmaxf(fabsf(r.c[s][c].re), fabsf(r.c[s][c].im)));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if ((tid & 31) == 0) red[tid >> 5].x = m;
+      __syncthreads();
+      m = 0.f;
+      for (int w = 0; w < (2 * Hd + 31) >> 5; ++w) m = fmaxf(m, red[w].x);
+      int e = 0;
+      frexpf(m, &e);   // m < 2^e
+      const float sc = m > 0.f ? ldexpf(1.f, 4 - max(e, -100)) : 1.f;   // finite even for tiny m
+      inv_sc = 1.f / sc;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r.c[s][c] = mk(r.c[s][c].re * sc, r.c[s][c].im * sc);
+    }
     st_buf(h ? sO : sE, Hd, i, r);
   }
   __syncthreads();
@@ -944,7 +1105,7 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   for (int s = 0; s < 2; ++s)
 #pragma unroll
     for (int c = 0; c < 3; ++c) x.c[s][c] = mk(0.f, 0.f);
-  block_apply(M, r_o, h, roh, t);          // t_o = A_oo^{-1} r_o
+  block_apply_pair<MT, H2>(M, r_o, h, roh, t);   // t_o = A_oo^{-1} r_o
   st_hbuf(sO, Hd, i, h, t);
   __syncthreads();
 
@@ -957,8 +1118,8 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
     Spinor<float> acc;
     zero(acc);
     // the hop code is specialised per direction pair (h) but appears once in the loop
-    hops_half_mask(h, g, odd ? fo : fe, odd ? bo : be, odd ? lex_o : lex_e, odd, odd ? r_o : r_e, odd ? sE : sO, M,
-                   acc);
+    hops_half_mask<MT, H2>(h, g, odd ? fo : fe, odd ? bo : be, odd ? lex_o : lex_e, odd, odd ? r_o : r_e,
+                           odd ? sE : sO, M, acc);
     exchange(acc, h, odd ? sO : sE, Hd, i, own);
     if (ph == 0) {
 #pragma unroll
@@ -974,7 +1135,7 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
 #pragma unroll
         for (int c = 0; c < 3; ++c)
           bin.c[s][c] = !odd ? rho.c[s][c] : (ph == nph - 1 ? roh.c[s][c] + 0.5f * own.c[s][c] : own.c[s][c]);
-      block_apply(M, odd ? r_o : r_e, h, bin, t);
+      block_apply_pair<MT, H2>(M, odd ? r_o : r_e, h, bin, t);
       if (odd) st_hbuf(sO, Hd, i, h, t);
     }
     if (ph != 0 && !odd) {
@@ -1019,6 +1180,12 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
     __syncthreads();
   }
   if (!a.last) {
+    if constexpr (H2) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rho.c[s][c] = mk(rho.c[s][c].re * inv_sc, rho.c[s][c].im * inv_sc);
+    }
     EvenHalfStore<VT>::store(rst, nrm, d, Hd, i, h, rho);
     __syncthreads();
   }
@@ -1026,6 +1193,12 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   // 5. site (h, i): u += delta, faces of delta
   Spinor<float> dl;
   ld_buf(h ? sO : sE, Hd, i, dl);
+  if constexpr (H2) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dl.c[s][c] = mk(dl.c[s][c].re * inv_sc, dl.c[s][c].im * inv_sc);
+  }
   typename VecPtr<VT>::type ust = VecPtr<VT>::make((char*)a.u_store + rhs * a.u_bytes, unr);
   Spinor<float> u;
   if (a.first) {
@@ -1051,9 +1224,9 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   }
 }
 
-template <typename MT, typename VT, bool MSMEM>
+template <typename MT, typename VT, bool MSMEM, bool H2>
 __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArgs a) {
-  sap_pair_body<MT, VT, MSMEM>(a, blockIdx.x);
+  sap_pair_body<MT, VT, MSMEM, H2>(a, blockIdx.x);
 }
 
 // Several lattices of the same domain shape in one launch: the grid is the concatenation
@@ -1070,10 +1243,10 @@ __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair_lattic
   int l = 0;
   while (l + 1 < m.nlat && (int)blockIdx.x >= m.first[l + 1]) ++l;
   switch (l) {   // constant indices keep the arguments in the parameter space
-    case 0: sap_pair_body<MT, VT, MSMEM>(m.lat[0], blockIdx.x - m.first[0]); break;
-    case 1: sap_pair_body<MT, VT, MSMEM>(m.lat[1], blockIdx.x - m.first[1]); break;
-    case 2: sap_pair_body<MT, VT, MSMEM>(m.lat[2], blockIdx.x - m.first[2]); break;
-    default: sap_pair_body<MT, VT, MSMEM>(m.lat[3], blockIdx.x - m.first[3]); break;
+    case 0: sap_pair_body<MT, VT, MSMEM, false>(m.lat[0], blockIdx.x - m.first[0]); break;
+    case 1: sap_pair_body<MT, VT, MSMEM, false>(m.lat[1], blockIdx.x - m.first[1]); break;
+    case 2: sap_pair_body<MT, VT, MSMEM, false>(m.lat[2], blockIdx.x - m.first[2]); break;
+    default: sap_pair_body<MT, VT, MSMEM, false>(m.lat[3], blockIdx.x - m.first[3]); break;
   }
 }
 
@@ -1102,18 +1275,18 @@ static int smem_optin() {
 
 int sap_max_domain_sites() { return 2 * SAP_MAX_THREADS; }
 
-template <typename MT, typename VT, bool MSMEM>
+template <typename MT, typename VT, bool MSMEM, bool H2 = false>
 static int launch_one(const SapArgs& a, int grid, int pair, cudaStream_t st) {
   size_t smem = sap_smem_bytes(a.g, std::is_same<MT, __half>::value ? P16 : P32, MSMEM);
   // static shared memory (barrier, reduction slots) is at most a few KB; the rest may be dynamic
   if (pair) {
     static int configured = 0;
     if (!configured) {
-      cudaFuncSetAttribute(sap_kernel_pair<MT, VT, MSMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(sap_kernel_pair<MT, VT, MSMEM, H2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            smem_optin() - 4096);
       configured = 1;
     }
-    sap_kernel_pair<MT, VT, MSMEM><<<grid, 2 * a.g.Hd, smem, st>>>(a);
+    sap_kernel_pair<MT, VT, MSMEM, H2><<<grid, 2 * a.g.Hd, smem, st>>>(a);
   } else {
     static int configured = 0;
     if (!configured) {
@@ -1172,6 +1345,11 @@ int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int 
   int pr = S.threads_per_site == 2;
   // matrices and vectors are stored in the same precision (FP16 or FP32)
   if (S.mat_prec != S.vec_prec) return -1;
+  if (S.half_arith) {   // packed FP16 products: FP16 storage and the two-thread kernel only
+    if (S.mat_prec != P16 || !pr) return -1;
+    return ms ? launch_one<__half, __half, true, true>(a, grid, 1, st)
+              : launch_one<__half, __half, false, true>(a, grid, 1, st);
+  }
   if (S.mat_prec == P16)
     return ms ? launch_one<__half, __half, true>(a, grid, pr, st) : launch_one<__half, __half, false>(a, grid, pr, st);
   return ms ? launch_one<float, float, true>(a, grid, pr, st) : launch_one<float, float, false>(a, grid, pr, st);

@@ -17,7 +17,7 @@ DD_OK = 0
 DD_ERR_INVALID, DD_ERR_DIMS, DD_ERR_NO_GAUGE, DD_ERR_NO_CLOVER = 1, 2, 3, 4
 DD_ERR_SINGULAR_CLOVER, DD_ERR_NOT_CONVERGED, DD_ERR_NONFINITE = 5, 6, 7
 DD_ERR_TIMEOUT, DD_ERR_OOM, DD_ERR_CUDA = 8, 9, 10
-DD_PREC_FP64, DD_PREC_FP32, DD_PREC_FP16 = 0, 1, 2
+DD_PREC_FP64, DD_PREC_FP32, DD_PREC_FP16, DD_PREC_FP16_H2 = 0, 1, 2, 3
 DD_HOST, DD_DEVICE = 0, 1
 DD_LAYOUT_CANONICAL, DD_LAYOUT_INTERNAL = 0, 1
 

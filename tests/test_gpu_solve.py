@@ -14,7 +14,7 @@ from gpu_helpers import ctx_for, gauge, rel
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [dd.DD_PREC_FP16, dd.DD_PREC_FP32], ids=["mixed", "fp32"])
+@pytest.mark.parametrize("prec", [dd.DD_PREC_FP16, dd.DD_PREC_FP32, dd.DD_PREC_FP16_H2], ids=["mixed", "fp32", "half2"])
 def test_solve_8x4_workload(prec):
     w = synth.WORKLOADS["8^4"]
     U = synth.make_gauge(w).numpy()
