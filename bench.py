@@ -515,7 +515,9 @@ def lattices_case(args):
 def workload_case(args):
     """One mixed-precision solve of a named workload (the larger lattices: 48^3x96,
     64^3x128), device-resident f and x, with the times of input generation, set-up and
-    solve; the true residual is the library's FP64 recomputation."""
+    solve; the true residual is the library's FP64 recomputation.  With --nrhs N > 1
+    (the batched 24^3x48 workload: 12 point sources, then Gaussian ones) the N solves run
+    in lockstep and, for comparison, one after another."""
     import torch
 
     import synth
@@ -530,7 +532,14 @@ def workload_case(args):
         U = synth.ape_smear(U, 0.5, w.ape_steps)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
-    f = synth.make_sources(w)[0]
+    nr = args.nrhs
+    if nr > 1:   # the batched workload's mix: the 12 point sources first, then Gaussian ones
+        pts = synth.point_sources(w.dims)
+        fs = pts[:min(nr, 12)] + synth.make_sources(w, max(0, nr - 12))
+        f = np.stack(fs)
+        del pts, fs
+    else:
+        f = synth.make_sources(w)[0]
     ctx = dd.Context(w.dims, w.domain, True, st.cuda_stream)
     t1 = time.perf_counter()
     ctx.dd_load_gauge(torch.view_as_real(U).contiguous(), dd.DD_DEVICE)
@@ -544,16 +553,28 @@ def workload_case(args):
     x_dev = torch.zeros_like(f_dev)
     m = args.m or w.m
     kw = dict(tol=w.tol, m=m, k=w.k, max_iter=20000, i_schwarz=w.i_schwarz, i_domain=w.i_domain)
-    t2 = time.perf_counter()
-    info = ctx.dd_solve(f_dev, x_dev, where=dd.DD_DEVICE, **kw)
-    t_solve = time.perf_counter() - t2
-    print(json.dumps({"case": "workload_solve", "workload": w.name, "lattice": list(w.dims), "kappa": w.kappa,
-                      "csw": w.csw, "domain": list(w.domain), "i_schwarz": w.i_schwarz, "i_domain": w.i_domain,
-                      "m": m, "k": w.k, "iterations": info.iterations, "restarts": info.restarts,
-                      "true_rel_residual": info.true_rel_residual, "solve_s": info.t_total, "wall_s": t_solve,
-                      "split_s": {"A": info.t_A, "M": info.t_M, "GS": info.t_GS, "other": info.t_other},
-                      "gen_random_s": t_rand, "gen_total_s": t_gen, "setup_s": t_setup,
-                      "device_gb_in_use": (lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info())}))
+
+    def run():
+        x_dev.zero_()
+        t = time.perf_counter()
+        info = ctx.dd_solve(f_dev, x_dev, nrhs=nr, where=dd.DD_DEVICE, **kw)
+        return info, time.perf_counter() - t
+
+    out = {"case": "workload_solve", "workload": w.name, "lattice": list(w.dims), "kappa": w.kappa, "csw": w.csw,
+           "domain": list(w.domain), "i_schwarz": w.i_schwarz, "i_domain": w.i_domain, "m": m, "k": w.k,
+           "nrhs": nr, "gen_random_s": t_rand, "gen_total_s": t_gen, "setup_s": t_setup}
+    forms = [("lockstep", "0"), ("sequential", "1")] if nr > 1 else [("single", "0")]
+    for name, seq in forms:
+        os.environ["DD_SEQUENTIAL_RHS"] = seq
+        if nr > 1:
+            run()   # warm-up: allocations and first launches
+        info, wall = run()
+        out[name] = {"iterations": info.iterations, "restarts": info.restarts,
+                     "true_rel_residual": info.true_rel_residual, "solve_s": info.t_total, "wall_s": wall,
+                     "split_s": {"A": info.t_A, "M": info.t_M, "GS": info.t_GS, "other": info.t_other}}
+    os.environ.pop("DD_SEQUENTIAL_RHS", None)
+    out["device_gb_in_use"] = (lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info())
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

@@ -162,7 +162,13 @@ dd_status dd_sap_precondition_noalloc(dd_ctx* ctx, const float* in, float* out, 
  * initial guess on entry (zeros are fine) and the solution on exit.  Outer FGMRES-DR
  * in FP32 vectors with FP64 Hessenberg, Gram-Schmidt coefficients and least squares;
  * x accumulated in FP64 and the residual recomputed with the FP64 operator at every
- * restart (reliable update).  info may be NULL. */
+ * restart (reliable update).  info may be NULL.
+ * With nrhs > 1 (and threads_per_site 0 or 2) the right-hand sides are solved in
+ * lockstep: each keeps its own basis, restarts and stopping point, while every Arnoldi
+ * step applies M and A to all unconverged ones in one launch each (per Schwarz
+ * half-sweep); this holds nrhs copies of the solver's buffers.  DD_SEQUENTIAL_RHS=1 in
+ * the environment solves them one after another instead.  info sums iterations,
+ * restarts and updates over the right-hand sides; true_rel_residual is the largest. */
 dd_status dd_solve(dd_ctx* ctx, const double* f, double* x, int nrhs, int where, const dd_solve_params* p,
                    dd_solve_info* info);
 

@@ -109,6 +109,12 @@ struct dd_ctx {
   void* scratch_in = nullptr;
   void* scratch_out = nullptr;
   SolverBuffers sv;
+  // lockstep solves: one set of solver buffers per right-hand side, and the device / pinned
+  // host arrays of per-right-hand-side pointers handed to the batched launches
+  std::vector<SolverBuffers> lock;
+  void** lock_ptrs = nullptr;
+  void** h_lock_ptrs = nullptr;
+  int lock_cap = 0;
   std::vector<void*> allocs;
 };
 
@@ -593,8 +599,7 @@ static void release(dd_ctx* c, void* p) {
 }
 
 // Free the outer solver's buffers (they are sized by the basis size m).
-static void release_solver(dd_ctx* c) {
-  SolverBuffers& s = c->sv;
+static void free_solver_buffers(dd_ctx* c, SolverBuffers& s) {
   cudaStreamSynchronize(c->st);
   for (void* p : {(void*)s.V, (void*)s.Z, (void*)s.w, (void*)s.x64,
                   (void*)s.f64, (void*)s.r64, (void*)s.canon64, (void*)s.H, (void*)s.R, (void*)s.P, (void*)s.Hn,
@@ -615,10 +620,20 @@ static void release_solver(dd_ctx* c) {
   s = SolverBuffers();
 }
 
-static dd_status ensure_solver(dd_ctx* c, int m) {
-  SolverBuffers& s = c->sv;
-  if (s.m >= m) return DD_OK;
-  if (s.m) release_solver(c);
+static void release_solver(dd_ctx* c) {
+  free_solver_buffers(c, c->sv);
+  for (SolverBuffers& b : c->lock) free_solver_buffers(c, b);
+  c->lock.clear();
+  release(c, c->lock_ptrs);
+  c->lock_ptrs = nullptr;
+  if (c->h_lock_ptrs) cudaFreeHost(c->h_lock_ptrs);
+  c->h_lock_ptrs = nullptr;
+  c->lock_cap = 0;
+}
+
+// Krylov basis, FP64 fields and small dense buffers for basis size m; streams and events
+// only for the context's own solver (the lockstep right-hand sides run on its stream).
+static dd_status alloc_solver_buffers(dd_ctx* c, SolverBuffers& s, int m, bool streams) {
   const Geom& g = c->g;
   long long n4 = g.V * 6;
   size_t vb = (size_t)n4 * 16;
@@ -650,14 +665,20 @@ static dd_status ensure_solver(dd_ctx* c, int m) {
   for (zd** p : {&s.h_c0, &s.h_y, &s.h_cn, &s.h_theta})
     if (cudaMallocHost(p, (m + 2) * sizeof(zd)) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned deflation buffers");
   s.h_dw = new DeflateWork();
-  if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s.side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s.ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s.ev_join, cudaEventDisableTiming) != cudaSuccess)
+  if (streams && (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+                  cudaStreamCreateWithFlags(&s.side, cudaStreamNonBlocking) != cudaSuccess ||
+                  cudaEventCreateWithFlags(&s.ev_in, cudaEventDisableTiming) != cudaSuccess ||
+                  cudaEventCreateWithFlags(&s.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                  cudaEventCreateWithFlags(&s.ev_join, cudaEventDisableTiming) != cudaSuccess))
     return fail(c, DD_ERR_CUDA, "solver stream");
   s.m = m;
   return DD_OK;
+}
+
+static dd_status ensure_solver(dd_ctx* c, int m) {
+  if (c->sv.m >= m) return DD_OK;
+  if (c->sv.m) release_solver(c);
+  return alloc_solver_buffers(c, c->sv, m, true);
 }
 
 struct Timer {
@@ -712,9 +733,10 @@ static dd_status read_status(dd_ctx* c, int n = 4) {
   return cuda_check(c, cudaStreamSynchronize(c->st), "solver step");
 }
 
-// rho2 = |f - A x|^2 into s.nrm2 (device) and return it on the host.
-static dd_status true_residual(dd_ctx* c, double* rho2) {
-  SolverBuffers& s = c->sv;
+// rho2 = |f - A x|^2 into s.nrm2 (device) and return it on the host (s: the context's own
+// solver buffers unless given).
+static dd_status true_residual(dd_ctx* c, double* rho2, SolverBuffers* sp = nullptr) {
+  SolverBuffers& s = sp ? *sp : c->sv;
   TRY(apply_internal(c, s.x64, s.r64, P64, s.f64));
   launch_norm2_64(s.r64, c->g.V * 12, s.partial, c->st);
   launch_reduce_partials(s.partial, 1, s.nrm2, 0, c->st);
@@ -909,6 +931,295 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
   return rc;
 }
 
+// ------------------------------------------------------------------ lockstep right-hand sides
+// Several right-hand sides solved together.  Each keeps its own Krylov basis, Hessenberg
+// matrix, restarts and stopping point, with the same steps as solve_one; they share the
+// two large applications of every Arnoldi step: the Schwarz preconditioner runs as one
+// launch per half-sweep over all active right-hand sides (each CTA stages its domain's
+// links and Schwarz matrices once for all of them) and the operator as one launch with
+// two right-hand sides per thread.  Each right-hand side sits at its own step j, so both
+// launches take device arrays of input and output pointers.
+struct LockRhs {
+  double nf = 0, rho2 = 0, rel = 0, rho_cycle = 0;
+  int j = 0, j0 = 0;
+  int iters = 0, restarts = 0, reliable = 0, deflated = 0;
+  bool done = false;
+  dd_status rc = DD_OK;
+};
+
+static dd_status ensure_lock(dd_ctx* c, int nrhs, int m) {
+  bool ok = (int)c->lock.size() >= nrhs;
+  for (int r = 0; ok && r < nrhs; ++r) ok = c->lock[r].m >= m;
+  if (!ok) {
+    for (SolverBuffers& b : c->lock) free_solver_buffers(c, b);
+    c->lock.clear();
+    c->lock.resize(nrhs);
+    for (int r = 0; r < nrhs; ++r) TRY(alloc_solver_buffers(c, c->lock[r], m, false));
+  }
+  if (c->lock_cap < nrhs) {
+    release(c, c->lock_ptrs);
+    if (c->h_lock_ptrs) cudaFreeHost(c->h_lock_ptrs);
+    c->lock_ptrs = nullptr;
+    c->h_lock_ptrs = nullptr;
+    TRY(dalloc(c, &c->lock_ptrs, 3 * (size_t)nrhs * sizeof(void*)));
+    if (cudaMallocHost(&c->h_lock_ptrs, 3 * (size_t)nrhs * sizeof(void*)) != cudaSuccess)
+      return fail(c, DD_ERR_OOM, "pinned pointer lists");
+    c->lock_cap = nrhs;
+  }
+  return DD_OK;
+}
+
+// z_r = M v_r for na right-hand sides given by device pointer lists.
+static dd_status sap_run_list(dd_ctx* c, const float4* const* vl, float4* const* zl, const dd_sap_params* p, int na) {
+  int prec = sap_prec(p->storage_prec);
+  TRY(ensure_sap(c, prec, na));
+  SapState S = sap_state(c, prec, p, na);
+  S.vlist = vl;
+  S.zlist = zl;
+  for (int s = 0; s < p->i_schwarz; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      int first = s == 0, use_faces = !(s == 0 && colour == 0), last = s == p->i_schwarz - 1;
+      if (sap_half_sweep(c->g, S, colour, first, use_faces, last, nullptr, nullptr, p->i_domain, c->st))
+        return fail(c, DD_ERR_CUDA, std::string("Schwarz launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+      TRY(launched(c));
+    }
+  return DD_OK;
+}
+
+// Gram-Schmidt of step j and the Hessenberg update for one right-hand side (the sequence
+// of solve_one, launched directly), then its status into the pinned mirror.
+static dd_status lock_gs(dd_ctx* c, SolverBuffers& s, int j, int m) {
+  const long long n4 = c->g.V * 6;
+  const int ldh = m + 1;
+  float4* vn = s.V + (long long)(j + 1) * n4;
+  double2* nrm_a = s.nrm2 + 1;
+  double2* nrm_b = s.nrm2 + 2;
+  int nk = launch_gs_dot(s.V, j + 1, n4, s.w, s.partial, nullptr, 0, c->st);
+  launch_gs_reduce(s.partial, j + 1, (double2*)s.hA, nullptr, 0, c->st);
+  launch_gs_project(vn, s.w, s.V, j + 1, n4, (const double2*)s.hA, s.partial2, nullptr, 0, c->st);
+  launch_gs_reduce(s.partial2, 0, nrm_a, nullptr, 0, c->st);
+  gs_decide_kernel<<<1, 1, 0, c->st>>>(s.hA, j + 1, nrm_a, s.hB, s.flag, s.nu2);
+  nk += launch_gs_dot(s.V, j + 1, n4, vn, s.partial, s.flag, 1, c->st);
+  launch_gs_reduce(s.partial, j + 1, (double2*)s.hB, s.flag, 1, c->st);
+  launch_gs_project(vn, vn, s.V, j + 1, n4, (const double2*)s.hB, s.partial2, s.flag, 1, c->st);
+  launch_gs_reduce(s.partial2, 0, nrm_b, s.flag, 1, c->st);
+  gs_decide2_kernel<<<1, 1, 0, c->st>>>(s.flag, nrm_b, s.nu2);
+  launch_scale_inplace(vn, n4, s.nu2, c->st);
+  arnoldi_finish_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, j, s.hA, s.hB, s.nu2, s.lsq, s.g, s.status);
+  TRY(launched(c, nk + 10));
+  return cuda_check(c, cudaMemcpyAsync(s.h_status, s.status, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st),
+                    "status");
+}
+
+// End of a cycle of one right-hand side after mm Arnoldi steps: x64 += Z y, FP64 residual,
+// then a deflated (or plain) restart, as in solve_one.
+static dd_status lock_end_cycle(dd_ctx* c, SolverBuffers& s, LockRhs& R, int mm, const dd_solve_params* p) {
+  const long long n4 = c->g.V * 6;
+  const int m = p->m, k = p->k, ldh = m + 1;
+  const double defl_tol = 1e-2;
+  lsq_solve_kernel<<<1, 1, 0, c->st>>>(s.R, ldh, mm, s.g, s.y);
+  launch_x_update(s.x64, s.Z, mm, n4, (const double2*)s.y, c->st);
+  TRY(launched(c, 2));
+  TRY(true_residual(c, &R.rho2, &s));
+  R.reliable++;
+  R.rel = sqrt(R.rho2) / R.nf;
+  if (!isfinite(R.rel)) {
+    R.rc = fail(c, DD_ERR_NONFINITE, "non-finite residual");
+    R.done = true;
+    return DD_OK;
+  }
+  if (R.rel <= p->tol) {
+    R.done = true;
+    return DD_OK;
+  }
+  if (R.iters >= p->max_iter) {
+    R.rc = fail(c, DD_ERR_NOT_CONVERGED, "iteration limit reached");
+    R.done = true;
+    return DD_OK;
+  }
+  R.restarts++;
+  bool done_defl = false;
+  if (k > 0 && mm > k) {
+    size_t hb = (size_t)ldh * (m + 1) * sizeof(zd);
+    TRY(cuda_check(c, cudaMemcpyAsync(s.h_H, s.H, hb, cudaMemcpyDeviceToHost, c->st), "H"));
+    TRY(cuda_check(c, cudaMemcpyAsync(s.h_c0, s.c0, (m + 1) * sizeof(zd), cudaMemcpyDeviceToHost, c->st), "c"));
+    TRY(cuda_check(c, cudaMemcpyAsync(s.h_y, s.y, m * sizeof(zd), cudaMemcpyDeviceToHost, c->st), "y"));
+    TRY(cuda_check(c, cudaStreamSynchronize(c->st), "deflation inputs"));
+    int drc = deflate(s.h_H, ldh, mm, k, s.h_c0, s.h_y, s.h_P, s.h_Hn, s.h_cn, s.h_theta, *s.h_dw);
+    if (drc == 0) {
+      TRY(cuda_check(c, cudaMemcpyAsync(s.P, s.h_P, hb, cudaMemcpyHostToDevice, c->st), "P"));
+      TRY(cuda_check(c, cudaMemcpyAsync(s.Hn, s.h_Hn, hb, cudaMemcpyHostToDevice, c->st), "Hn"));
+      int nk = launch_recombine(s.V, s.V, mm + 1, k + 1, n4, (const double2*)s.P, ldh, c->st);
+      nk += launch_recombine(s.Z, s.Z, mm, k, n4, (const double2*)s.P, ldh, c->st);
+      launch_r64_to_v32(s.w, s.r64, n4, s.nrm2, c->st);
+      nk += launch_multi_dot(s.V, k + 1, n4, s.w, s.partial, c->st);
+      launch_reduce_partials(s.partial, k + 1, (double2*)s.cp, 0, c->st);
+      scale_coeffs_kernel<<<1, 1, 0, c->st>>>(s.cp, k + 1, s.nrm2);
+      TRY(launched(c, nk + 3));
+      std::vector<zd> cp(k + 1);
+      TRY(cuda_check(c, cudaMemcpyAsync(cp.data(), s.cp, (k + 1) * sizeof(zd), cudaMemcpyDeviceToHost, c->st), "cp"));
+      TRY(cuda_check(c, cudaStreamSynchronize(c->st), "cp"));
+      double pc = 0;
+      for (auto& z : cp) pc += abs2(z);
+      double miss = sqrt(fmax(0.0, 1.0 - pc / R.rho2));
+      if (miss <= defl_tol) {
+        restart_lsq_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, k, s.Hn, s.cp, s.g, s.c0, s.lsq, s.status);
+        TRY(launched(c));
+        R.j0 = k;
+        done_defl = true;
+        R.deflated++;
+      }
+    }
+  }
+  if (!done_defl) {
+    launch_r64_to_v32(s.V, s.r64, n4, s.nrm2, c->st);
+    plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq);
+    TRY(launched(c, 2));
+    R.j0 = 0;
+  }
+  R.j = R.j0;
+  R.rho_cycle = sqrt(R.rho2);
+  return DD_OK;
+}
+
+static dd_status solve_lockstep(dd_ctx* c, const double* f, double* x, int nrhs, int where, const dd_solve_params* p,
+                                dd_solve_info* info) {
+  const Geom& g = c->g;
+  const long long n4 = g.V * 6;
+  const int m = p->m;
+  const double tol = p->tol;
+  TRY(ensure_lock(c, nrhs, m));
+  std::vector<LockRhs> R(nrhs);
+  size_t cb = (size_t)g.V * 24 * 8;
+  cudaMemcpyKind in_kind = where == DD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaMemcpyKind out_kind = where == DD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  cudaEvent_t e0, e1, e2, e3, tstart, tend;
+  for (cudaEvent_t* e : {&e0, &e1, &e2, &e3, &tstart, &tend}) cudaEventCreate(e);
+  cudaEventRecord(tstart, c->st);
+  double tA = 0, tM = 0, tGS = 0;
+  dd_status rc = DD_OK;
+  // set-up: fields in, FP64 residual, first basis vector
+  for (int r = 0; r < nrhs && rc == DD_OK; ++r) {
+    SolverBuffers& s = c->lock[r];
+    TRY(cuda_check(c, cudaMemcpyAsync(s.canon64, f + (size_t)r * g.V * 24, cb, in_kind, c->st), "copy f"));
+    launch_pack_spinor(g, s.canon64, P64, view(g, s.f64, P64), c->st);
+    TRY(cuda_check(c, cudaMemcpyAsync(s.canon64, x + (size_t)r * g.V * 24, cb, in_kind, c->st), "copy x"));
+    launch_pack_spinor(g, s.canon64, P64, view(g, s.x64, P64), c->st);
+    launch_norm2_64(s.f64, g.V * 12, s.partial, c->st);
+    launch_reduce_partials(s.partial, 1, s.nrm2, 0, c->st);
+    TRY(launched(c, 4));
+    double2 h;
+    TRY(cuda_check(c, cudaMemcpyAsync(&h, s.nrm2, sizeof(double2), cudaMemcpyDeviceToHost, c->st), "norm f"));
+    TRY(cuda_check(c, cudaStreamSynchronize(c->st), "norm f"));
+    if (h.x == 0.0) {   // zero source: x = 0
+      cudaMemsetAsync(s.x64, 0, field_bytes(g, P64), c->st);
+      R[r].done = true;
+      continue;
+    }
+    R[r].nf = sqrt(h.x);
+    TRY(true_residual(c, &R[r].rho2, &s));
+    R[r].reliable++;
+    R[r].rel = sqrt(R[r].rho2) / R[r].nf;
+    if (!isfinite(R[r].rel)) {
+      R[r].rc = fail(c, DD_ERR_NONFINITE, "non-finite residual");
+      R[r].done = true;
+    } else if (R[r].rel <= tol) {
+      R[r].done = true;
+    } else {
+      launch_r64_to_v32(s.V, s.r64, n4, s.nrm2, c->st);
+      plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, m + 1, m, s.nrm2, s.g, s.c0, s.lsq);
+      TRY(launched(c, 2));
+      R[r].rho_cycle = sqrt(R[r].rho2);
+    }
+  }
+  std::vector<int> act;
+  const float4** vl = (const float4**)c->lock_ptrs;
+  while (rc == DD_OK) {
+    act.clear();
+    for (int r = 0; r < nrhs; ++r)
+      if (!R[r].done) act.push_back(r);
+    if (act.empty()) break;
+    const int na = (int)act.size();
+    void** hp = c->h_lock_ptrs;
+    for (int i = 0; i < na; ++i) {
+      SolverBuffers& s = c->lock[act[i]];
+      hp[i] = s.V + (long long)R[act[i]].j * n4;
+      hp[na + i] = s.Z + (long long)R[act[i]].j * n4;
+      hp[2 * na + i] = s.w;
+    }
+    TRY(cuda_check(c, cudaMemcpyAsync(c->lock_ptrs, hp, 3 * (size_t)na * sizeof(void*), cudaMemcpyHostToDevice, c->st),
+                   "pointer lists"));
+    cudaEventRecord(e0, c->st);
+    TRY(sap_run_list(c, vl, (float4* const*)(c->lock_ptrs + na), &p->sap, na));
+    cudaEventRecord(e1, c->st);
+    launch_apply_A_multi_list(g, gauge_view(c, P32), clover_view(c, P32), (const float4* const*)(c->lock_ptrs + na),
+                              (float4* const*)(c->lock_ptrs + 2 * na), na, c->st);
+    TRY(launched(c));
+    cudaEventRecord(e2, c->st);
+    for (int r : act) TRY(lock_gs(c, c->lock[r], R[r].j, m));
+    cudaEventRecord(e3, c->st);
+    TRY(cuda_check(c, cudaStreamSynchronize(c->st), "lockstep step"));
+    float ms;
+    cudaEventElapsedTime(&ms, e0, e1); tM += ms * 1e-3;
+    cudaEventElapsedTime(&ms, e1, e2); tA += ms * 1e-3;
+    cudaEventElapsedTime(&ms, e2, e3); tGS += ms * 1e-3;
+    for (int r : act) {
+      LockRhs& Q = R[r];
+      SolverBuffers& s = c->lock[r];
+      Q.iters++;
+      const double est = s.h_status[0];
+      if (!isfinite(est) || !isfinite(s.h_status[2])) {
+        Q.rc = fail(c, DD_ERR_NONFINITE, "non-finite Arnoldi step");
+        Q.done = true;
+        continue;
+      }
+      if (c->trace)
+        fprintf(stderr, "[dd] rhs %d it %d j %d est/rho %.3e\n", r, Q.iters, Q.j, est / Q.rho_cycle);
+      // the cycle ends when the target is met, FP32 vectors cannot resolve further, the
+      // basis is full or the iteration budget is spent
+      if (est <= 0.5 * tol * Q.nf || est <= 2e-6 * Q.rho_cycle || Q.iters >= p->max_iter || Q.j + 1 == m) {
+        TRY(lock_end_cycle(c, s, Q, Q.j + 1, p));
+      } else {
+        Q.j++;
+      }
+    }
+  }
+  cudaEventRecord(tend, c->st);
+  cudaEventSynchronize(tend);
+  float ms_total = 0;
+  cudaEventElapsedTime(&ms_total, tstart, tend);
+  for (cudaEvent_t e : {e0, e1, e2, e3, tstart, tend}) cudaEventDestroy(e);
+  dd_status worst = DD_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    SolverBuffers& s = c->lock[r];
+    launch_unpack_spinor(g, view(g, s.x64, P64), s.canon64, P64, c->st);
+    TRY(launched(c));
+    TRY(cuda_check(c, cudaMemcpyAsync(x + (size_t)r * g.V * 24, s.canon64, cb, out_kind, c->st), "copy x out"));
+    if (R[r].rc != DD_OK && worst == DD_OK) worst = R[r].rc;
+  }
+  TRY(cuda_check(c, cudaStreamSynchronize(c->st), "solve"));
+  if (info) {
+    for (const LockRhs& Q : R) {
+      info->iterations += Q.iters;
+      info->restarts += Q.restarts;
+      info->reliable_updates += Q.reliable;
+      info->deflated_restarts += Q.deflated;
+      info->true_rel_residual = fmax(info->true_rel_residual, Q.rel);
+      const double V = (double)g.V;
+      info->flops_nominal += Q.iters * (1848.0 * V + p->sap.i_schwarz * (p->sap.i_domain + 1) * 1848.0 * V) +
+                             Q.reliable * 1848.0 * V;
+    }
+    info->t_total = ms_total * 1e-3;
+    info->t_A = tA;
+    info->t_M = tM;
+    info->t_GS = tGS;
+    info->t_other = ms_total * 1e-3 - tA - tM - tGS;
+    info->status = worst;
+  }
+  if (worst == DD_OK) TRY(sap_error_flag(c));
+  return worst;
+}
+
 extern "C" dd_status dd_solve(dd_ctx* c, const double* f, double* x, int nrhs, int where, const dd_solve_params* p,
                               dd_solve_info* info) {
   if (!c || !f || !x || !p || nrhs < 1) return DD_ERR_INVALID;
@@ -935,6 +1246,11 @@ extern "C" dd_status dd_solve(dd_ctx* c, const double* f, double* x, int nrhs, i
   cudaStreamWaitEvent(s.stream, s.ev_in, 0);
   StreamSwap swap{c, c->st};
   c->st = s.stream;
+  // several right-hand sides in lockstep, unless the domain solve runs one thread per site
+  // (no batched kernel) or DD_SEQUENTIAL_RHS=1 asks for one solve after another
+  const char* seq = getenv("DD_SEQUENTIAL_RHS");
+  if (nrhs > 1 && p->sap.threads_per_site != 1 && !(seq && seq[0] == '1'))
+    return solve_lockstep(c, f, x, nrhs, where, p, info);
   const Geom& g = c->g;
   size_t cb = (size_t)g.V * 24 * 8;
   cudaMemcpyKind in_kind = where == DD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;

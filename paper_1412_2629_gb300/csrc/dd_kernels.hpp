@@ -39,6 +39,9 @@ void launch_build_clover(const Geom& g, const double* canon, double kappa, doubl
 // stride = one field): each link and clover block is loaded once per site.
 void launch_apply_A_multi(const Geom& g, GaugeView U, CloverView C, FieldView in, FieldView out, int nrhs,
                           cudaStream_t st);
+// The same for FP32 fields given by device arrays of nrhs input and output pointers.
+void launch_apply_A_multi_list(const Geom& g, GaugeView U, CloverView C, const float4* const* in,
+                               float4* const* out, int nrhs, cudaStream_t st);
 // out = A in, or out = f - A in when f != nullptr.  FP64 and FP32 fields use the matching
 // gauge/clover precision; FP16 fields use FP16 gauge/clover and FP32 arithmetic.
 void launch_apply_A(const Geom& g, GaugeView U, CloverView C, FieldView in, FieldView out, const FieldView* f,
@@ -61,6 +64,10 @@ struct SapState {
   bool inject_wait_timeout = false;   // test hook: make the bounded wait run out (no fault)
   int nrhs = 1;                // right-hand sides in one launch (their buffers follow each other)
   bool half_arith = false;     // FP16 storage with packed FP16 hop and clover products
+  // device arrays of nrhs input / output pointers (FP32 internal fields), instead of v and
+  // z with their fixed stride; two threads per site only
+  const float4* const* vlist = nullptr;
+  float4* const* zlist = nullptr;
   long long r_bytes = 0;       // bytes of one right-hand side's residual / solution storage
   long long u_bytes = 0;
 };

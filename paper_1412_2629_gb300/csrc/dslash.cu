@@ -8,6 +8,8 @@
 // the links.  The diagonal 1/(2 kappa) is folded into the stored clover.
 // Bytes per site (algorithmic, each field read once): 4 links + clover + in + out =
 // 192 reals; FP32 768 B, FP64 1536 B, FP16 384 B + 8 B of spinor norms.
+#include <type_traits>
+
 #include "dd_kernels.hpp"
 
 namespace dd {
@@ -134,7 +136,8 @@ __device__ inline void hop_pair_multi(const Geom& g, const Site& st, long long s
 template <typename T, int NR>
 __global__ void __launch_bounds__(128) apply_A_multi_kernel(Geom g, LinkPtr<T> U, CloverPtr<T> C, SpinorPtr<T> in0,
                                                              SpinorPtr<T> out0, long long unit_stride,
-                                                             long long norm_stride, int nrhs) {
+                                                             long long norm_stride, int nrhs,
+                                                             const float4* const* in_list, float4* const* out_list) {
   typedef typename Arith<T>::type R;
   long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (s >= g.V) return;
@@ -149,6 +152,12 @@ __global__ void __launch_bounds__(128) apply_A_multi_kernel(Geom g, LinkPtr<T> U
     out[r].p += rr * unit_stride;
     shift_norm(in[r], rr * norm_stride);
     shift_norm(out[r], rr * norm_stride);
+    if constexpr (std::is_same<T, float>::value) {
+      if (in_list) {   // FP32 fields anywhere in memory
+        in[r].p = const_cast<float4*>(in_list[rr]);
+        out[r].p = out_list[rr];
+      }
+    }
   }
   Site st = decode(g, s);
   Spinor<R> acc[NR];
@@ -181,15 +190,24 @@ void launch_apply_A_multi(const Geom& g, GaugeView U, CloverView C, FieldView in
   if (in.prec == P32) {
     apply_A_multi_kernel<float, NR><<<grid, 128, 0, st>>>(
         g, LinkPtr<float>{(const float2*)U.links}, CloverPtr<float>{(const float4*)C.m},
-        SpinorPtr<float>{(float4*)in.data}, SpinorPtr<float>{(float4*)out.data}, g.V * 6, 0, nrhs);
+        SpinorPtr<float>{(float4*)in.data}, SpinorPtr<float>{(float4*)out.data}, g.V * 6, 0, nrhs, nullptr, nullptr);
   } else {
     // FP16 fields are V * 52 bytes each (values, then the per-site norms) and follow each
     // other: 13 V / 4 uint4 units or 13 V floats apart (V is a multiple of 64)
     apply_A_multi_kernel<__half, NR><<<grid, 128, 0, st>>>(
         g, LinkPtr<__half>{(const uint32_t*)U.links}, CloverPtr<__half>{(const uint4*)C.m},
         SpinorPtr<__half>{(uint4*)in.data, in.norm}, SpinorPtr<__half>{(uint4*)out.data, out.norm}, 13 * g.V / 4,
-        13 * g.V, nrhs);
+        13 * g.V, nrhs, nullptr, nullptr);
   }
+}
+
+void launch_apply_A_multi_list(const Geom& g, GaugeView U, CloverView C, const float4* const* in,
+                               float4* const* out, int nrhs, cudaStream_t st) {
+  const int NR = 2;
+  dim3 grid((unsigned)((g.V + 127) / 128), (unsigned)((nrhs + NR - 1) / NR));
+  apply_A_multi_kernel<float, NR><<<grid, 128, 0, st>>>(
+      g, LinkPtr<float>{(const float2*)U.links}, CloverPtr<float>{(const float4*)C.m}, SpinorPtr<float>{nullptr},
+      SpinorPtr<float>{nullptr}, 0, 0, nrhs, in, out);
 }
 
 }  // namespace dd

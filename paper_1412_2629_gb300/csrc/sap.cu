@@ -310,6 +310,8 @@ struct SapArgs {
   float4* faces;
   const float4* v;
   float4* z;
+  const float4* const* vptr;   // if set: input / output of right-hand side r at vptr[r] / zptr[r]
+  float4* const* zptr;
   int* err;
   // Bound of the wait for the staged matrices, and extra bytes the barrier is told to
   // expect: 0 normally; a test sets it so the wait runs out and the error path is taken.
@@ -1051,7 +1053,7 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   EvenStore<VT> rst{reinterpret_cast<decltype(EvenStore<VT>::p)>((char*)a.r_store + rhs * a.r_bytes), rnr};
   {
     Spinor<float> r;
-    const SpinorPtr<float> vin{const_cast<float4*>(a.v) + rhs * a.v_stride};
+    const SpinorPtr<float> vin{const_cast<float4*>(a.vptr ? a.vptr[rhs] : a.v + rhs * a.v_stride)};
     if (a.first) vin.load(g, s_site, r);
     else if (h == 0) rst.load(d, Hd, i, r);
     else zero(r);
@@ -1211,7 +1213,7 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
       for (int c = 0; c < 3; ++c) u.c[s][c] = u.c[s][c] + dl.c[s][c];
   }
   if (a.last) {
-    SpinorPtr<float> zo{a.z + rhs * a.v_stride};
+    SpinorPtr<float> zo{a.zptr ? a.zptr[rhs] : a.z + rhs * a.v_stride};
     zo.store(g, s_site, u);
   } else {
     ust.store(g, s_site, u);
@@ -1338,7 +1340,8 @@ int sap_half_sweep_lattices(const Geom* gs, const SapState* Ss, int nlat, int co
 int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int use_faces, int last,
                    const float4* v, float4* z, int i_domain, cudaStream_t st) {
   if (g.Hd > SAP_MAX_THREADS || (g.Hd & 31)) return -1;
-  if (S.nrhs > 1 && S.threads_per_site != 2) return -1;   // only the pair kernel loops over right-hand sides
+  // only the pair kernel loops over right-hand sides and reads pointer lists
+  if ((S.nrhs > 1 || S.vlist) && S.threads_per_site != 2) return -1;
   SapArgs a = make_args(g, S, colour, first, use_faces, last, v, z, i_domain);
   int grid = g.ND / 2;
   bool ms = S.mat_in_smem;
@@ -1373,6 +1376,8 @@ static SapArgs make_args(const Geom& g, const SapState& S, int colour, int first
   a.faces = S.faces;
   a.v = v;
   a.z = z;
+  a.vptr = S.vlist;
+  a.zptr = S.zlist;
   a.err = S.err;
   a.nrhs = S.nrhs;
   a.v_stride = g.V * 6;
