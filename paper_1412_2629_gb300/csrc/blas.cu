@@ -105,63 +105,6 @@ void launch_reduce_partials(const double2* partial, int nv, double2* out, int ac
   reduce_partials_kernel<<<nv, 256, 0, st>>>(partial, blas_partials_blocks(), nv, out, accumulate);
 }
 
-// w -= sum_i h_i V_i; optionally partial[b] = |w|^2 over the block's share.
-template <int NV>
-__global__ void __launch_bounds__(BT) multi_axpy_kernel(float4* w, const float4* V, int v0, int nv, long long n4,
-                                                        const double2* h, double2* norm_partial, int final_pass) {
-  __shared__ float2 hs[NV];
-  if (threadIdx.x < NV) {
-    int i = v0 + threadIdx.x;
-    hs[threadIdx.x] = i < nv ? make_float2((float)h[i].x, (float)h[i].y) : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  float nrm = 0.f;
-  for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n4; q += (long long)gridDim.x * BT) {
-    float4 a = w[q];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      if (v0 + i < nv) {
-        float4 v = V[(long long)(v0 + i) * n4 + q];
-        float2 c = hs[i];
-        a.x -= c.x * v.x - c.y * v.y;
-        a.y -= c.x * v.y + c.y * v.x;
-        a.z -= c.x * v.z - c.y * v.w;
-        a.w -= c.x * v.w + c.y * v.z;
-      }
-    }
-    w[q] = a;
-    if (final_pass) nrm += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
-  }
-  if (final_pass && norm_partial) {
-    double2 acc[1] = {make_double2(nrm, 0.0)};
-    __shared__ double2 out[1];
-    block_reduce<1>(acc, out);
-    if (threadIdx.x == 0) norm_partial[blockIdx.x] = out[0];
-  }
-}
-
-int launch_multi_axpy(float4* w, const float4* V, int nv, long long n4, const double2* h, double2* norm_partial,
-                      cudaStream_t st) {
-  int nb = blas_partials_blocks(), n = 0;
-  for (int v0 = 0; v0 < nv; v0 += NCHUNK, ++n) {
-    int fin = v0 + NCHUNK >= nv;
-    multi_axpy_kernel<NCHUNK><<<nb, BT, 0, st>>>(w, V, v0, nv, n4, h, norm_partial, fin);
-  }
-  return n;
-}
-
-// v = w / sqrt(nrm2)
-__global__ void scale_to_kernel(float4* v, const float4* w, long long n4, const double2* nrm2) {
-  float s = (float)(1.0 / sqrt(nrm2->x));
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
-    float4 a = w[q];
-    v[q] = make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
-  }
-}
-void launch_scale_to(float4* v, const float4* w, long long n4, const double2* nrm2, cudaStream_t st) {
-  scale_to_kernel<<<blas_partials_blocks(), BT, 0, st>>>(v, w, n4, nrm2);
-}
-
 // |x|^2 of an FP64 field (double2 units); exact FP64 arithmetic throughout.
 __global__ void __launch_bounds__(BT) norm2_64_kernel(const double2* x, long long n2, double2* partial) {
   double s = 0;
@@ -276,30 +219,6 @@ int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n
     recombine_launch<16>(nout - l0 < 16 ? nout - l0 : 16, out, V, nv, l0, n4, P, ldp, st);
   return n;
 }
-
-__global__ void copy64_to32_kernel(float4* out, const double2* in, long long n4) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
-    double2 a = in[2 * q], b = in[2 * q + 1];
-    out[q] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
-  }
-}
-void launch_copy64_to32(float4* out, const double2* in, long long n4, cudaStream_t st) {
-  copy64_to32_kernel<<<blas_partials_blocks(), BT, 0, st>>>(out, in, n4);
-}
-
-__global__ void axpy_64_kernel(double2* x, const double2* y, double a, long long n2) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n2; q += (long long)gridDim.x * blockDim.x) {
-    double2 u = x[q], v = y[q];
-    x[q] = make_double2(u.x + a * v.x, u.y + a * v.y);
-  }
-}
-void launch_axpy_64(double2* x, const double2* y, double a, long long n2, cudaStream_t st) {
-  axpy_64_kernel<<<blas_partials_blocks(), BT, 0, st>>>(x, y, a, n2);
-}
-
-}  // namespace dd
-
-namespace dd {
 
 // ------------------------------------------------------------------ Gram-Schmidt passes
 // Classical Gram-Schmidt with selective reorthogonalisation, gated on the device so no

@@ -91,17 +91,11 @@ void* sap_noalloc_scratch();
 int blas_partials_blocks();
 int launch_multi_dot(const float4* V, int nv, long long n4, const float4* w, double2* partial, cudaStream_t st);
 void launch_reduce_partials(const double2* partial, int nv, double2* out, int accumulate, cudaStream_t st);
-int launch_multi_axpy(float4* w, const float4* V, int nv, long long n4, const double2* h, double2* norm_partial,
-                       cudaStream_t st);
-void launch_scale_to(float4* v, const float4* w, long long n4, const double2* nrm2, cudaStream_t st);
 void launch_norm2_64(const double2* x, long long n2, double2* partial, cudaStream_t st);
-void launch_dot_64_32(const float4* V, int nv, long long n4, const double2* r, double2* partial, cudaStream_t st);
 void launch_x_update(double2* x, const float4* Z, int nz, long long n4, const double2* y, cudaStream_t st);
 void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2* nrm2, cudaStream_t st);
 int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n4, const double2* P, int ldp,
                       cudaStream_t st);
-void launch_copy64_to32(float4* out, const double2* in, long long n4, cudaStream_t st);
-void launch_axpy_64(double2* x, const double2* y, double a, long long n2, cudaStream_t st);
 
 // Classical Gram-Schmidt passes with device-gated reorthogonalisation (blas.cu).  A kernel
 // given a gate runs only when *gate == want.
