@@ -681,12 +681,6 @@ static dd_status ensure_solver(dd_ctx* c, int m) {
   return alloc_solver_buffers(c, c->sv, m, true);
 }
 
-struct Timer {
-  cudaEvent_t a, b;
-  Timer() { cudaEventCreate(&a); cudaEventCreate(&b); }
-  ~Timer() { cudaEventDestroy(a); cudaEventDestroy(b); }
-};
-
 // Run a launch sequence of the outer solver: directly on its first use, captured into a
 // CUDA graph on its second (so one-time set-up inside the sequence stays out of the
 // capture), replayed from the graph afterwards.  If capture is not possible the
