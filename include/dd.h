@@ -189,10 +189,14 @@ long long dd_launch_count(const dd_ctx* ctx);
  * load = n / (slots * ceil(n / slots)).  Pure host function. */
 double dd_load_model(long long n_domains_per_colour, int slots);
 
-/* Pick a domain shape and I_domain for this lattice (the context's own shape is not
- * changed): candidates allowed by the constraints above are timed on the device with
- * the current gauge field and clover.  Writes the best shape to domain_out and its SAP
- * parameters to out. */
+/* Pick a domain shape, I_domain and threads per site for this lattice (the context's
+ * own shape is not changed): candidates allowed by the constraints above (extents 2, 4
+ * or 8 per direction, I_domain 2..6) are timed on the device with the current gauge
+ * field and clover, and scored by time per factor of residual reduction of f - A M f.
+ * storage_prec: DD_PREC_FP16, DD_PREC_FP16_H2 or DD_PREC_FP32 (else DD_ERR_INVALID);
+ * out->i_schwarz > 0 is kept, else 16.  Writes the best shape to domain_out and its SAP
+ * parameters to out.  With DD_TRACE set, one line per candidate gives its time, its
+ * residual factor and the load model's estimate (dd_load_model) for that shape. */
 dd_status dd_autotune(dd_ctx* ctx, int storage_prec, int domain_out[4], dd_sap_params* out);
 
 /* Host build of the deflated-restart step that dd_solve runs on the device: given the

@@ -1344,6 +1344,8 @@ __global__ void sub_norm2_kernel(const float4* a, const float4* b, long long n4,
 
 extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4], dd_sap_params* out) {
   if (!c || !domain_out || !out) return DD_ERR_INVALID;
+  if (storage_prec != DD_PREC_FP16 && storage_prec != DD_PREC_FP32 && storage_prec != DD_PREC_FP16_H2)
+    return fail(c, DD_ERR_INVALID, "autotune: storage_prec must be DD_PREC_FP16, DD_PREC_FP16_H2 or DD_PREC_FP32");
   if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
   int i_schwarz = out->i_schwarz > 0 ? out->i_schwarz : 16;
   const int ext[3] = {2, 4, 8};
@@ -1378,6 +1380,7 @@ extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4],
                                                                           sap_mat_fits_smem(t->g, sap_prec(storage_prec))) > 116 * 1024 ? 1 : 2));
             for (int cand = 0; cand < 10; ++cand) {
               const int id = 2 + cand / 2, tps = 1 + cand % 2;
+              if (tps == 1 && storage_prec == DD_PREC_FP16_H2) continue;   // packed FP16: two threads per site
               dd_sap_params sp = {i_schwarz, id, storage_prec, tps};
               if (sap_run(t, v, z, &sp) != DD_OK) break;   // warm-up
               cudaEventRecord(e0, c->st);
@@ -1393,7 +1396,11 @@ extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4],
               cudaEventElapsedTime(&ms, e0, e1);
               double q = sqrt(h.x / h.y);
               double score = ms / fmax(1e-3, -log(fmax(q, 1e-30)));
-              (void)load;
+              // the measured time already carries the wave quantisation; the model's
+              // estimate of it is reported beside each candidate
+              if (c->trace)
+                fprintf(stderr, "[dd] autotune b %dx%dx%dx%d I_d %d tps %d: %.3f ms, |1 - AM| %.3e, load %.2f\n", b[0],
+                        b[1], b[2], b[3], id, tps, ms, q, load);
               if (q < 1.0 && score < best) {
                 best = score;
                 for (int mu = 0; mu < 4; ++mu) bestb[mu] = b[mu];
