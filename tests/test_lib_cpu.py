@@ -73,3 +73,42 @@ def test_host_deflation_matches_oracle(ddmod):
     cls = c - Hbar @ y
     assert np.allclose(P @ cn, cls, atol=1e-12 * np.linalg.norm(c))
     assert np.allclose(Hn, P.conj().T @ Hbar @ P[:m, :k], atol=1e-12 * np.linalg.norm(Hbar))
+
+
+def _create(ddmod, dims, dom):
+    L = ddmod.lib()
+    h = ctypes.c_void_p()
+    s = L.dd_create(ctypes.byref(h), (ctypes.c_int * 4)(*dims), (ctypes.c_int * 4)(*dom), 1, None)
+    if s == 0:
+        L.dd_destroy(h)
+    return s
+
+
+@pytest.mark.parametrize("dims,dom", [
+    ((16, 8, 8, 8), (8, 4, 4, 3)),     # b_mu not a power of two (and L / b not whole)
+    ((12, 8, 8, 8), (4, 4, 4, 4)),     # 3 domains in x: the two colours would not alternate
+    ((8, 8, 8, 8), (8, 4, 4, 4)),      # one domain in x: a hop would wrap into its own domain
+    ((8, 8, 8, 8), (2, 2, 2, 2)),      # 16 sites per domain: below a warp pair
+    ((32, 32, 32, 32), (8, 8, 4, 4)),  # 1024 sites per domain: above the CTA's threads
+    ((0, 8, 8, 8), (4, 4, 4, 4)),
+], ids=["b3", "odd_count", "one_domain", "tiny_domain", "huge_domain", "zero_extent"])
+def test_create_rejects_disallowed_shapes(ddmod, dims, dom):
+    """Domain constraints of the C ABI (Sec. II-D): b_mu a power of two, L_mu / b_mu even
+    and at least 2 (consistent two-colouring under periodic wrap), 64..512 sites per
+    domain.  Checked before any device call, so this holds without a GPU."""
+    assert _create(ddmod, dims, dom) == ddmod.DD_ERR_DIMS
+
+
+def test_null_arguments_are_invalid_not_fatal(ddmod):
+    L = ddmod.lib()
+    assert L.dd_create(None, (ctypes.c_int * 4)(8, 8, 8, 8), (ctypes.c_int * 4)(4, 4, 4, 4), 1, None) == \
+        ddmod.DD_ERR_INVALID
+    assert L.dd_destroy(None) == ddmod.DD_ERR_INVALID
+    assert L.dd_load_gauge(None, None, 0) == ddmod.DD_ERR_INVALID
+    assert L.dd_solve(None, None, None, 1, 0, None, None) == ddmod.DD_ERR_INVALID
+
+
+def test_host_deflation_rejects_bad_sizes(ddmod):
+    z = np.zeros(64 * 64 * 2)
+    for m, k in ((0, 0), (8, 0), (8, 8), (64, 4)):
+        assert ddmod.lib().dd_deflate_host(m, k, *([z.ctypes.data] * 7)) == ddmod.DD_ERR_INVALID
