@@ -307,6 +307,12 @@ def main():
         ms = e0.elapsed_time(e1) / steps
         return ms, infos, ctx.dd_launch_count() - l0
 
+    # FP32 CUDA-core peak, measured (FFMA microbenchmark, ~2 s of back-to-back launches)
+    clk_p = ClockSampler(local)
+    clk_p.start()
+    peak_burst, peak_sust = dd.dd_fp32_peak(2000)
+    peak_clocks = clk_p.stop()
+
     clk = ClockSampler(local)
     clk.start()
     mixed = dd.DD_PREC_FP16_H2 if args.sap_prec == "half2" else dd.DD_PREC_FP16
@@ -338,7 +344,9 @@ def main():
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    fp32_units = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    # the Schwarz kernel runs inside a seconds-long solve: the sustained FFMA figure
+    fp32_peak = peak_sust
     sap_sha = src_sha(["paper_1412_2629_gb300/csrc/sap.cu", "paper_1412_2629_gb300/csrc/dd_common.cuh"])
     dsl_sha = src_sha(["paper_1412_2629_gb300/csrc/dslash.cu", "paper_1412_2629_gb300/csrc/dd_common.cuh"])
     sap_traffic = read_profile("sap_kernel_32x64.txt", sap_sha)
@@ -367,8 +375,11 @@ def main():
         "roofline": {"kernel": SAP_KERNEL[args.sap_prec], "bound": "alu",
                      "achieved": sap_tflops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": sap_tflops / fp32_peak,
                      "traffic": sap_traffic,
-                     "peak_note": f"FP32 CUDA cores: {props.multi_processor_count} SMs x 128 lanes x 2 flop x "
-                                  f"{sm_max:.0f} MHz (max SM clock)",
+                     "peak_note": "of measured: FFMA microbenchmark (dd_fp32_peak), sustained over ~2 s; "
+                                  f"burst {peak_burst:.1f} TFLOP/s; unit counts {props.multi_processor_count} SMs x "
+                                  f"128 lanes x 2 flop x {sm_max:.0f} MHz = {fp32_units:.1f} TFLOP/s",
+                     "frac_of_unit_count_peak": sap_tflops / fp32_units,
+                     "peak_clocks": peak_clocks,
                      "flops_per_launch": sap_flops_launch, "launch_ms": 1e3 * sap_launch_s},
         "dslash": {"kernel": "apply_A_kernel<float>", "bound": "hbm", "achieved": dsl_gbs, "peak": hbm,
                    "unit": "GB/s", "frac": dsl_gbs / hbm, "traffic": dsl_traffic, "launch_ms": 1e3 * a_launch_s,

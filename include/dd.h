@@ -104,8 +104,11 @@ dd_status dd_create(dd_ctx** out, const int dims[4], const int domain[4], int t_
 dd_status dd_destroy(dd_ctx* ctx);
 const char* dd_last_error(const dd_ctx* ctx);
 
-/* Load the gauge field (canonical FP64 layout, host or device memory per `where`).
- * It is copied; FP64, FP32 and FP16 internal copies are made. */
+/* Load the gauge field U_mu(x) of the hopping term (Sec. II-B, Eq. 2; canonical FP64
+ * layout, host or device memory per `where`).  It is copied; FP64, FP32 and FP16 copies
+ * in the domain-major layout are made (Sec. III-A: each domain's data contiguous), with
+ * the antiperiodic time boundary folded into the links U_t(x) at t = L_t - 1.  The
+ * caller's buffer is not retained.  Returns DD_ERR_OOM if the copies cannot be allocated. */
 dd_status dd_load_gauge(dd_ctx* ctx, const double* U, int where);
 
 /* Build the clover term (Eq. 3) with the diagonal 1/(2 kappa) folded in, in FP64, and
@@ -142,9 +145,9 @@ dd_status dd_apply_D_batch(dd_ctx* ctx, const void* in, void* out, int nrhs, int
 
 /* out = M in like dd_sap_precondition, but without allocating: the paper has no
  * counterpart to this entry point.  It is for callers that cannot call cudaMalloc when
- * they apply the preconditioner: code running under CUDA stream capture (a cudaMalloc
- * there breaks or invalidates the capture), frameworks that own all device memory through
- * their own pool, and loops that cannot afford cudaMalloc's device-wide synchronisation.
+ * they apply the preconditioner: frameworks that own all device memory through their own
+ * pool (a cudaMalloc behind the pool's back can fail or fragment it), and loops that
+ * cannot afford cudaMalloc's device-wide synchronisation.
  * in/out: FP32 device buffers in the internal layout (see dd_pack_spinor); the context's
  * gauge field and clover must already be built (dd_load_gauge / dd_build_clover allocate,
  * this call does not).  The Schwarz working state lives in one fixed 64 MiB array in the
@@ -154,7 +157,9 @@ dd_status dd_apply_D_batch(dd_ctx* ctx, const void* in, void* out, int nrhs, int
  * ~4e5 sites).  All calls share that array, so calls that overlap on the GPU (other
  * streams, other contexts, other threads) race and must be serialised by the caller.
  * The first call on each device looks up the array's address (cudaGetSymbolAddress) with
- * that device current; make it before any stream capture.  Synchronous like the others. */
+ * that device current; make that first call before any stream capture.  The call is
+ * synchronous like the others: it reads the kernel's error word back and waits for the
+ * stream before it returns. */
 dd_status dd_sap_precondition_noalloc(dd_ctx* ctx, const float* in, float* out, const dd_sap_params* p);
 
 /* Solve A x = f (Sec. II-C, Table I) for nrhs right-hand sides stored one after another
@@ -184,19 +189,38 @@ dd_status dd_unpack_spinor(dd_ctx* ctx, const void* internal, int internal_prec,
 /* Number of kernels this context has launched since it was created. */
 long long dd_launch_count(const dd_ctx* ctx);
 
+/* Measured FP32 CUDA-core peak of the current device (the roofline denominator of the
+ * Schwarz kernel, which is bound by FP32 arithmetic): back-to-back launches of a kernel
+ * whose threads run eight independent FFMA chains each (no memory traffic), for at least
+ * duration_ms milliseconds of device time after one warm-up launch.  burst_tflops: the
+ * fastest launch; sustained_tflops: all launches together (clocks settle under the power
+ * limit).  2 flop per FFMA.  Uses its own stream and a 16-byte buffer; changes no device
+ * setting. */
+dd_status dd_fp32_peak(int duration_ms, double* burst_tflops, double* sustained_tflops);
+
 /* Wave-quantisation load of the Schwarz kernel, the GPU analogue of Eq. 6-7: with
  * n = number of domains of one colour and `slots` CTAs resident at once,
  * load = n / (slots * ceil(n / slots)).  Pure host function. */
 double dd_load_model(long long n_domains_per_colour, int slots);
 
-/* Pick a domain shape, I_domain and threads per site for this lattice (the context's
- * own shape is not changed): candidates allowed by the constraints above (extents 2, 4
- * or 8 per direction, I_domain 2..6) are timed on the device with the current gauge
- * field and clover, and scored by time per factor of residual reduction of f - A M f.
- * storage_prec: DD_PREC_FP16, DD_PREC_FP16_H2 or DD_PREC_FP32 (else DD_ERR_INVALID);
- * out->i_schwarz > 0 is kept, else 16.  Writes the best shape to domain_out and its SAP
- * parameters to out.  With DD_TRACE set, one line per candidate gives its time, its
- * residual factor and the load model's estimate (dd_load_model) for that shape. */
+/* Autotuner (Sec. IV-B: the domain size and I_domain are chosen by the overall
+ * time-to-solution; Eq. 6-7 give the load of a domain count).  Picks a domain shape,
+ * I_Schwarz, I_domain and threads per site for this lattice with the context's gauge
+ * field and clover; the context's own shape is not changed.  Every candidate runs a short
+ * FGMRES-DR(16, 4) solve from x = 0 of a fixed pseudo-random source on the device (12
+ * Arnoldi steps in the shape stage, 48 afterwards) and is scored by its device time per
+ * e-fold of true-residual reduction.  Stages: (1) every allowed shape with extents 2, 4 or
+ * 8 at I_Schwarz 4, I_domain 4, two threads per site, keeping the four best; (2) I_domain
+ * 2..6 x threads per site 1, 2 on those shapes; (3) I_Schwarz in {1, 2, 4, 8, 16}, then
+ * I_domain again, at the best shape.  On entry, out->i_schwarz, out->i_domain and
+ * out->threads_per_site > 0 fix that parameter (threads_per_site 2 is needed for
+ * several right-hand sides in lockstep); storage_prec: DD_PREC_FP16, DD_PREC_FP16_H2 or
+ * DD_PREC_FP32 (else DD_ERR_INVALID).  Writes the best shape to domain_out and its
+ * parameters to out.  Temporary device memory (two FP64 fields here, one context per
+ * candidate) is released before returning.  Returns the first candidate error other than
+ * a refused shape or a diverging solve, or DD_ERR_NOT_CONVERGED if no candidate reduced
+ * the residual.  With DD_TRACE set, one line per candidate gives its iterations, time,
+ * residual, score and the load model's estimate (dd_load_model) for that shape. */
 dd_status dd_autotune(dd_ctx* ctx, int storage_prec, int domain_out[4], dd_sap_params* out);
 
 /* Host build of the deflated-restart step that dd_solve runs on the device: given the

@@ -16,6 +16,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <array>
 #include <map>
 #include <string>
@@ -364,12 +365,21 @@ extern "C" dd_status dd_unpack_spinor(dd_ctx* c, const void* internal, int iprec
 // ------------------------------------------------------------------ Schwarz preconditioner
 static void release(dd_ctx* c, void* p);
 
+// The outer solver's captured graphs hold the addresses of the Schwarz state; they are
+// destroyed whenever that state is reallocated, so no replay touches freed memory.
+static void drop_graphs(dd_ctx* c) {
+  for (auto& kv : c->sv.graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  c->sv.graphs.clear();
+}
+
 // Schwarz state (residual, solution, faces) for nrhs right-hand sides, one after another.
 static dd_status ensure_sap(dd_ctx* c, int prec, int nrhs = 1) {
   SapBuffers& b = c->sap[prec];
   if (b.faces && b.cap >= nrhs) return DD_OK;
   if (b.faces) {
     cudaStreamSynchronize(c->st);
+    drop_graphs(c);
     for (void* q : {(void*)b.r_store, (void*)b.r_norm, (void*)b.u_store, (void*)b.u_norm, (void*)b.faces}) release(c, q);
     b = SapBuffers();
   }
@@ -1300,124 +1310,199 @@ extern "C" dd_status dd_deflate_host(int m, int k, const double* Hbar, const dou
 }
 
 // ------------------------------------------------------------------ autotuner
-// Deterministic pseudo-random FP32 field (splitmix64 per unit), for tuning runs only.
-__global__ void fill_random_kernel(float4* v, long long n4, unsigned long long seed) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
-    float f[4];
-    for (int e = 0; e < 4; ++e) {
-      unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(4 * q + e + 1);
-      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-      z ^= z >> 31;
-      f[e] = (float)((z >> 40) * (1.0 / 16777216.0)) - 0.5f;
-    }
-    v[q] = make_float4(f[0], f[1], f[2], f[3]);
+// Deterministic pseudo-random FP64 field (splitmix64 per real), for tuning runs only.
+__global__ void fill_random64_kernel(double* v, long long n, unsigned long long seed) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(q + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[q] = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
   }
 }
 
-__global__ void sub_norm2_kernel(const float4* a, const float4* b, long long n4, double2* out) {
-  __shared__ double sh[256];
-  double s = 0;
-  double t = 0;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
-    float4 x = a[q], y = b[q];
-    float dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z, dw = x.w - y.w;
-    s += dx * dx + dy * dy + dz * dz + dw * dw;
-    t += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
-  }
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) atomicAdd(&out->x, sh[0]);
-  __syncthreads();
-  sh[threadIdx.x] = t;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) atomicAdd(&out->y, sh[0]);
-}
+namespace {
+// One candidate of the search and its measured score.
+struct TuneCand {
+  int b[4];
+  int i_domain, i_schwarz, tps;
+  double score = 1e300;   // seconds per e-fold of residual reduction (lower is better)
+  double res = 1.0, t = 0.0;
+  int iters = 0;
+};
 
+// A context of the candidate's domain shape with the tuned context's gauge field and
+// clover; nullptr (status in *st) when the shape is not allowed or set-up failed.
+dd_ctx* tune_ctx(dd_ctx* c, const int b[4], dd_status* st) {
+  dd_ctx* t = nullptr;
+  *st = dd_create(&t, c->g.L, b, c->anti, c->st);
+  if (*st != DD_OK) return nullptr;
+  *st = dd_load_gauge(t, c->Ucanon, DD_DEVICE);
+  if (*st == DD_OK) *st = dd_build_clover(t, c->kappa, c->csw);
+  if (*st != DD_OK) {
+    if (*st == DD_ERR_SINGULAR_CLOVER) *st = DD_OK;   // same clover as the tuned context
+    else { dd_destroy(t); return nullptr; }
+  }
+  return t;
+}
+}  // namespace
+
+// Time-to-solution search (Sec. IV-B: I_domain and the domain size are chosen by the
+// overall time-to-solution, Eq. 6-7 give the load of a domain count).  Each candidate runs
+// a short solve from x = 0 of a fixed pseudo-random source; its score is the solve's
+// device time divided by the number of e-folds by which it reduced the true residual.
 extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4], dd_sap_params* out) {
   if (!c || !domain_out || !out) return DD_ERR_INVALID;
   if (storage_prec != DD_PREC_FP16 && storage_prec != DD_PREC_FP32 && storage_prec != DD_PREC_FP16_H2)
     return fail(c, DD_ERR_INVALID, "autotune: storage_prec must be DD_PREC_FP16, DD_PREC_FP16_H2 or DD_PREC_FP32");
+  if (out->i_schwarz < 0 || out->i_domain < 0 || out->threads_per_site < 0 || out->threads_per_site > 2 ||
+      (storage_prec == DD_PREC_FP16_H2 && out->threads_per_site == 1))
+    return fail(c, DD_ERR_INVALID, "autotune: bad fixed parameters");
   if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
-  int i_schwarz = out->i_schwarz > 0 ? out->i_schwarz : 16;
-  const int ext[3] = {2, 4, 8};
-  double best = 1e300;
-  int bestb[4] = {c->g.b[0], c->g.b[1], c->g.b[2], c->g.b[3]}, best_id = 5, best_tps = 2;
-  long long n4 = c->g.V * 6;
-  float4 *v = nullptr, *z = nullptr, *w = nullptr;
-  double2* acc = nullptr;
-  TRY(dalloc(c, &v, (size_t)n4 * 16));
-  TRY(dalloc(c, &z, (size_t)n4 * 16));
-  TRY(dalloc(c, &w, (size_t)n4 * 16));
-  TRY(dalloc(c, &acc, sizeof(double2)));
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  const int fix_is = out->i_schwarz, fix_id = out->i_domain;
+  const int fix_tps = storage_prec == DD_PREC_FP16_H2 ? 2 : out->threads_per_site;
+  const long long nreal = c->g.V * 24;
+  double *f = nullptr, *x = nullptr;
+  TRY(dalloc(c, &f, (size_t)nreal * 8));
+  dd_status st = dalloc(c, &x, (size_t)nreal * 8);
+  if (st != DD_OK) { release(c, f); return st; }
+  fill_random64_kernel<<<blas_partials_blocks(), 256, 0, c->st>>>(f, nreal, 12345);
+  st = launched(c);
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  for (int a0 = 0; a0 < 3; ++a0)
-    for (int a1 = 0; a1 < 3; ++a1)
-      for (int a2 = 0; a2 < 3; ++a2)
-        for (int a3 = 0; a3 < 3; ++a3) {
-          int b[4] = {ext[a0], ext[a1], ext[a2], ext[a3]};
-          dd_ctx* t = nullptr;
-          if (dd_create(&t, c->g.L, b, c->anti, c->st) != DD_OK) continue;
-          dd_status s = dd_load_gauge(t, c->Ucanon, DD_DEVICE);
-          if (s == DD_OK) s = dd_build_clover(t, c->kappa, c->csw);
-          if (s == DD_OK) {
-            fill_random_kernel<<<blas_partials_blocks(), 256, 0, c->st>>>(v, n4, 12345);
-            // slots: CTAs resident at once, for the load model
-            double load = dd_load_model(t->g.ND / 2, sms * (sap_smem_bytes(t->g, sap_prec(storage_prec),
-                                                                          sap_mat_fits_smem(t->g, sap_prec(storage_prec))) > 116 * 1024 ? 1 : 2));
-            for (int cand = 0; cand < 10; ++cand) {
-              const int id = 2 + cand / 2, tps = 1 + cand % 2;
-              if (tps == 1 && storage_prec == DD_PREC_FP16_H2) continue;   // packed FP16: two threads per site
-              dd_sap_params sp = {i_schwarz, id, storage_prec, tps};
-              if (sap_run(t, v, z, &sp) != DD_OK) break;   // warm-up
-              cudaEventRecord(e0, c->st);
-              if (sap_run(t, v, z, &sp) != DD_OK) break;
-              cudaEventRecord(e1, c->st);
-              apply_internal(t, z, w, P32);
-              cudaMemsetAsync(acc, 0, sizeof(double2), c->st);
-              sub_norm2_kernel<<<blas_partials_blocks(), 256, 0, c->st>>>(w, v, n4, acc);
-              double2 h;
-              cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, c->st);
-              cudaStreamSynchronize(c->st);
-              float ms = 0;
-              cudaEventElapsedTime(&ms, e0, e1);
-              double q = sqrt(h.x / h.y);
-              double score = ms / fmax(1e-3, -log(fmax(q, 1e-30)));
-              // the measured time already carries the wave quantisation; the model's
-              // estimate of it is reported beside each candidate
-              if (c->trace)
-                fprintf(stderr, "[dd] autotune b %dx%dx%dx%d I_d %d tps %d: %.3f ms, |1 - AM| %.3e, load %.2f\n", b[0],
-                        b[1], b[2], b[3], id, tps, ms, q, load);
-              if (q < 1.0 && score < best) {
-                best = score;
-                for (int mu = 0; mu < 4; ++mu) bestb[mu] = b[mu];
-                best_id = id;
-                best_tps = tps;
-              }
-            }
+  dd_solve_params sp;
+  sp.tol = 1e-7;
+  sp.m = 16;
+  sp.k = 4;
+  sp.max_iter = 48;
+  // score one candidate on context t (its shape), keeping the first hard error in st
+  auto score = [&](dd_ctx* t, TuneCand& cd) {
+    if (st != DD_OK) return;
+    sp.sap.i_schwarz = cd.i_schwarz;
+    sp.sap.i_domain = cd.i_domain;
+    sp.sap.storage_prec = storage_prec;
+    sp.sap.threads_per_site = cd.tps;
+    dd_status s = cuda_check(c, cudaMemsetAsync(x, 0, (size_t)nreal * 8, c->st), "autotune x");
+    dd_solve_info info;
+    memset(&info, 0, sizeof(info));
+    if (s == DD_OK) s = dd_solve(t, f, x, 1, DD_DEVICE, &sp, &info);
+    c->launches += t->launches;
+    t->launches = 0;
+    if (s == DD_OK || s == DD_ERR_NOT_CONVERGED) {
+      cd.res = info.true_rel_residual;
+      cd.t = info.t_total;
+      cd.iters = info.iterations;
+      const double efold = -log(cd.res);
+      cd.score = (isfinite(cd.res) && cd.res < 1.0 && efold > 1e-3) ? cd.t / efold : 1e300;
+    } else if (s == DD_ERR_NONFINITE) {
+      cd.score = 1e300;   // diverged: not a candidate
+    } else {
+      st = s;
+      c->err = "autotune candidate failed: " + t->err;
+    }
+    if (c->trace) {
+      const long long n = t->g.ND / 2;
+      const bool big = sap_smem_bytes(t->g, sap_prec(storage_prec), sap_mat_fits_smem(t->g, sap_prec(storage_prec))) >
+                       116 * 1024;
+      fprintf(stderr,
+              "[dd] autotune b %dx%dx%dx%d I_S %d I_d %d tps %d: %d it, %.3f ms, residual %.3e, %.4f ms/e-fold, "
+              "load %.2f\n",
+              cd.b[0], cd.b[1], cd.b[2], cd.b[3], cd.i_schwarz, cd.i_domain, cd.tps, cd.iters, 1e3 * cd.t, cd.res,
+              1e3 * cd.score, dd_load_model(n, sms * (big ? 1 : 2)));
+    }
+  };
+  TuneCand best;
+  best.score = 1e300;
+  // stage 1: every allowed domain shape (extents 2, 4 or 8) with a short solve at
+  // provisional parameters; the four best shapes go on
+  const int ext[3] = {2, 4, 8};
+  const int is0 = fix_is > 0 ? fix_is : 4, id0 = fix_id > 0 ? fix_id : 4, tps0 = fix_tps > 0 ? fix_tps : 2;
+  std::vector<TuneCand> shapes;
+  sp.max_iter = 12;
+  for (int a0 = 0; a0 < 3 && st == DD_OK; ++a0)
+    for (int a1 = 0; a1 < 3 && st == DD_OK; ++a1)
+      for (int a2 = 0; a2 < 3 && st == DD_OK; ++a2)
+        for (int a3 = 0; a3 < 3 && st == DD_OK; ++a3) {
+          TuneCand cd;
+          const int b[4] = {ext[a0], ext[a1], ext[a2], ext[a3]};
+          memcpy(cd.b, b, sizeof(b));
+          cd.i_schwarz = is0;
+          cd.i_domain = id0;
+          cd.tps = tps0;
+          dd_status cs;
+          dd_ctx* t = tune_ctx(c, b, &cs);
+          if (!t) {
+            if (cs != DD_ERR_DIMS) { st = cs; c->err = "autotune: candidate set-up failed"; }
+            continue;
           }
-          c->launches += t->launches;
+          score(t, cd);
           dd_destroy(t);
+          if (cd.score < 1e300) shapes.push_back(cd);
         }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  for (int mu = 0; mu < 4; ++mu) domain_out[mu] = bestb[mu];
-  out->i_schwarz = i_schwarz;
-  out->i_domain = best_id;
-  out->threads_per_site = best_tps;
+  std::sort(shapes.begin(), shapes.end(), [](const TuneCand& p, const TuneCand& q) { return p.score < q.score; });
+  if (shapes.size() > 4) shapes.resize(4);
+  // stage 2: I_domain x threads per site on the kept shapes, with longer solves
+  sp.max_iter = 48;
+  for (const TuneCand& sh : shapes) {
+    if (st != DD_OK) break;
+    dd_status cs;
+    dd_ctx* t = tune_ctx(c, sh.b, &cs);
+    if (!t) { st = cs == DD_OK ? DD_ERR_CUDA : cs; break; }
+    for (int id = 2; id <= 6 && st == DD_OK; ++id) {
+      if (fix_id > 0 && id != fix_id) continue;
+      for (int tps = 1; tps <= 2 && st == DD_OK; ++tps) {
+        if (fix_tps > 0 && tps != fix_tps) continue;
+        TuneCand cd = sh;
+        cd.i_domain = id;
+        cd.tps = tps;
+        score(t, cd);
+        if (cd.score < best.score) best = cd;
+      }
+    }
+    dd_destroy(t);
+  }
+  // stage 3: I_Schwarz, then I_domain again, at the chosen shape and threads per site
+  if (st == DD_OK && best.score < 1e300 && (fix_is == 0 || fix_id == 0)) {
+    dd_status cs;
+    dd_ctx* t = tune_ctx(c, best.b, &cs);
+    if (!t) {
+      st = cs == DD_OK ? DD_ERR_CUDA : cs;
+    } else {
+      if (fix_is == 0) {
+        const int is_set[5] = {1, 2, 4, 8, 16};
+        const TuneCand base = best;
+        for (int q = 0; q < 5 && st == DD_OK; ++q) {
+          if (is_set[q] == base.i_schwarz) continue;
+          TuneCand cd = base;
+          cd.i_schwarz = is_set[q];
+          score(t, cd);
+          if (cd.score < best.score) best = cd;
+        }
+      }
+      if (fix_id == 0) {
+        const TuneCand base = best;
+        for (int id = 2; id <= 6 && st == DD_OK; ++id) {
+          if (id == base.i_domain) continue;
+          TuneCand cd = base;
+          cd.i_domain = id;
+          score(t, cd);
+          if (cd.score < best.score) best = cd;
+        }
+      }
+      dd_destroy(t);
+    }
+  }
+  cudaStreamSynchronize(c->st);
+  release(c, f);
+  release(c, x);
+  if (st != DD_OK) return st;
+  if (best.score >= 1e300)
+    return fail(c, DD_ERR_NOT_CONVERGED, "autotune: no candidate reduced the residual");
+  for (int mu = 0; mu < 4; ++mu) domain_out[mu] = best.b[mu];
+  out->i_schwarz = best.i_schwarz;
+  out->i_domain = best.i_domain;
+  out->threads_per_site = best.tps;
   out->storage_prec = storage_prec;
   return cuda_check(c, cudaStreamSynchronize(c->st), "autotune");
 }
@@ -1426,8 +1511,9 @@ extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4],
 // Same preconditioner as dd_sap_precondition (internal FP32 layout), but its working
 // state (stored residual, solution, face buffers, error word) lives in a fixed array of
 // the library's global memory instead of context buffers made by cudaMalloc.  The first
-// call on a device looks up that array's device address (cudaGetSymbolAddress); make
-// that first call before any stream capture.
+// call on a device looks up that array's device address (cudaGetSymbolAddress) with the
+// device current.  The call is synchronous: it reads the error word back and waits for
+// the stream.
 extern "C" dd_status dd_sap_precondition_noalloc(dd_ctx* c, const float* in, float* out, const dd_sap_params* p) {
   if (!c || !in || !out) return DD_ERR_INVALID;
   TRY(check_sap_params(c, p));
@@ -1465,6 +1551,7 @@ extern "C" dd_status dd_sap_precondition_noalloc(dd_ctx* c, const float* in, flo
   S.mat_in_smem = sap_mat_fits_smem(g, prec);
   S.threads_per_site = p->threads_per_site ? p->threads_per_site : 2;
   S.half_arith = p->storage_prec == DD_PREC_FP16_H2;
+  S.inject_wait_timeout = c->inject_wait_timeout;
   // the error word must start at zero; residual, solution and faces are written before
   // they are read within one call
   TRY(cuda_check(c, cudaMemsetAsync(S.err, 0, sizeof(int), c->st), "clear error word"));

@@ -22,6 +22,7 @@
 // owns even site i and odd site i and keeps x, rho and r_o in registers, so every MR
 // step runs on chip.  The MR inner products are reduced with warp shuffles and one
 // exchange through shared memory.
+#include <mutex>
 #include <type_traits>
 
 #include "dd_kernels.hpp"
@@ -330,7 +331,7 @@ template <typename MT, typename VT, bool MSMEM>
 __global__ void __launch_bounds__(SAP_MAX_THREADS, 1) sap_kernel(SapArgs a) {
   const Geom& g = a.g;
   extern __shared__ float4 smem[];
-  __shared__ uint64_t mbar;
+  __shared__ uint64_t mbar, mbar_inj;   // staged copies; injected bytes (test hook)
   __shared__ float4 red[SAP_MAX_THREADS / 32];
   const int tid = threadIdx.x;
   const int Hd = g.Hd, Vd = g.Vd;
@@ -364,12 +365,17 @@ __global__ void __launch_bounds__(SAP_MAX_THREADS, 1) sap_kernel(SapArgs a) {
     M.lk = reinterpret_cast<const LkT*>(sbase);
     M.cm = reinterpret_cast<const CmT*>(sbase + lk_bytes);
     sE = reinterpret_cast<float4*>(sbase + lk_bytes + cm_bytes);
-    if (tid == 0) mbar_init(&mbar, 1);
+    if (tid == 0) {
+      mbar_init(&mbar, 1);
+      mbar_init(&mbar_inj, 1);
+    }
     __syncthreads();
     if (tid == 0) {
-      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes) + a.extra_tx);
+      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes));
       bulk_g2s(sbase, glk, (uint32_t)lk_bytes, &mbar);
       bulk_g2s(sbase + lk_bytes, gcm, (uint32_t)cm_bytes, &mbar);
+      // test hook: bytes that nobody sends, on a barrier of their own
+      if (a.extra_tx) mbar_expect_tx(&mbar_inj, a.extra_tx);
     }
   } else {
     M.lk = glk;
@@ -399,8 +405,11 @@ __global__ void __launch_bounds__(SAP_MAX_THREADS, 1) sap_kernel(SapArgs a) {
   }
   if (MSMEM) {
     bool ok = mbar_wait(&mbar, 0, a.wait_ns);
+    if (a.extra_tx) ok = mbar_wait(&mbar_inj, 0, a.wait_ns) && ok;
     if (__syncthreads_or(!ok)) {
-      // the copy did not complete in time: flag it, give it one more bounded wait, leave
+      // a wait ran out: flag it; then wait (bounded) for the staged copies themselves,
+      // which were issued and will land, so none is left writing into this CTA's shared
+      // memory after it exits
       if (tid == 0) atomicExch(a.err, 1);
       mbar_wait(&mbar, 0, a.wait_ns);
       return;
@@ -980,7 +989,7 @@ template <typename MT, typename VT, bool MSMEM, bool H2>
 __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   const Geom& g = a.g;
   extern __shared__ float4 smem[];
-  __shared__ uint64_t mbar;
+  __shared__ uint64_t mbar, mbar_inj;   // staged copies; injected bytes (test hook)
   __shared__ float4 red[2 * SAP_MAX_THREADS / 32];
   __shared__ float nrm[2 * SAP_MAX_THREADS];
   const int tid = threadIdx.x;
@@ -1015,12 +1024,17 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
     M.lk = reinterpret_cast<const LkT*>(sbase);
     M.cm = reinterpret_cast<const CmT*>(sbase + lk_bytes);
     sE = reinterpret_cast<float4*>(sbase + lk_bytes + cm_bytes);
-    if (tid == 0) mbar_init(&mbar, 1);
+    if (tid == 0) {
+      mbar_init(&mbar, 1);
+      mbar_init(&mbar_inj, 1);
+    }
     __syncthreads();
     if (tid == 0) {
-      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes) + a.extra_tx);
+      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes));
       bulk_g2s(sbase, glk, (uint32_t)lk_bytes, &mbar);
       bulk_g2s(sbase + lk_bytes, gcm, (uint32_t)cm_bytes, &mbar);
+      // test hook: bytes that nobody sends, on a barrier of their own
+      if (a.extra_tx) mbar_expect_tx(&mbar_inj, a.extra_tx);
     }
   } else {
     M.lk = glk;
@@ -1059,7 +1073,9 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
     else zero(r);
     if (MSMEM && rhs == 0) {
       bool ok = mbar_wait(&mbar, 0, a.wait_ns);
+      if (a.extra_tx) ok = mbar_wait(&mbar_inj, 0, a.wait_ns) && ok;
       if (__syncthreads_or(!ok)) {
+        // as in sap_kernel: flag, then a bounded wait for the real copies before leaving
         if (tid == 0) atomicExch(a.err, 1);
         mbar_wait(&mbar, 0, a.wait_ns);
         return;
@@ -1406,11 +1422,16 @@ size_t sap_noalloc_scratch_bytes() { return SAP_NOALLOC_SCRATCH_BYTES; }
 
 // Device address of the scratch array on the current device.  In host code the array's
 // name is only a stand-in, so the address is looked up with cudaGetSymbolAddress, once per
-// device, with that device current.  Returns nullptr if the lookup fails.
+// device, with that device current; a mutex makes the first lookups from several threads
+// safe.  The address belongs to the device's context: after cudaDeviceReset the cache is
+// stale, and the library (whose contexts are then invalid too) must not be used on that
+// device again in this process.  Returns nullptr if the lookup fails.
 void* sap_noalloc_scratch() {
+  static std::mutex mu;
   static void* addr[64] = {};
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
   if (!addr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_sap_noalloc_scratch) != cudaSuccess) {

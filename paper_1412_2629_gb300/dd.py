@@ -80,6 +80,7 @@ def lib():
             "dd_load_model": (D, [C.c_longlong, I]),
             "dd_autotune": (I, [P, I, C.POINTER(I), C.POINTER(dd_sap_params)]),
             "dd_deflate_host": (I, [I, I, P, P, P, P, P, P, P]),
+            "dd_fp32_peak": (I, [I, C.POINTER(D), C.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -181,9 +182,11 @@ class Context:
     def dd_launch_count(self):
         return lib().dd_launch_count(self._h)
 
-    def dd_autotune(self, storage_prec=DD_PREC_FP16, i_schwarz=16):
+    def dd_autotune(self, storage_prec=DD_PREC_FP16, i_schwarz=0, i_domain=0, threads_per_site=0):
+        """Returns (domain shape, (i_schwarz, i_domain, storage_prec, threads_per_site));
+        a parameter given > 0 is kept fixed."""
         dom = (C.c_int * 4)()
-        p = dd_sap_params(i_schwarz, 0, storage_prec)
+        p = dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site)
         self._check(lib().dd_autotune(self._h, storage_prec, dom, C.byref(p)))
         return tuple(dom), (p.i_schwarz, p.i_domain, p.storage_prec, p.threads_per_site)
 
@@ -198,6 +201,15 @@ def dd_sap_precondition_lattices(ctxs, ins, outs, i_schwarz, i_domain, storage_p
     s = lib().dd_sap_precondition_lattices(hs, pi, po, n, C.byref(p))
     if s != DD_OK:
         raise DDError(s, lib().dd_last_error(ctxs[0]._h).decode())
+
+
+def dd_fp32_peak(duration_ms=2000):
+    """(burst, sustained) FP32 TFLOP/s of the current device from the FFMA kernel."""
+    b, s = C.c_double(), C.c_double()
+    st = lib().dd_fp32_peak(int(duration_ms), C.byref(b), C.byref(s))
+    if st != DD_OK:
+        raise DDError(st, "dd_fp32_peak failed")
+    return b.value, s.value
 
 
 def dd_load_model(n_domains_per_colour, slots):

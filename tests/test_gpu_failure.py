@@ -1,7 +1,8 @@
 """Failure detection through the C ABI, with no GPU fault: shapes the library refuses,
 calls in the wrong order, an iteration limit, a non-finite source, and a bounded device
 wait that is made to run out (the Schwarz kernel is told to expect 16 bytes that nobody
-sends; it gives up after 50 ms, sets an error word and returns)."""
+sends, on a barrier of their own; it gives up after 50 ms, sets an error word, waits for
+its real staged copies and returns)."""
 import numpy as np
 import pytest
 import torch
@@ -69,6 +70,12 @@ def test_bounded_wait_runs_out_and_context_stays_usable(monkeypatch):
     with pytest.raises(dd.DDError) as e:
         c.dd_sap_precondition(src, torch.empty_like(src), 1, 2, dd.DD_PREC_FP16)
     assert e.value.status == dd.DD_ERR_TIMEOUT
+    # the allocation-free entry point runs the same kernel on its fixed array: same status
+    nb = c.dd_spinor_bytes(dd.DD_PREC_FP32, dd.DD_LAYOUT_INTERNAL)
+    vi = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    c.dd_pack_spinor(src, dd.DD_PREC_FP32, vi, dd.DD_PREC_FP32)
+    s = c.dd_sap_precondition_noalloc(vi, torch.empty_like(vi), 1, 2, dd.DD_PREC_FP16, check=False)
+    assert s == dd.DD_ERR_TIMEOUT
     # a fresh context on the same GPU works, and so does the operator of the first one
     ok = ctx_for(dims, dom, U, 0.13, 1.0)
     out = torch.empty_like(src)

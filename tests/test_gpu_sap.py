@@ -3,10 +3,13 @@ multiplicative SAP with the same domains, colours and MR step count.
 
 Bars (MR step lengths depend on the data, so rounding compounds mildly): FP32 storage
 <= 1e-5, FP16 storage <= 5e-3 relative L2.  FP16 storage with packed FP16 products
-(DD_PREC_FP16_H2) <= 2e-2: every SU(3) and clover-block product is rounded to FP16
-(unit roundoff u = 2^-11), about three roundings per operator application, compounding
-like a random walk over the up to 2 I_S (I_d + 2) ~ 200 applications of these cases:
-sqrt(200) * 3u = 2e-2."""
+(DD_PREC_FP16_H2) is held to the same 5e-3: its products round to FP16 (u = 2^-11) like
+the FP16-stored operands they multiply, and the error measured against the oracle is
+0.9-1.0e-3 on these cases.
+
+The cases span one partial wave of CTAs (8 to 96 domains per colour) up to several waves
+(32x32x16x16 with 8x4x4x4 domains: 256 domains per colour on 152 SMs, one CTA per SM, as
+in the benchmark's launches)."""
 import numpy as np
 import pytest
 import torch
@@ -59,7 +62,7 @@ def test_sap_matches_oracle(case):
         assert rel(got16, u) <= 5e-3
     goth2 = sap_gpu(c, f, i_s, i_d, dd.DD_PREC_FP16_H2, 2)
     print(f"half2 products: rel L2 {rel(goth2, u):.2e} against the oracle")
-    assert rel(goth2, u) <= 2e-2
+    assert rel(goth2, u) <= 5e-3
 
 
 def solver_solve(solver, r, colour, i_d, U, bc):
@@ -78,7 +81,7 @@ def test_sap_full_size_properties():
     """On the 32^3x64 workload, in the launch configuration of the benchmark: with the
     Schwarz parameters the solver uses there (I_Schwarz = 2, I_domain = 4) M reduces the
     residual, |f - A M f| < |f|, and the FP16-storage result stays within 5e-3 of the
-    FP32 one (2e-2 with packed FP16 products).  With the paper's I_Schwarz = 16 the multiplicative iteration is not a
+    FP32 one (also with packed FP16 products).  With the paper's I_Schwarz = 16 the multiplicative iteration is not a
     contraction on this workload (kappa = 0.136 lies above the critical kappa of these
     smooth synthetic fields), which the oracle shows on an 8^4 lattice of the same kind."""
     w = synth.WORKLOADS["32^3x64"]
@@ -101,4 +104,31 @@ def test_sap_full_size_properties():
     assert float(d) <= 5e-3
     d2 = (z[dd.DD_PREC_FP16_H2] - z[dd.DD_PREC_FP32]).norm() / z[dd.DD_PREC_FP32].norm()
     print(f"32^3x64: FP16 storage {float(d):.2e}, half2 products {float(d2):.2e} from FP32")
-    assert float(d2) <= 2e-2
+    assert float(d2) <= 5e-3
+
+
+def test_sap_several_waves_matches_oracle():
+    """32x32x16x16 lattice of the 32^3x64 workload's kind (width 0.5 + 5 APE steps, kappa
+    0.136, c_sw 1.5) with its 8x4x4x4 domains: 512 domains, 256 per colour, so each
+    half-sweep runs 1.7 waves of one CTA per SM on 152 SMs.  I_Schwarz = 2 and I_domain = 4
+    as in the benchmark, so the second sweep reads the stored residual and the faces.  All
+    storage forms and both thread layouts against one oracle application."""
+    dims, dom = (32, 32, 16, 16), (8, 4, 4, 4)
+    kappa, csw, i_s, i_d = 0.1360, 1.5, 2, 4
+    Ud = synth.random_su3_field(dims, 0.5, 61, device="cuda")
+    Ud = synth.ape_smear(Ud, 0.5, 5)
+    U = Ud.cpu().numpy()
+    f = synth.gaussian_source(dims, 62)
+    c = ctx_for(dims, dom, Ud, kappa, csw)
+    del Ud
+    got = {}
+    for prec, tps in ((dd.DD_PREC_FP32, 1), (dd.DD_PREC_FP32, 2), (dd.DD_PREC_FP16, 1), (dd.DD_PREC_FP16, 2),
+                      (dd.DD_PREC_FP16_H2, 2)):
+        got[(prec, tps)] = sap_gpu(c, f, i_s, i_d, prec, tps)
+    F = W.field_strength(U)
+    u = DD.sap(U, F, f, kappa, csw, DD.Domains(dims, dom), i_s, i_d)
+    bars = {dd.DD_PREC_FP32: 1e-5, dd.DD_PREC_FP16: 5e-3, dd.DD_PREC_FP16_H2: 5e-3}
+    for (prec, tps), z in got.items():
+        e = rel(z, u)
+        print(f"storage {prec} tps {tps}: rel L2 {e:.2e}")
+        assert e <= bars[prec]

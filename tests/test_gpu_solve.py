@@ -3,10 +3,12 @@ against the oracle's own SAP-FGMRES-DR solution and a sparse direct solve."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spl
+import torch
 
 import synth
 from oracle import dense as DN
 from oracle import solve as S
+from oracle import wilson as W
 from paper_1412_2629_gb300 import dd
 
 from gpu_helpers import ctx_for, gauge, rel
@@ -81,3 +83,63 @@ def test_graph_replay_matches_direct_launches(monkeypatch):
     c2.dd_solve(f, xd, **kw)
     assert np.array_equal(xd, xs[0])
     assert S.true_residual(U, xd, f, 0.1250, 1.5) <= 1e-10
+
+
+@pytest.fixture(scope="module")
+def bench_lattice():
+    """The 32^3x64 workload on the GPU, and the oracle's field strength of its links."""
+    w = synth.WORKLOADS["32^3x64"]
+    Ud = synth.make_gauge(w, device="cuda")
+    c = ctx_for(w.dims, w.domain, Ud, w.kappa, w.csw)
+    U = Ud.cpu().numpy()
+    del Ud
+    return w, c, U, W.field_strength(U), synth.make_sources(w)[0]
+
+
+@pytest.mark.parametrize("prec", [dd.DD_PREC_FP16, dd.DD_PREC_FP32], ids=["mixed", "fp32"])
+def test_benchmark_solve_true_residual_by_oracle(bench_lattice, prec):
+    """The solve the benchmark times: 32^3x64, width 0.5 + 5 APE steps, kappa 0.136,
+    c_sw 1.5, 8x4x4x4 domains, (I_Schwarz, I_domain, m, k) = (2, 4, 40, 8), two threads per
+    site, device-resident f and x (the benchmark's call), in the mixed form (FP16 storage
+    in the Schwarz kernel) and the plain FP32 form.  The oracle recomputes
+    |f - A x| / |f| in FP64 on the whole lattice from the returned x."""
+    w, c, U, F, f = bench_lattice
+    fd = torch.view_as_real(torch.from_numpy(f)).cuda().contiguous()
+    xd = torch.zeros_like(fd)
+    info = c.dd_solve(fd, xd, where=dd.DD_DEVICE, tol=w.tol, m=w.m, k=w.k, max_iter=2000,
+                      i_schwarz=w.i_schwarz, i_domain=w.i_domain, storage_prec=prec)
+    x = torch.view_as_complex(xd.cpu()).numpy()
+    r = f - W.apply_A(U, x, w.kappa, w.csw, F)
+    res = float(np.linalg.norm(r) / np.linalg.norm(f))
+    print(f"32^3x64 kappa {w.kappa}: {info.iterations} it, library {info.true_rel_residual:.3e}, oracle {res:.3e}")
+    assert info.true_rel_residual <= 1e-10
+    assert res <= 1e-10
+
+
+def test_solve_after_schwarz_state_grows_matches_fresh_context():
+    """Captured Arnoldi-step graphs hold the Schwarz state's addresses.  A batched call with
+    more right-hand sides reallocates that state; the graphs must be rebuilt, so a solve
+    after it equals, bit for bit, the same solve on a fresh context."""
+    dims, dom = (16, 8, 8, 8), (8, 4, 4, 4)
+    U = gauge(dims, 0.5, 31, ape=2)
+    f = synth.gaussian_source(dims, 32)
+    kw = dict(tol=1e-10, m=8, k=2, i_schwarz=2, i_domain=3, storage_prec=dd.DD_PREC_FP16)
+    c = ctx_for(dims, dom, U, 0.1250, 1.5)
+    x1 = np.zeros_like(f)
+    info = c.dd_solve(f, x1, **kw)
+    assert info.restarts >= 1          # some Arnoldi steps were replayed from graphs
+    nb = c.dd_spinor_bytes(dd.DD_PREC_FP32, dd.DD_LAYOUT_INTERNAL)
+    fs = [synth.gaussian_source(dims, 40 + r) for r in range(3)]
+    src = torch.empty(3 * nb, dtype=torch.uint8, device="cuda")
+    for r, fr in enumerate(fs):
+        c.dd_pack_spinor(torch.view_as_real(torch.from_numpy(fr)).cuda().contiguous(), dd.DD_PREC_FP64,
+                         src[r * nb:(r + 1) * nb], dd.DD_PREC_FP32)
+    out = torch.empty_like(src)
+    c.dd_sap_precondition_batch(src, out, 3, 2, 3, dd.DD_PREC_FP16)
+    x2 = np.zeros_like(f)
+    c.dd_solve(f, x2, **kw)
+    fresh = ctx_for(dims, dom, U, 0.1250, 1.5)
+    x3 = np.zeros_like(f)
+    fresh.dd_solve(f, x3, **kw)
+    assert np.array_equal(x2, x3)
+    assert np.array_equal(x1, x3)

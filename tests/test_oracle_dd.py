@@ -100,12 +100,22 @@ def test_mr_one_step_and_monotone(small):
         prev = norms
 
 
-def test_mr_scalar_exact():
-    """MR on a 1x1 system a x = b gives x = b / a after one step."""
-    a, b = 2.0 - 0.7j, 0.3 + 1.1j
-    p = a * b
-    alpha = np.conj(p) * b / (np.conj(p) * p)
-    assert abs(alpha * b - b / a) < 1e-15
+def test_mr_exact_on_a_scalar_operator():
+    """With every link zero and c_sw = 0 the Schur complement of Eq. 5 is the scalar
+    1/(2 kappa) on even sites, so BlockSolver.mr must return x = 2 kappa f after one step
+    with a zero residual, and a second step (<p, p> = 0) must leave x unchanged."""
+    kappa = 0.13
+    U = np.zeros(DIMS[::-1] + (4, 3, 3), dtype=np.complex128)
+    dom = DD.Domains(DIMS, B2)
+    bs = DD.BlockSolver(U, None, kappa, 0.0, dom)
+    f = synth.gaussian_source(DIMS, 33)
+    for colour in (0, 1):
+        cm = (dom.colour == colour)[..., None, None].astype(float)
+        fe = f * bs.even * cm
+        for n in (1, 2):
+            x, rho = bs.mr(fe, cm, n)
+            assert np.abs(x - 2.0 * kappa * fe).max() <= 1e-15 * np.abs(fe).max()
+            assert np.abs(rho).max() <= 1e-15 * np.abs(fe).max()
 
 
 def test_sap_equals_dense_block_gauss_seidel(small):

@@ -1,8 +1,8 @@
 """The allocation-free Schwarz entry point, dd_sap_precondition_noalloc.
 
-Some callers cannot call cudaMalloc when they apply the preconditioner: code running
-under CUDA stream capture, frameworks that hand out all device memory from their own
-pool, and loops that cannot afford cudaMalloc's device-wide synchronisation.  For them
+Some callers cannot call cudaMalloc when they apply the preconditioner: frameworks that
+hand out all device memory from their own pool, and loops that cannot afford cudaMalloc's
+device-wide synchronisation.  For them
 the library keeps the Schwarz working state in one fixed array of its own device memory.
 These tests call that entry point through the C ABI twice in a row and check it against
 the allocating entry point, dd_sap_precondition, with the tolerances of the Schwarz
