@@ -222,7 +222,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-mixed", action="store_true", help="time the mixed solve only (profiling runs)")
-    ap.add_argument("--case", default="solve", choices=["solve", "sap", "dslash", "sap_lattices", "workload_solve"],
+    ap.add_argument("--case", default="solve",
+                    choices=["solve", "sap", "dslash", "sap_lattices", "workload_solve", "bicgstab"],
                     help="sap / dslash: time one kernel alone on --lattice (kernel studies, ncu captures)")
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--domain", default="", help="kernel studies: domain shape (default: the workload's)")
@@ -232,6 +233,8 @@ def main():
     ap.add_argument("--sap-prec", default="fp16", choices=["fp16", "half2"],
                     help="mixed form: FP16 storage with FP32 arithmetic, or with packed FP16 products")
     ap.add_argument("--m", type=int, default=0, help="workload_solve: basis size (0: the workload's)")
+    ap.add_argument("--kappa", type=float, default=0.0, help="bicgstab: kappa (0: the workload's)")
+    ap.add_argument("--max-iter", type=int, default=4000, help="bicgstab: BiCGstab iterations allowed")
     args = ap.parse_args()
     if not args.only_mixed:
         args.warmup = max(args.warmup, 3)   # profiling runs (--only-mixed) may skip the warm-up
@@ -258,6 +261,8 @@ def main():
         return lattices_case(args)
     if args.case == "workload_solve":
         return workload_case(args)
+    if args.case == "bicgstab":
+        return bicgstab_case(args)
     if args.case != "solve":
         return kernel_case(args, local)
 
@@ -585,6 +590,45 @@ def workload_case(args):
                      "split_s": {"A": info.t_A, "M": info.t_M, "GS": info.t_GS, "other": info.t_other}}
     os.environ.pop("DD_SEQUENTIAL_RHS", None)
     out["device_gb_in_use"] = (lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info())
+    print(json.dumps(out))
+
+
+def bicgstab_case(args):
+    """The paper's comparison (Sec. IV-C, Table III non-DD rows) on one GPU: the standard
+    solvers -- BiCGstab in FP64, and FP64 Richardson around FP32 BiCGstab -- against the
+    domain-decomposed solver (mixed form, the benchmark's parameters) on the same lattice,
+    source and kappa; device-resident f and x, time-to-solution with CUDA events."""
+    import torch
+
+    import synth
+    from paper_1412_2629_gb300 import dd
+    base = synth.WORKLOADS[args.workload if args.workload in synth.WORKLOADS else WORKLOAD]
+    kappa = args.kappa or base.kappa
+    st = torch.cuda.current_stream()
+    U, f = make_inputs(base, "cuda")
+    ctx = dd.Context(base.dims, base.domain, True, st.cuda_stream)
+    ctx.dd_load_gauge(torch.view_as_real(U).contiguous(), dd.DD_DEVICE)
+    ctx.dd_build_clover(kappa, base.csw)
+    del U
+    fd = torch.view_as_real(torch.from_numpy(f)).cuda().contiguous()
+    xd = torch.zeros_like(fd)
+    out = {"case": "bicgstab", "workload": base.name, "kappa": kappa, "csw": base.csw, "max_iter": args.max_iter}
+    runs = [("dd_mixed", lambda: ctx.dd_solve(fd, xd, where=dd.DD_DEVICE, tol=base.tol, m=base.m, k=base.k,
+                                              max_iter=5000, i_schwarz=base.i_schwarz, i_domain=base.i_domain,
+                                              check=False)),
+            ("bicgstab_fp64", lambda: ctx.dd_solve_bicgstab(fd, xd, where=dd.DD_DEVICE, tol=base.tol,
+                                                            max_iter=args.max_iter, precision=dd.DD_PREC_FP64,
+                                                            check=False)),
+            ("richardson_bicgstab_fp32", lambda: ctx.dd_solve_bicgstab(fd, xd, where=dd.DD_DEVICE, tol=base.tol,
+                                                                       max_iter=args.max_iter,
+                                                                       precision=dd.DD_PREC_FP32, inner_tol=1e-5,
+                                                                       check=False))]
+    for name, fn in runs:
+        xd.zero_()
+        torch.cuda.synchronize()
+        info = fn()
+        out[name] = {"status": info.status, "iterations": info.iterations, "corrections": info.restarts + 1,
+                     "true_rel_residual": info.true_rel_residual, "solve_s": info.t_total, "t_A_s": info.t_A}
     print(json.dumps(out))
 
 

@@ -177,6 +177,31 @@ dd_status dd_sap_precondition_noalloc(dd_ctx* ctx, const float* in, float* out, 
 dd_status dd_solve(dd_ctx* ctx, const double* f, double* x, int nrhs, int where, const dd_solve_params* p,
                    dd_solve_info* info);
 
+/* Standard (not domain-decomposed) comparison solver, the kind the paper measures its
+ * solver against (Sec. IV-C, Table III: BiCGstab in double precision; mixed-precision
+ * Richardson iteration around BiCGstab).  Solves A x = f like dd_solve (canonical FP64
+ * layout, host or device memory per `where`; x holds the initial guess on entry):
+ *   precision DD_PREC_FP64: BiCGstab in FP64 on the FP64 operator; its recursive residual
+ *     drifts from the true one, so the true residual is recomputed (FP64) whenever the
+ *     recursion reports convergence, and BiCGstab resumes from it if needed;
+ *   precision DD_PREC_FP32: Richardson iteration (defect correction) in FP64: r = f - A x
+ *     in FP64, a correction e from BiCGstab in FP32 on the FP32 operator for A e = r / |r|
+ *     to relative residual inner_tol, x += |r| e in FP64, until |f - A x| / |f| <= tol.
+ * max_iter bounds the BiCGstab iterations in total (two operator applications each).
+ * info: iterations = BiCGstab iterations, restarts = Richardson corrections after the
+ * first, reliable_updates = FP64 residuals, t_A = operator time, t_M = t_GS = 0.
+ * Temporary device memory (3 FP64 fields, 7 fields of the iteration's precision) is
+ * allocated per call and released before returning.  Returns DD_ERR_NOT_CONVERGED with
+ * info filled when max_iter is reached. */
+typedef struct {
+  double tol;        /* target |f - A x| / |f| (FP64-recomputed) */
+  int max_iter;      /* BiCGstab iterations in total */
+  int precision;     /* DD_PREC_FP64 or DD_PREC_FP32 (mixed Richardson) */
+  double inner_tol;  /* DD_PREC_FP32: residual reduction of each inner solve, 0 < inner_tol < 1 */
+} dd_bicgstab_params;
+dd_status dd_solve_bicgstab(dd_ctx* ctx, const double* f, double* x, int where, const dd_bicgstab_params* p,
+                            dd_solve_info* info);
+
 /* Bytes of one spinor field for a precision and layout (FP16 internal: values and norms). */
 size_t dd_spinor_bytes(const dd_ctx* ctx, int prec, int layout);
 
@@ -223,11 +248,15 @@ double dd_load_model(long long n_domains_per_colour, int slots);
  * residual, score and the load model's estimate (dd_load_model) for that shape. */
 dd_status dd_autotune(dd_ctx* ctx, int storage_prec, int domain_out[4], dd_sap_params* out);
 
-/* Host build of the deflated-restart step that dd_solve runs on the device: given the
+/* The small dense step of a deflated restart (Sec. II-C, Table I; GMRES-DR with flexible
+ * preconditioning), run on the host by the same code that dd_solve runs as one warp on
+ * the device (a team of one thread here), so it can be checked without a GPU.  Given the
  * (m+1) x m Hessenberg matrix Hbar (column-major, leading dimension m+1, complex as
  * re, im pairs), the cycle's right-hand side c (m+1) and least-squares solution y (m),
  * return the orthonormal (m+1) x (k+1) basis P, Hn = P^H Hbar P_k ((k+1) x k, ld m+1),
- * cn = P^H (c - Hbar y) and the harmonic Ritz values theta (m, sorted by modulus). */
+ * cn = P^H (c - Hbar y) and the harmonic Ritz values theta (m, sorted by modulus).
+ * All arrays are host memory owned by the caller; 1 <= k < m < 64 (else DD_ERR_INVALID);
+ * DD_ERR_NONFINITE when a step fails (the solver then restarts without deflation). */
 dd_status dd_deflate_host(int m, int k, const double* Hbar, const double* c, const double* y, double* P, double* Hn,
                           double* cn, double* theta);
 

@@ -3,11 +3,11 @@
 //
 // Outer solver (Table I): flexible GMRES with deflated restarts.  Krylov vectors V, Z are
 // FP32 fields; Gram-Schmidt coefficients, the Hessenberg matrix, its least-squares
-// problem are FP64 on the device (the m x m harmonic-Ritz eigenproblem of a deflated
-// restart runs on the host, the basis recombination on the device); the solution is accumulated
-// in FP64 and at every restart the residual is recomputed with the FP64 operator
-// (reliable update), which is what makes the 1e-10 target reachable with FP32 Krylov
-// vectors.  A deflated restart keeps the k harmonic Ritz vectors of smallest modulus;
+// problem and the m x m harmonic-Ritz eigenproblem of a deflated restart are FP64 on the
+// device (the last one in a one-warp kernel beside the reliable update), as is the basis
+// recombination; the solution is accumulated in FP64 and at every restart the residual is
+// recomputed with the FP64 operator (reliable update), which is what makes the 1e-10
+// target reachable with FP32 Krylov vectors.  A deflated restart keeps the k harmonic Ritz vectors of smallest modulus;
 // its right-hand side is the projection of the recomputed FP64 residual onto the new
 // basis, and the restart falls back to a plain one when that projection misses more
 // than `defl_tol` of the residual.
@@ -70,10 +70,10 @@ struct SolverBuffers {
   LsqState* lsq = nullptr;
   int* flag = nullptr;                 // Gram-Schmidt: 1 when a second projection is needed
   double* nu2 = nullptr;               // squared norm of the projected vector
-  // host side of the deflated restart (pinned)
-  zd *h_H = nullptr, *h_c0 = nullptr, *h_y = nullptr, *h_P = nullptr, *h_Hn = nullptr, *h_cn = nullptr;
-  zd* h_theta = nullptr;
-  DeflateWork* h_dw = nullptr;
+  // deflated restart on the device: workspace and flags ([0] deflation status, [1] the
+  // recombination gate: deflation succeeded and the residual is above target)
+  DeflateWork* dW = nullptr;
+  int* dflags = nullptr;
 };
 
 struct dd_ctx {
@@ -591,10 +591,42 @@ __global__ void plain_restart_kernel(zd* H, zd* R, int ldh, int m, const double2
   lsq->nrot = 0;
 }
 
-// cp = rho * cp (the projection was taken against r / rho)
-__global__ void scale_coeffs_kernel(zd* cp, int n, const double2* nrm2) {
-  double rho = sqrt(nrm2->x);
-  for (int i = 0; i < n; ++i) cp[i] = rho * cp[i];
+// The deflated restart's small dense step (harmonic Ritz pairs, P, Hn, cn) by one warp.
+__global__ void deflate_kernel(const zd* H, int ldh, int mm, int k, const zd* c0, const zd* y, zd* P, zd* Hn, zd* cn,
+                               zd* theta, DeflateWork* W, int* flags) {
+  const Team T{(int)threadIdx.x, (int)blockDim.x};
+  const int rc = deflate(T, H, ldh, mm, k, c0, y, P, Hn, cn, theta, *W);
+  if (threadIdx.x == 0) flags[0] = rc;
+}
+
+// flags[1] = 1 when the basis is to be recombined: a deflation was computed and succeeded,
+// and the recomputed residual is still above target (|r|^2 > tol2).
+__global__ void restart_gate_kernel(int* flags, int want, const double2* nrm2, double tol2) {
+  flags[1] = (want && flags[0] == 0 && nrm2->x > tol2) ? 1 : 0;
+}
+
+// After the projection cp = V_{k+1}^H (r / rho): cp <- rho cp, and whether the deflated
+// restart keeps enough of r: |r - V_{k+1} cp| <= defl_tol |r|.  status[8..11] = |r|^2,
+// decision, the part of r that the projection misses, deflation status.
+__global__ void restart_decide_kernel(const int* flags, int want, int k, zd* cp, const double2* nrm2, double defl_tol,
+                                      double* status) {
+  const double rho2 = nrm2->x;
+  int dec = 0;
+  double miss = 1.0;
+  if (want && flags[1]) {
+    const double rho = sqrt(rho2);
+    double pc = 0;
+    for (int i = 0; i <= k; ++i) {
+      cp[i] = rho * cp[i];
+      pc += abs2(cp[i]);
+    }
+    miss = sqrt(fmax(0.0, 1.0 - pc / rho2));
+    dec = miss <= defl_tol ? 1 : 0;
+  }
+  status[8] = rho2;
+  status[9] = dec;
+  status[10] = miss;
+  status[11] = want ? (double)flags[0] : -1.0;
 }
 
 // ------------------------------------------------------------------ solver
@@ -615,12 +647,9 @@ static void free_solver_buffers(dd_ctx* c, SolverBuffers& s) {
                   (void*)s.f64, (void*)s.r64, (void*)s.canon64, (void*)s.H, (void*)s.R, (void*)s.P, (void*)s.Hn,
                   (void*)s.g, (void*)s.c0, (void*)s.y, (void*)s.hA, (void*)s.hB, (void*)s.cn, (void*)s.theta,
                   (void*)s.cp, (void*)s.partial, (void*)s.partial2, (void*)s.nrm2, (void*)s.status, (void*)s.lsq,
-                  (void*)s.flag, (void*)s.nu2})
+                  (void*)s.flag, (void*)s.nu2, (void*)s.dW, (void*)s.dflags})
     release(c, p);
-  for (void* p : {(void*)s.h_status, (void*)s.h_H, (void*)s.h_c0, (void*)s.h_y, (void*)s.h_P, (void*)s.h_Hn,
-                  (void*)s.h_cn, (void*)s.h_theta})
-    if (p) cudaFreeHost(p);
-  delete s.h_dw;
+  if (s.h_status) cudaFreeHost(s.h_status);
   for (auto& kv : s.graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   if (s.stream) cudaStreamDestroy(s.stream);
@@ -664,17 +693,13 @@ static dd_status alloc_solver_buffers(dd_ctx* c, SolverBuffers& s, int m, bool s
   TRY(dalloc(c, &s.partial, (size_t)blas_partials_blocks() * (m + 2) * sizeof(double2)));
   TRY(dalloc(c, &s.partial2, (size_t)blas_partials_blocks() * sizeof(double2)));
   TRY(dalloc(c, &s.nrm2, 4 * sizeof(double2)));
-  TRY(dalloc(c, &s.status, 8 * sizeof(double)));
+  TRY(dalloc(c, &s.status, 16 * sizeof(double)));
   TRY(dalloc(c, &s.lsq, sizeof(LsqState)));
   TRY(dalloc(c, &s.flag, 16));
   TRY(dalloc(c, &s.nu2, 16));
+  TRY(dalloc(c, &s.dW, sizeof(DeflateWork)));
+  TRY(dalloc(c, &s.dflags, 16 * sizeof(int)));
   if (cudaMallocHost(&s.h_status, 8 * sizeof(double)) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned status");
-  size_t hb = (size_t)ld * (m + 1) * sizeof(zd);
-  for (zd** p : {&s.h_H, &s.h_P, &s.h_Hn})
-    if (cudaMallocHost(p, hb) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned deflation buffers");
-  for (zd** p : {&s.h_c0, &s.h_y, &s.h_cn, &s.h_theta})
-    if (cudaMallocHost(p, (m + 2) * sizeof(zd)) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned deflation buffers");
-  s.h_dw = new DeflateWork();
   if (streams && (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
                   cudaStreamCreateWithFlags(&s.side, cudaStreamNonBlocking) != cudaSuccess ||
                   cudaEventCreateWithFlags(&s.ev_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -749,6 +774,72 @@ static dd_status true_residual(dd_ctx* c, double* rho2, SolverBuffers* sp = null
   TRY(cuda_check(c, cudaMemcpyAsync(&h, s.nrm2, sizeof(double2), cudaMemcpyDeviceToHost, c->st), "norm"));
   TRY(cuda_check(c, cudaStreamSynchronize(c->st), "norm"));
   *rho2 = h.x;
+  return DD_OK;
+}
+
+// End of a cycle after mm Arnoldi steps, on the device: y from the least-squares problem;
+// the deflated restart's small dense step (one warp, on the second stream beside the
+// reliable update when `side` is set); x64 += Z y; r64 = f - A64 x64 and |r64|^2; then,
+// when the deflation succeeded and |r64| is still above target, V <- V P_{k+1} and
+// Z <- Z P_k in place and the projection of r64 onto the new V_{k+1}.  The one host read
+// returns |r64|^2 and whether the deflated restart keeps enough of r64.
+struct CycleEnd {
+  double rho2 = 0, miss = 1;
+  bool deflate = false;
+  int defl_rc = -1;
+};
+
+static dd_status end_cycle(dd_ctx* c, SolverBuffers& s, int mm, const dd_solve_params* p, double nf, bool side,
+                           CycleEnd* out) {
+  const long long n4 = c->g.V * 6;
+  const int m = p->m, k = p->k, ldh = m + 1;
+  const double defl_tol = 1e-2;
+  const int want = k > 0 && mm > k;
+  lsq_solve_kernel<<<1, 1, 0, c->st>>>(s.R, ldh, mm, s.g, s.y);
+  int nk = 1;
+  cudaStream_t ds = c->st;
+  if (want) {
+    if (side && s.side) {
+      cudaEventRecord(s.ev_fork, c->st);
+      cudaStreamWaitEvent(s.side, s.ev_fork, 0);
+      ds = s.side;
+    }
+    deflate_kernel<<<1, 32, 0, ds>>>(s.H, ldh, mm, k, s.c0, s.y, s.P, s.Hn, s.cn, s.theta, s.dW, s.dflags);
+    nk++;
+    if (ds != c->st) cudaEventRecord(s.ev_join, ds);
+  }
+  launch_x_update(s.x64, s.Z, mm, n4, (const double2*)s.y, c->st);
+  nk++;
+  TRY(launched(c, nk));
+  TRY(apply_internal(c, s.x64, s.r64, P64, s.f64));
+  launch_norm2_64(s.r64, c->g.V * 12, s.partial, c->st);
+  launch_reduce_partials(s.partial, 1, s.nrm2, 0, c->st);
+  nk = 2;
+  if (want && ds != c->st) cudaStreamWaitEvent(c->st, s.ev_join, 0);
+  const double tol2 = (p->tol * nf) * (p->tol * nf);
+  restart_gate_kernel<<<1, 1, 0, c->st>>>(s.dflags, want, s.nrm2, tol2);
+  nk++;
+  if (want) {
+    // V <- V P_{k+1}, Z <- Z P_k in place: every output element depends only on the inputs
+    // at the same position, which its thread reads before writing
+    const int* gate = s.dflags + 1;
+    nk += launch_recombine(s.V, s.V, mm + 1, k + 1, n4, (const double2*)s.P, ldh, c->st, gate);
+    nk += launch_recombine(s.Z, s.Z, mm, k, n4, (const double2*)s.P, ldh, c->st, gate);
+    launch_r64_to_v32(s.w, s.r64, n4, s.nrm2, c->st, gate);
+    nk += 1 + launch_gs_dot(s.V, k + 1, n4, s.w, s.partial, gate, 1, c->st);
+    launch_gs_reduce(s.partial, k + 1, (double2*)s.cp, gate, 1, c->st);
+    nk++;
+  }
+  restart_decide_kernel<<<1, 1, 0, c->st>>>(s.dflags, want, k, s.cp, s.nrm2, defl_tol, s.status);
+  nk++;
+  TRY(launched(c, nk));
+  TRY(cuda_check(c, cudaMemcpyAsync(s.h_status, s.status + 8, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st),
+                 "restart status"));
+  TRY(cuda_check(c, cudaStreamSynchronize(c->st), "restart"));
+  out->rho2 = s.h_status[0];
+  out->deflate = s.h_status[1] != 0.0;
+  out->miss = s.h_status[2];
+  out->defl_rc = (int)s.h_status[3];
   return DD_OK;
 }
 
@@ -841,69 +932,36 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
       if (est <= 0.5 * tol * nf || est <= 2e-6 * rho_cycle || iters >= p->max_iter) { mm = j + 1; break; }
     }
     if (rc != DD_OK) break;
-    lsq_solve_kernel<<<1, 1, 0, c->st>>>(s.R, ldh, mm, s.g, s.y);
-    launch_x_update(s.x64, Zv(0), mm, n4, (const double2*)s.y, c->st);
-    TRY(launched(c, 2));
-    TRY(true_residual(c, &rho2));
-    reliable++;
-    rel = sqrt(rho2) / nf;
-    if (!isfinite(rel)) { rc = fail(c, DD_ERR_NONFINITE, "non-finite residual"); break; }
-    if (rel <= tol) break;
-    if (iters >= p->max_iter) { rc = fail(c, DD_ERR_NOT_CONVERGED, "iteration limit reached"); break; }
-    restarts++;
     if (c->trace && getenv("DD_TRACE")[0] == '2') {
       // orthogonality of the finished basis: max |V^H V - I|
       double dev = 0;
       std::vector<zd> row(mm + 1);
       for (int i = 0; i <= mm; ++i) {
         launch_multi_dot(Vv(0), mm + 1, n4, Vv(i), s.partial, c->st);
-        launch_reduce_partials(s.partial, mm + 1, (double2*)s.cp, 0, c->st);
-        cudaMemcpyAsync(row.data(), s.cp, (mm + 1) * sizeof(zd), cudaMemcpyDeviceToHost, c->st);
+        launch_reduce_partials(s.partial, mm + 1, (double2*)s.hB, 0, c->st);
+        cudaMemcpyAsync(row.data(), s.hB, (mm + 1) * sizeof(zd), cudaMemcpyDeviceToHost, c->st);
         cudaStreamSynchronize(c->st);
         for (int l = 0; l <= mm; ++l) dev = fmax(dev, zabs(row[l] - Z(l == i ? 1.0 : 0.0)));
       }
       fprintf(stderr, "[dd] basis orthogonality max|V^H V - I| = %.3e over %d vectors\n", dev, mm + 1);
     }
-    bool done_defl = false;
-    if (k > 0 && mm > k) {
-      // the (m+1) x m eigen-problem of the harmonic Ritz values is tiny: solve it on the
-      // host (same code as the device build) and keep the basis recombination on the GPU
-      size_t hb = (size_t)ldh * (m + 1) * sizeof(zd);
-      TRY(cuda_check(c, cudaMemcpyAsync(s.h_H, s.H, hb, cudaMemcpyDeviceToHost, c->st), "H"));
-      TRY(cuda_check(c, cudaMemcpyAsync(s.h_c0, s.c0, (m + 1) * sizeof(zd), cudaMemcpyDeviceToHost, c->st), "c"));
-      TRY(cuda_check(c, cudaMemcpyAsync(s.h_y, s.y, m * sizeof(zd), cudaMemcpyDeviceToHost, c->st), "y"));
-      TRY(cuda_check(c, cudaStreamSynchronize(c->st), "deflation inputs"));
-      int drc = deflate(s.h_H, ldh, mm, k, s.h_c0, s.h_y, s.h_P, s.h_Hn, s.h_cn, s.h_theta, *s.h_dw);
-      if (drc == 0) {
-        TRY(cuda_check(c, cudaMemcpyAsync(s.P, s.h_P, hb, cudaMemcpyHostToDevice, c->st), "P"));
-        TRY(cuda_check(c, cudaMemcpyAsync(s.Hn, s.h_Hn, hb, cudaMemcpyHostToDevice, c->st), "Hn"));
-        // V <- V P_{k+1}, Z <- Z P_k in place: every output element depends only on the
-        // inputs at the same position, which its thread reads before writing
-        int nk = launch_recombine(s.V, s.V, mm + 1, k + 1, n4, (const double2*)s.P, ldh, c->st);
-        nk += launch_recombine(s.Z, s.Z, mm, k, n4, (const double2*)s.P, ldh, c->st);
-        // project the FP64 residual onto the new basis
-        launch_r64_to_v32(s.w, s.r64, n4, s.nrm2, c->st);
-        nk += launch_multi_dot(Vv(0), k + 1, n4, s.w, s.partial, c->st);
-        launch_reduce_partials(s.partial, k + 1, (double2*)s.cp, 0, c->st);
-        scale_coeffs_kernel<<<1, 1, 0, c->st>>>(s.cp, k + 1, s.nrm2);
-        TRY(launched(c, nk + 3));
-        std::vector<zd> cp(k + 1);
-        TRY(cuda_check(c, cudaMemcpyAsync(cp.data(), s.cp, (k + 1) * sizeof(zd), cudaMemcpyDeviceToHost, c->st), "cp"));
-        TRY(cuda_check(c, cudaStreamSynchronize(c->st), "cp"));
-        double pc = 0;
-        for (auto& z : cp) pc += abs2(z);
-        double miss = sqrt(fmax(0.0, 1.0 - pc / rho2));
-        if (c->trace) fprintf(stderr, "[dd] restart: true residual %.3e, deflation misses %.3e\n", rel, miss);
-        if (miss <= defl_tol) {
-          restart_lsq_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, k, s.Hn, s.cp, s.g, s.c0, s.lsq, s.status);
-          TRY(launched(c));
-          j0 = k;
-          done_defl = true;
-          deflated++;
-        }
-      }
-    }
-    if (!done_defl) {
+    CycleEnd ce;
+    TRY(end_cycle(c, s, mm, p, nf, true, &ce));
+    rho2 = ce.rho2;
+    reliable++;
+    rel = sqrt(rho2) / nf;
+    if (!isfinite(rel)) { rc = fail(c, DD_ERR_NONFINITE, "non-finite residual"); break; }
+    if (rel <= tol) break;
+    if (iters >= p->max_iter) { rc = fail(c, DD_ERR_NOT_CONVERGED, "iteration limit reached"); break; }
+    restarts++;
+    if (c->trace)
+      fprintf(stderr, "[dd] restart: true residual %.3e, deflation status %d, misses %.3e\n", rel, ce.defl_rc, ce.miss);
+    if (ce.deflate) {
+      restart_lsq_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, k, s.Hn, s.cp, s.g, s.c0, s.lsq, s.status);
+      TRY(launched(c));
+      j0 = k;
+      deflated++;
+    } else {
       launch_r64_to_v32(Vv(0), s.r64, n4, s.nrm2, c->st);
       plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq);
       TRY(launched(c, 2));
@@ -1020,11 +1078,9 @@ static dd_status lock_gs(dd_ctx* c, SolverBuffers& s, int j, int m) {
 static dd_status lock_end_cycle(dd_ctx* c, SolverBuffers& s, LockRhs& R, int mm, const dd_solve_params* p) {
   const long long n4 = c->g.V * 6;
   const int m = p->m, k = p->k, ldh = m + 1;
-  const double defl_tol = 1e-2;
-  lsq_solve_kernel<<<1, 1, 0, c->st>>>(s.R, ldh, mm, s.g, s.y);
-  launch_x_update(s.x64, s.Z, mm, n4, (const double2*)s.y, c->st);
-  TRY(launched(c, 2));
-  TRY(true_residual(c, &R.rho2, &s));
+  CycleEnd ce;
+  TRY(end_cycle(c, s, mm, p, R.nf, false, &ce));
+  R.rho2 = ce.rho2;
   R.reliable++;
   R.rel = sqrt(R.rho2) / R.nf;
   if (!isfinite(R.rel)) {
@@ -1042,40 +1098,12 @@ static dd_status lock_end_cycle(dd_ctx* c, SolverBuffers& s, LockRhs& R, int mm,
     return DD_OK;
   }
   R.restarts++;
-  bool done_defl = false;
-  if (k > 0 && mm > k) {
-    size_t hb = (size_t)ldh * (m + 1) * sizeof(zd);
-    TRY(cuda_check(c, cudaMemcpyAsync(s.h_H, s.H, hb, cudaMemcpyDeviceToHost, c->st), "H"));
-    TRY(cuda_check(c, cudaMemcpyAsync(s.h_c0, s.c0, (m + 1) * sizeof(zd), cudaMemcpyDeviceToHost, c->st), "c"));
-    TRY(cuda_check(c, cudaMemcpyAsync(s.h_y, s.y, m * sizeof(zd), cudaMemcpyDeviceToHost, c->st), "y"));
-    TRY(cuda_check(c, cudaStreamSynchronize(c->st), "deflation inputs"));
-    int drc = deflate(s.h_H, ldh, mm, k, s.h_c0, s.h_y, s.h_P, s.h_Hn, s.h_cn, s.h_theta, *s.h_dw);
-    if (drc == 0) {
-      TRY(cuda_check(c, cudaMemcpyAsync(s.P, s.h_P, hb, cudaMemcpyHostToDevice, c->st), "P"));
-      TRY(cuda_check(c, cudaMemcpyAsync(s.Hn, s.h_Hn, hb, cudaMemcpyHostToDevice, c->st), "Hn"));
-      int nk = launch_recombine(s.V, s.V, mm + 1, k + 1, n4, (const double2*)s.P, ldh, c->st);
-      nk += launch_recombine(s.Z, s.Z, mm, k, n4, (const double2*)s.P, ldh, c->st);
-      launch_r64_to_v32(s.w, s.r64, n4, s.nrm2, c->st);
-      nk += launch_multi_dot(s.V, k + 1, n4, s.w, s.partial, c->st);
-      launch_reduce_partials(s.partial, k + 1, (double2*)s.cp, 0, c->st);
-      scale_coeffs_kernel<<<1, 1, 0, c->st>>>(s.cp, k + 1, s.nrm2);
-      TRY(launched(c, nk + 3));
-      std::vector<zd> cp(k + 1);
-      TRY(cuda_check(c, cudaMemcpyAsync(cp.data(), s.cp, (k + 1) * sizeof(zd), cudaMemcpyDeviceToHost, c->st), "cp"));
-      TRY(cuda_check(c, cudaStreamSynchronize(c->st), "cp"));
-      double pc = 0;
-      for (auto& z : cp) pc += abs2(z);
-      double miss = sqrt(fmax(0.0, 1.0 - pc / R.rho2));
-      if (miss <= defl_tol) {
-        restart_lsq_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, k, s.Hn, s.cp, s.g, s.c0, s.lsq, s.status);
-        TRY(launched(c));
-        R.j0 = k;
-        done_defl = true;
-        R.deflated++;
-      }
-    }
-  }
-  if (!done_defl) {
+  if (ce.deflate) {
+    restart_lsq_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, k, s.Hn, s.cp, s.g, s.c0, s.lsq, s.status);
+    TRY(launched(c));
+    R.j0 = k;
+    R.deflated++;
+  } else {
     launch_r64_to_v32(s.V, s.r64, n4, s.nrm2, c->st);
     plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq);
     TRY(launched(c, 2));
@@ -1291,6 +1319,228 @@ extern "C" dd_status dd_solve(dd_ctx* c, const double* f, double* x, int nrhs, i
   return worst;
 }
 
+// ------------------------------------------------------------------ BiCGstab comparison solver
+// The standard, non-domain-decomposed solvers the paper compares against (Sec. IV-C,
+// Table III): BiCGstab in FP64 on the FP64 operator, or an FP64 Richardson iteration
+// (defect correction) whose corrections come from BiCGstab in FP32 on the FP32 operator.
+namespace {
+struct BicgRun {
+  double tA = 0;
+  int a_apps = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+// A in -> out (or f - A in with f) in precision prec, timed
+dd_status bicg_apply(dd_ctx* c, BicgRun& R, const void* in, void* out, int prec, const void* f = nullptr) {
+  cudaEventRecord(R.e0, c->st);
+  TRY(apply_internal(c, in, out, prec, f));
+  cudaEventRecord(R.e1, c->st);
+  R.a_apps++;
+  return DD_OK;
+}
+
+// BiCGstab on A x = b (b given through r = b - A x on entry, x updated in place) until
+// |r| <= stop or iters reaches limit.  U: float4 (FP32) or double2 (FP64).  bnorm: |b|.
+// Returns the iterations taken; *rel: the recursive |r| / bnorm at exit.
+template <typename U>
+dd_status bicgstab(dd_ctx* c, BicgRun& R, int prec, U* x, U* r, U* rh, U* pv, U* v, U* s, U* t, zd* sc, double2* part,
+                   double* h_sc, double stop, int limit, int* iters, double* rnorm) {
+  using K = BicgKernels<U>;
+  const Geom& g = c->g;
+  K::copy(g, rh, r, c->st);
+  K::copy(g, pv, nullptr, c->st);
+  K::copy(g, v, nullptr, c->st);
+  launch_bicg_reset(sc, c->st);
+  TRY(launched(c, 4));
+  int it = 0;
+  double rn = *rnorm;
+  float ms = 0;
+  while (it < limit && rn > stop) {
+    K::dot(g, rh, r, nullptr, nullptr, part, sc, 4, c->st);
+    launch_bicg_scalars(sc, 0, c->st);
+    K::p_update(g, pv, r, v, sc, c->st);
+    TRY(launched(c, 4));
+    TRY(bicg_apply(c, R, pv, v, prec));
+    cudaEventSynchronize(R.e1);
+    cudaEventElapsedTime(&ms, R.e0, R.e1);
+    R.tA += ms * 1e-3;
+    K::dot(g, rh, v, nullptr, nullptr, part, sc, 5, c->st);
+    launch_bicg_scalars(sc, 1, c->st);
+    K::s_update(g, s, r, v, sc, c->st);
+    TRY(launched(c, 4));
+    TRY(bicg_apply(c, R, s, t, prec));
+    K::dot(g, t, s, t, t, part, sc, 6, c->st);
+    launch_bicg_scalars(sc, 2, c->st);
+    K::xr_update(g, x, r, pv, s, t, sc, part, c->st);
+    TRY(launched(c, 5));
+    TRY(cuda_check(c, cudaMemcpyAsync(h_sc, sc + 8, 2 * sizeof(zd), cudaMemcpyDeviceToHost, c->st), "bicgstab"));
+    TRY(cuda_check(c, cudaStreamSynchronize(c->st), "bicgstab"));
+    cudaEventElapsedTime(&ms, R.e0, R.e1);
+    R.tA += ms * 1e-3;
+    ++it;
+    rn = sqrt(h_sc[0]);
+    if (c->trace) fprintf(stderr, "[dd] bicgstab it %d |r| %.3e\n", it, rn);
+    if (!isfinite(rn)) return fail(c, DD_ERR_NONFINITE, "non-finite BiCGstab residual");
+    if (h_sc[2] != 0.0) {   // breakdown: restart the recurrence with rhat = r
+      K::copy(g, rh, r, c->st);
+      K::copy(g, pv, nullptr, c->st);
+      K::copy(g, v, nullptr, c->st);
+      launch_bicg_reset(sc, c->st);
+      TRY(launched(c, 4));
+    }
+  }
+  *iters = it;
+  *rnorm = rn;
+  return DD_OK;
+}
+
+__global__ void sqrt_to_coeff_kernel(double2* y, const double2* nrm2) { y[0] = make_double2(sqrt(nrm2->x), 0.0); }
+}  // namespace
+
+extern "C" dd_status dd_solve_bicgstab(dd_ctx* c, const double* f, double* x, int where, const dd_bicgstab_params* p,
+                                       dd_solve_info* info) {
+  if (!c || !f || !x || !p) return DD_ERR_INVALID;
+  if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
+  if (!(p->tol > 0) || p->max_iter < 1 || (p->precision != DD_PREC_FP64 && p->precision != DD_PREC_FP32) ||
+      (p->precision == DD_PREC_FP32 && !(p->inner_tol > 0 && p->inner_tol < 1)))
+    return fail(c, DD_ERR_INVALID, "bad BiCGstab parameters");
+  if (info) memset(info, 0, sizeof(*info));
+  const Geom& g = c->g;
+  const size_t b64 = field_bytes(g, P64), b32 = field_bytes(g, P32);
+  const bool mixed = p->precision == DD_PREC_FP32;
+  const size_t bw = mixed ? b32 : b64;
+  std::vector<void*> bufs;
+  auto alloc = [&](void** q, size_t n) -> dd_status {
+    dd_status st = dalloc(c, q, n);
+    if (st == DD_OK) bufs.push_back(*q);
+    return st;
+  };
+  struct Cleanup {
+    dd_ctx* c;
+    std::vector<void*>* b;
+    BicgRun* R;
+    ~Cleanup() {
+      cudaStreamSynchronize(c->st);
+      for (void* q : *b) release(c, q);
+      if (R->e0) cudaEventDestroy(R->e0);
+      if (R->e1) cudaEventDestroy(R->e1);
+    }
+  };
+  BicgRun R;
+  Cleanup cleanup{c, &bufs, &R};
+  void *x64, *f64, *r64, *canon, *xw, *r, *rh, *pv, *v, *s, *t, *part, *sc, *coef;
+  TRY(alloc(&x64, b64));
+  TRY(alloc(&f64, b64));
+  TRY(alloc(&r64, b64));
+  TRY(alloc(&canon, b64));
+  for (void** q : {&xw, &r, &rh, &pv, &v, &s, &t}) TRY(alloc(q, bw));
+  TRY(alloc(&part, 2 * (size_t)blas_partials_blocks() * sizeof(double2)));
+  TRY(alloc(&sc, 16 * sizeof(zd)));
+  TRY(alloc(&coef, 2 * sizeof(double2)));
+  double* h_sc = nullptr;
+  if (cudaMallocHost(&h_sc, 4 * sizeof(double)) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned scalars");
+  struct HostFree { double* p; ~HostFree() { cudaFreeHost(p); } } hf{h_sc};
+  cudaEventCreate(&R.e0);
+  cudaEventCreate(&R.e1);
+  cudaEvent_t tstart, tend;
+  cudaEventCreate(&tstart);
+  cudaEventCreate(&tend);
+  struct EvFree { cudaEvent_t a, b; ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(b); } } ef{tstart, tend};
+  const size_t cb = (size_t)g.V * 24 * 8;
+  cudaMemcpyKind in_kind = where == DD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaEventRecord(tstart, c->st);
+  TRY(cuda_check(c, cudaMemcpyAsync(canon, f, cb, in_kind, c->st), "copy f"));
+  launch_pack_spinor(g, canon, P64, view(g, f64, P64), c->st);
+  TRY(cuda_check(c, cudaMemcpyAsync(canon, x, cb, in_kind, c->st), "copy x"));
+  launch_pack_spinor(g, canon, P64, view(g, x64, P64), c->st);
+  TRY(launched(c, 2));
+  // |f| and the FP64 residual
+  double2* part2 = (double2*)part;
+  auto norm64 = [&](const void* field, double* out) -> dd_status {
+    launch_norm2_64((const double2*)field, g.V * 12, part2, c->st);
+    launch_reduce_partials(part2, 1, (double2*)coef + 1, 0, c->st);
+    TRY(launched(c, 2));
+    double2 h;
+    TRY(cuda_check(c, cudaMemcpyAsync(&h, (double2*)coef + 1, sizeof(h), cudaMemcpyDeviceToHost, c->st), "norm"));
+    TRY(cuda_check(c, cudaStreamSynchronize(c->st), "norm"));
+    *out = h.x;
+    return DD_OK;
+  };
+  double nf2 = 0;
+  TRY(norm64(f64, &nf2));
+  const double nf = sqrt(nf2);
+  dd_status rc = DD_OK;
+  int iters = 0, outer = 0, reliable = 0;
+  double rel = 0;
+  if (nf2 == 0.0) {
+    cudaMemsetAsync(x64, 0, b64, c->st);
+  } else {
+    while (true) {
+      // FP64 true residual
+      TRY(bicg_apply(c, R, x64, r64, P64, f64));
+      reliable++;
+      double rho2 = 0;
+      TRY(norm64(r64, &rho2));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, R.e0, R.e1);
+      R.tA += ms * 1e-3;
+      rel = sqrt(rho2) / nf;
+      if (c->trace) fprintf(stderr, "[dd] bicgstab outer %d true residual %.3e\n", outer, rel);
+      if (!isfinite(rel)) { rc = fail(c, DD_ERR_NONFINITE, "non-finite residual"); break; }
+      if (rel <= p->tol) break;
+      if (iters >= p->max_iter) { rc = fail(c, DD_ERR_NOT_CONVERGED, "iteration limit reached"); break; }
+      int it = 0;
+      if (!mixed) {
+        // FP64 BiCGstab on the true residual; its recursive residual drifts, so it stops a
+        // little below the target and the loop recomputes the true one
+        BicgKernels<double2>::copy(g, (double2*)r, (const double2*)r64, c->st);
+        TRY(launched(c));
+        double rn = sqrt(rho2);
+        TRY(bicgstab<double2>(c, R, P64, (double2*)x64, (double2*)r, (double2*)rh, (double2*)pv, (double2*)v,
+                              (double2*)s, (double2*)t, (zd*)sc, part2, h_sc, 0.5 * p->tol * nf,
+                              p->max_iter - iters, &it, &rn));
+      } else {
+        // correction e from A32 e = r / |r| to inner_tol, then x += |r| e in FP64
+        launch_norm2_64((const double2*)r64, g.V * 12, part2, c->st);
+        launch_reduce_partials(part2, 1, (double2*)coef + 1, 0, c->st);
+        launch_r64_to_v32((float4*)r, (const double2*)r64, g.V * 6, (const double2*)coef + 1, c->st);
+        BicgKernels<float4>::copy(g, (float4*)xw, nullptr, c->st);
+        TRY(launched(c, 4));
+        double rn = 1.0;
+        TRY(bicgstab<float4>(c, R, P32, (float4*)xw, (float4*)r, (float4*)rh, (float4*)pv, (float4*)v, (float4*)s,
+                             (float4*)t, (zd*)sc, part2, h_sc, p->inner_tol, p->max_iter - iters, &it, &rn));
+        sqrt_to_coeff_kernel<<<1, 1, 0, c->st>>>((double2*)coef, (const double2*)coef + 1);
+        launch_x_update((double2*)x64, (const float4*)xw, 1, g.V * 6, (const double2*)coef, c->st);
+        TRY(launched(c, 2));
+      }
+      iters += it;
+      outer++;
+      if (it == 0) { rc = fail(c, DD_ERR_NOT_CONVERGED, "BiCGstab made no progress"); break; }
+    }
+  }
+  launch_unpack_spinor(g, view(g, x64, P64), canon, P64, c->st);
+  TRY(launched(c));
+  TRY(cuda_check(c, cudaMemcpyAsync(x, canon, cb, where == DD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                    c->st),
+                 "copy x out"));
+  cudaEventRecord(tend, c->st);
+  TRY(cuda_check(c, cudaStreamSynchronize(c->st), "bicgstab"));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, tstart, tend);
+  if (info) {
+    info->status = rc;
+    info->iterations = iters;
+    info->restarts = outer > 0 ? outer - 1 : 0;
+    info->reliable_updates = reliable;
+    info->true_rel_residual = rel;
+    info->t_total = ms * 1e-3;
+    info->t_A = R.tA;
+    info->t_other = ms * 1e-3 - R.tA;
+    info->flops_nominal = 1848.0 * (double)g.V * R.a_apps;
+  }
+  return rc;
+}
+
 // ------------------------------------------------------------------ host utilities
 extern "C" double dd_load_model(long long n, int slots) {
   if (n <= 0 || slots <= 0) return 0.0;
@@ -1303,7 +1553,8 @@ extern "C" dd_status dd_deflate_host(int m, int k, const double* Hbar, const dou
   if (m < 1 || m >= DD_MAXM || k < 1 || k >= m || !Hbar || !cvec || !yvec || !P || !Hn || !cn || !theta)
     return DD_ERR_INVALID;
   DeflateWork* W = new DeflateWork();
-  int rc = deflate((const zd*)Hbar, m + 1, m, k, (const zd*)cvec, (const zd*)yvec, (zd*)P, (zd*)Hn, (zd*)cn,
+  const Team T{0, 1};
+  int rc = deflate(T, (const zd*)Hbar, m + 1, m, k, (const zd*)cvec, (const zd*)yvec, (zd*)P, (zd*)Hn, (zd*)cn,
                    (zd*)theta, *W);
   delete W;
   return rc == 0 ? DD_OK : DD_ERR_NONFINITE;

@@ -147,15 +147,17 @@ void launch_x_update(double2* x, const float4* Z, int nz, long long n4, const do
 
 // v = r / sqrt(nrm2) in FP32 (the FP64 and FP32 layouts hold the same complex numbers
 // in the same order: double2 unit 2q and 2q+1 <-> float4 unit q).
-__global__ void r64_to_v32_kernel(float4* v, const double2* r, long long n4, const double2* nrm2) {
+__global__ void r64_to_v32_kernel(float4* v, const double2* r, long long n4, const double2* nrm2, const int* gate) {
+  if (gate && *gate != 1) return;
   double s = 1.0 / sqrt(nrm2->x);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
     double2 a = r[2 * q], b = r[2 * q + 1];
     v[q] = make_float4((float)(a.x * s), (float)(a.y * s), (float)(b.x * s), (float)(b.y * s));
   }
 }
-void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2* nrm2, cudaStream_t st) {
-  r64_to_v32_kernel<<<blas_partials_blocks(), BT, 0, st>>>(v, r, n4, nrm2);
+void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2* nrm2, cudaStream_t st,
+                       const int* gate) {
+  r64_to_v32_kernel<<<blas_partials_blocks(), BT, 0, st>>>(v, r, n4, nrm2, gate);
 }
 
 // out_l = sum_i P[i + l ldp] V_i for l < nout (P complex FP64, column-major).  One pass
@@ -167,7 +169,8 @@ void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2*
 constexpr int RBT = 128, RU = 8;
 template <int NO>
 __global__ void __launch_bounds__(RBT) recombine_kernel(float4* out, const float4* V, int nv, int l0,
-                                                        long long n4, const double2* P, int ldp) {
+                                                        long long n4, const double2* P, int ldp, const int* gate) {
+  if (gate && *gate != 1) return;
   __shared__ float2 ps[64][NO];
   for (int t = threadIdx.x; t < nv * NO; t += RBT) {
     int i = t / NO, l = t % NO;
@@ -205,18 +208,18 @@ __global__ void __launch_bounds__(RBT) recombine_kernel(float4* out, const float
 
 template <int NO>
 static void recombine_launch(int nl, float4* out, const float4* V, int nv, int l0, long long n4, const double2* P,
-                             int ldp, cudaStream_t st) {
+                             int ldp, cudaStream_t st, const int* gate) {
   if constexpr (NO > 1) {
-    if (nl < NO) return recombine_launch<NO - 1>(nl, out, V, nv, l0, n4, P, ldp, st);
+    if (nl < NO) return recombine_launch<NO - 1>(nl, out, V, nv, l0, n4, P, ldp, st, gate);
   }
-  recombine_kernel<NO><<<2 * blas_partials_blocks(), RBT, 0, st>>>(out, V, nv, l0, n4, P, ldp);
+  recombine_kernel<NO><<<2 * blas_partials_blocks(), RBT, 0, st>>>(out, V, nv, l0, n4, P, ldp, gate);
 }
 
 int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n4, const double2* P, int ldp,
-                     cudaStream_t st) {
+                     cudaStream_t st, const int* gate) {
   int n = 0;
   for (int l0 = 0; l0 < nout; l0 += 16, ++n)
-    recombine_launch<16>(nout - l0 < 16 ? nout - l0 : 16, out, V, nv, l0, n4, P, ldp, st);
+    recombine_launch<16>(nout - l0 < 16 ? nout - l0 : 16, out, V, nv, l0, n4, P, ldp, st, gate);
   return n;
 }
 

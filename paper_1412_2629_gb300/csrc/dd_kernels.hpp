@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "dd_common.cuh"
+#include "smalldense.cuh"
 
 namespace dd {
 
@@ -93,9 +94,12 @@ int launch_multi_dot(const float4* V, int nv, long long n4, const float4* w, dou
 void launch_reduce_partials(const double2* partial, int nv, double2* out, int accumulate, cudaStream_t st);
 void launch_norm2_64(const double2* x, long long n2, double2* partial, cudaStream_t st);
 void launch_x_update(double2* x, const float4* Z, int nz, long long n4, const double2* y, cudaStream_t st);
-void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2* nrm2, cudaStream_t st);
+// v = r / sqrt(nrm2); with a gate, only when *gate == 1
+void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2* nrm2, cudaStream_t st,
+                       const int* gate = nullptr);
+// out_l = sum_i P(i, l) V_i for l < nout (in place allowed); with a gate, only when *gate == 1
 int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n4, const double2* P, int ldp,
-                      cudaStream_t st);
+                     cudaStream_t st, const int* gate = nullptr);
 
 // Classical Gram-Schmidt passes with device-gated reorthogonalisation (blas.cu).  A kernel
 // given a gate runs only when *gate == want.
@@ -105,4 +109,22 @@ void launch_gs_reduce(const double2* partial, int nv, double2* out, const int* g
 void launch_gs_project(float4* out, const float4* w, const float4* V, int nv, long long n4, const double2* h,
                        double2* norm_partial, const int* gate, int want, cudaStream_t st);
 void launch_scale_inplace(float4* v, long long n4, const double* nu2, cudaStream_t st);
+
+// ---- BiCGstab comparison solver (krylov.cu).  U = float4 (FP32 fields) or double2 (FP64
+// fields); sc: the recurrence's scalars on the device (see krylov.cu); partial: at least
+// 2 blas_partials_blocks() double2.
+template <typename U>
+struct BicgKernels {
+  // sc[slot] = <a, b>; with c, d also sc[slot + 1] = <c, d>
+  static void dot(const Geom& g, const U* a, const U* b, const U* c, const U* d, double2* partial, zd* sc, int slot,
+                  cudaStream_t st);
+  static void p_update(const Geom& g, U* p, const U* r, const U* v, const zd* sc, cudaStream_t st);
+  static void s_update(const Geom& g, U* s, const U* r, const U* v, const zd* sc, cudaStream_t st);
+  // x += alpha p + omega s, r = s - omega t, sc[8] = |r|^2
+  static void xr_update(const Geom& g, U* x, U* r, const U* p, const U* s, const U* t, zd* sc, double2* partial,
+                        cudaStream_t st);
+  static void copy(const Geom& g, U* dst, const U* src, cudaStream_t st);   // src null: zero
+};
+void launch_bicg_scalars(zd* sc, int stage, cudaStream_t st);
+void launch_bicg_reset(zd* sc, cudaStream_t st);
 }  // namespace dd

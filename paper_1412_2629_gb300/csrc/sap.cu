@@ -985,9 +985,55 @@ __device__ inline void hops_half_mask(int h, const Geom& g, unsigned fwd, unsign
 // scaled by a power of two, 16 / 2^ceil(log2 max|r|), before it enters the work buffers,
 // and everything that leaves them (the new residual, delta) is scaled back.  The MR
 // iteration is invariant under that scaling and powers of two are exact in FP32.
-template <typename MT, typename VT, bool MSMEM, bool H2>
+// Domain shapes the two-thread kernel is also compiled for (SHAPE 1: 8x4x4x4, 2: 4x4x4x4;
+// 0: shape read at run time).  With the shape known at compile time every local stride,
+// site count and work-buffer offset is a constant, so shared-memory addresses fold into
+// immediate offsets and the index arithmetic of the hop phases disappears.
+template <int SHAPE> struct ShapeOf;
+template <> struct ShapeOf<1> {
+  __host__ __device__ static constexpr int b(int mu) { return mu == 0 ? 8 : 4; }
+  __host__ __device__ static constexpr int lg(int mu) { return mu == 0 ? 3 : 2; }
+};
+template <> struct ShapeOf<2> {
+  __host__ __device__ static constexpr int b(int) { return 4; }
+  __host__ __device__ static constexpr int lg(int) { return 2; }
+};
+
+int sap_shape_id(const Geom& g) {
+  if (g.b[0] == 8 && g.b[1] == 4 && g.b[2] == 4 && g.b[3] == 4) return 1;
+  if (g.b[0] == 4 && g.b[1] == 4 && g.b[2] == 4 && g.b[3] == 4) return 2;
+  return 0;
+}
+
+// The geometry with the domain fields replaced by compile-time constants (SHAPE != 0).
+template <int SHAPE>
+__device__ __forceinline__ Geom fixed_shape(const Geom& in) {
+  Geom g = in;
+  if constexpr (SHAPE != 0) {
+    using S = ShapeOf<SHAPE>;
+    constexpr int vd = S::b(0) * S::b(1) * S::b(2) * S::b(3);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      g.b[mu] = S::b(mu);
+      g.lgb[mu] = S::lg(mu);
+      g.face_n[mu] = vd / S::b(mu);
+    }
+    g.bstride[0] = 1;
+    g.bstride[1] = S::b(0);
+    g.bstride[2] = S::b(0) * S::b(1);
+    g.bstride[3] = S::b(0) * S::b(1) * S::b(2);
+    g.Vd = vd;
+    g.Hd = vd / 2;
+    g.lgVd = S::lg(0) + S::lg(1) + S::lg(2) + S::lg(3);
+  }
+  return g;
+}
+
+template <typename MT, typename VT, bool MSMEM, bool H2, int SHAPE = 0>
 __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
-  const Geom& g = a.g;
+  // hop phases use g (constant domain fields when SHAPE != 0); the face code, which indexes
+  // the face offsets at run time, reads the kernel parameters a.g directly
+  const Geom g = fixed_shape<SHAPE>(a.g);
   extern __shared__ float4 smem[];
   __shared__ uint64_t mbar, mbar_inj;   // staged copies; injected bytes (test hook)
   __shared__ float4 red[2 * SAP_MAX_THREADS / 32];
@@ -1084,8 +1130,8 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
     if (a.use_faces) {
       Spinor<float> acc;
       zero(acc);
-      if (h) face_hops_rt(g, (int)d, n, lo, fs, bs, r_site, fr, M, acc);
-      else face_hops_rt(g, (int)d, n, le, fs, bs, r_site, fr, M, acc);
+      if (h) face_hops_rt(a.g, (int)d, n, lo, fs, bs, r_site, fr, M, acc);
+      else face_hops_rt(a.g, (int)d, n, le, fs, bs, r_site, fr, M, acc);
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -1177,12 +1223,27 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
       }
       if ((tid & 31) == 0) red[tid >> 5] = make_float4(pr_re, pr_im, pp, 0.f);
       __syncthreads();
+      // every warp sums the nwarp partial sums the same way (lane l holds entry l, a
+      // butterfly over the lanes, lane 0's total broadcast), so all threads get one alpha
       float sr = 0.f, si = 0.f, sp = 0.f;
-      for (int w = 0; w < nwarp; ++w) {
-        float4 q = red[w];
-        sr += q.x;
-        si += q.y;
-        sp += q.z;
+      {
+        const int lane = tid & 31;
+        if (lane < nwarp) {
+          const float4 q = red[lane];
+          sr = q.x;
+          si = q.y;
+          sp = q.z;
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          if (o >= nwarp) break;
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+          sp += __shfl_xor_sync(0xffffffffu, sp, o);
+        }
+        sr = __shfl_sync(0xffffffffu, sr, 0);
+        si = __shfl_sync(0xffffffffu, si, 0);
+        sp = __shfl_sync(0xffffffffu, sp, 0);
       }
       cx<float> alpha = sp > 0.f ? mk(sr / sp, si / sp) : mk(0.f, 0.f);
 #pragma unroll
@@ -1235,16 +1296,16 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
     ust.store(g, s_site, u);
   }
   if (!(a.last && a.colour == 1)) {
-    if (h) face_write_rt(g, d, lo, fs, bs, r_site, fr, M, dl);
-    else face_write_rt(g, d, le, fs, bs, r_site, fr, M, dl);
+    if (h) face_write_rt(a.g, d, lo, fs, bs, r_site, fr, M, dl);
+    else face_write_rt(a.g, d, le, fs, bs, r_site, fr, M, dl);
   }
   __syncthreads();   // the work buffers are reused by the next right-hand side
   }
 }
 
-template <typename MT, typename VT, bool MSMEM, bool H2>
+template <typename MT, typename VT, bool MSMEM, bool H2, int SHAPE>
 __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArgs a) {
-  sap_pair_body<MT, VT, MSMEM, H2>(a, blockIdx.x);
+  sap_pair_body<MT, VT, MSMEM, H2, SHAPE>(a, blockIdx.x);
 }
 
 // Several lattices of the same domain shape in one launch: the grid is the concatenation
@@ -1293,18 +1354,27 @@ static int smem_optin() {
 
 int sap_max_domain_sites() { return 2 * SAP_MAX_THREADS; }
 
+template <typename MT, typename VT, bool MSMEM, bool H2, int SHAPE>
+static void launch_pair(const SapArgs& a, int grid, size_t smem, cudaStream_t st) {
+  static int configured = 0;
+  if (!configured) {
+    // static shared memory (barriers, reduction slots) is a few KB; the rest may be dynamic
+    cudaFuncSetAttribute(sap_kernel_pair<MT, VT, MSMEM, H2, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem_optin() - 4096);
+    configured = 1;
+  }
+  sap_kernel_pair<MT, VT, MSMEM, H2, SHAPE><<<grid, 2 * a.g.Hd, smem, st>>>(a);
+}
+
 template <typename MT, typename VT, bool MSMEM, bool H2 = false>
 static int launch_one(const SapArgs& a, int grid, int pair, cudaStream_t st) {
   size_t smem = sap_smem_bytes(a.g, std::is_same<MT, __half>::value ? P16 : P32, MSMEM);
-  // static shared memory (barrier, reduction slots) is at most a few KB; the rest may be dynamic
   if (pair) {
-    static int configured = 0;
-    if (!configured) {
-      cudaFuncSetAttribute(sap_kernel_pair<MT, VT, MSMEM, H2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem_optin() - 4096);
-      configured = 1;
+    switch (sap_shape_id(a.g)) {
+      case 1: launch_pair<MT, VT, MSMEM, H2, 1>(a, grid, smem, st); break;
+      case 2: launch_pair<MT, VT, MSMEM, H2, 2>(a, grid, smem, st); break;
+      default: launch_pair<MT, VT, MSMEM, H2, 0>(a, grid, smem, st); break;
     }
-    sap_kernel_pair<MT, VT, MSMEM, H2><<<grid, 2 * a.g.Hd, smem, st>>>(a);
   } else {
     static int configured = 0;
     if (!configured) {

@@ -1,8 +1,10 @@
 // Small dense complex FP64 algebra of the outer solver (FGMRES with deflated restarts).
 // Everything here works on (m+1) x m problems with m <= DD_MAXM, in column-major
-// arrays with leading dimension ld, and compiles for host and device: the solver runs
-// it on the device in a one-thread kernel; the C ABI also exposes the host build so it
-// can be checked without a GPU.
+// arrays with leading dimension ld, and compiles for host and device.  The incremental
+// least-squares solver runs on the device in one-thread kernels; the deflated restart
+// (harmonic Ritz pairs and the new basis coefficients) is written for a team of threads
+// that share every step: the solver runs it as one warp on the device, and the C ABI
+// runs the same code with a team of one on the host so it can be checked without a GPU.
 #pragma once
 
 #include <math.h>
@@ -93,41 +95,111 @@ DD_HD inline void lsq_solve(const zd* R, int ld, int n, const zd* g, zd* y) {
   }
 }
 
-// ---------------------------------------------------------------- eigen-decomposition
-// A (n x n, leading dimension ld) is overwritten by its Schur form T = Q^H A Q; Q (ld)
-// receives the unitary factor.  Givens reduction to Hessenberg form, then the implicit
-// single-shift QR iteration with Wilkinson shifts.  Returns the number of iterations or
-// -1 if it did not converge.
-DD_HD inline int schur(zd* A, zd* Q, int n, int ld) {
+// ---------------------------------------------------------------- cooperative team
+// The threads that share the deflated restart: thread tid of nt; sync() separates steps
+// (a barrier of the CTA on the device, nothing on the host, where nt = 1).  Every member
+// runs the same control flow: decisions are taken from data that all of them read after
+// the same barrier.
+struct Team {
+  int tid, nt;
+  DD_HD void sync() const {
+#ifdef __CUDA_ARCH__
+    __syncthreads();
+#endif
+  }
+};
+
+// ---------------------------------------------------------------- Hessenberg LU
+// In place LU of the upper Hessenberg A (n x n, ld) with partial pivoting between the two
+// rows that can hold column c's pivot: step c swaps rows c, c+1 when |A(c+1, c)| is the
+// larger (piv[c] = 1) and subtracts l[c] times row c from row c+1.  An exactly zero pivot
+// is replaced by `tiny` (inverse iteration factors matrices that are singular up to
+// rounding).  The strictly lower part of A is left undefined.
+DD_HD inline void hess_lu(const Team& T, zd* A, int n, int ld, int* piv, zd* l, double tiny) {
   auto a = [&](int i, int j) -> zd& { return A[i + (long)j * ld]; };
-  auto q = [&](int i, int j) -> zd& { return Q[i + (long)j * ld]; };
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) q(i, j) = Z(i == j ? 1.0 : 0.0);
-  // Hessenberg reduction: zero a(i, j) for i > j + 1 using rows (i - 1, i)
-  for (int j = 0; j + 2 < n; ++j)
-    for (int i = n - 1; i >= j + 2; --i) {
-      if (abs2(a(i, j)) == 0.0) continue;
-      Rot r = make_rot(a(i - 1, j), a(i, j));
-      for (int k = 0; k < n; ++k) rot_apply(r, a(i - 1, k), a(i, k));
-      for (int k = 0; k < n; ++k) rot_apply_right(r, a(k, i - 1), a(k, i));
-      for (int k = 0; k < n; ++k) rot_apply_right(r, q(k, i - 1), q(k, i));
-      a(i, j) = Z(0.0);
+  for (int c = 0; c + 1 < n; ++c) {
+    const bool sw = abs2(a(c + 1, c)) > abs2(a(c, c));
+    T.sync();   // every member has read the pivot candidates
+    if (sw)
+      for (int j = c + T.tid; j < n; j += T.nt) { zd t = a(c, j); a(c, j) = a(c + 1, j); a(c + 1, j) = t; }
+    T.sync();
+    zd d = a(c, c);
+    if (abs2(d) == 0.0) d = Z(tiny);
+    const zd f = zdiv(a(c + 1, c), d);
+    T.sync();   // every member has read row c + 1's first entry
+    for (int j = c + 1 + T.tid; j < n; j += T.nt) a(c + 1, j) = a(c + 1, j) - f * a(c, j);
+    if (T.tid == 0) {
+      a(c, c) = d;
+      piv[c] = sw ? 1 : 0;
+      l[c] = f;
     }
-  int total = 0;
-  int hi = n - 1, iter = 0;
+    T.sync();
+  }
+  if (T.tid == 0 && abs2(a(n - 1, n - 1)) == 0.0) a(n - 1, n - 1) = Z(tiny);
+  T.sync();
+}
+
+// x <- U^{-1} x for the upper triangle U of A (column-oriented back substitution).
+DD_HD inline void upper_solve(const Team& T, const zd* A, int n, int ld, zd* x) {
+  for (int i = n - 1; i >= 0; --i) {
+    if (T.tid == 0) x[i] = zdiv(x[i], A[i + (long)i * ld]);
+    T.sync();
+    for (int r = T.tid; r < i; r += T.nt) x[r] = x[r] - A[r + (long)i * ld] * x[i];
+    T.sync();
+  }
+}
+
+// x <- (A^H)^{-1} x for the factored Hessenberg A = (L-steps)^{-1} U: first U^H g = x by
+// forward substitution, then the adjoint of every elimination and swap, last step first.
+DD_HD inline void hess_solve_adjoint(const Team& T, const zd* A, int n, int ld, const int* piv, const zd* l, zd* x) {
+  for (int i = 0; i < n; ++i) {
+    if (T.tid == 0) x[i] = zdiv(x[i], conj(A[i + (long)i * ld]));
+    T.sync();
+    for (int r = i + 1 + T.tid; r < n; r += T.nt) x[r] = x[r] - conj(A[i + (long)r * ld]) * x[i];
+    T.sync();
+  }
+  if (T.tid == 0)
+    for (int c = n - 2; c >= 0; --c) {
+      x[c] = x[c] - conj(l[c]) * x[c + 1];
+      if (piv[c]) { zd t = x[c]; x[c] = x[c + 1]; x[c + 1] = t; }
+    }
+  T.sync();
+}
+
+// x <- A^{-1} x for the factored Hessenberg A: the swaps and eliminations in order, then U.
+DD_HD inline void hess_solve(const Team& T, const zd* A, int n, int ld, const int* piv, const zd* l, zd* x) {
+  if (T.tid == 0)
+    for (int c = 0; c + 1 < n; ++c) {
+      if (piv[c]) { zd t = x[c]; x[c] = x[c + 1]; x[c + 1] = t; }
+      x[c + 1] = x[c + 1] - l[c] * x[c];
+    }
+  T.sync();
+  upper_solve(T, A, n, ld, x);
+}
+
+// ---------------------------------------------------------------- eigenvalues
+// Eigenvalues of the upper Hessenberg A (n x n, ld) by the implicit single-shift QR
+// iteration with Wilkinson shifts (an exceptional shift every 11th step), each sweep
+// restricted to the active block [lo, hi]: A's diagonal holds the eigenvalues on return.
+// Returns the number of sweeps, or -1 if the iteration did not converge.
+DD_HD inline int hess_eigenvalues(const Team& T, zd* A, int n, int ld) {
+  auto a = [&](int i, int j) -> zd& { return A[i + (long)j * ld]; };
   const double eps = 2.220446049250313e-16;
+  int total = 0, hi = n - 1, iter = 0;
   while (hi > 0) {
     int lo = hi;
     while (lo > 0) {
       double s = zabs(a(lo - 1, lo - 1)) + zabs(a(lo, lo));
       if (s == 0.0) s = 1.0;
-      if (zabs(a(lo, lo - 1)) <= eps * s) { a(lo, lo - 1) = Z(0.0); break; }
+      if (zabs(a(lo, lo - 1)) <= eps * s) break;
       --lo;
     }
+    T.sync();
+    if (lo > 0 && T.tid == 0) a(lo, lo - 1) = Z(0.0);
+    T.sync();
     if (lo == hi) { --hi; iter = 0; continue; }
     if (++iter > 60 * n) return -1;
     ++total;
-    // Wilkinson shift: eigenvalue of the trailing 2x2 block closest to a(hi, hi)
     zd aa = a(hi - 1, hi - 1), bb = a(hi - 1, hi), cc = a(hi, hi - 1), dd = a(hi, hi);
     zd tr2 = 0.5 * (aa + dd);
     zd det = aa * dd - bb * cc;
@@ -136,163 +208,167 @@ DD_HD inline int schur(zd* A, zd* Q, int n, int ld) {
     zd sq = Z(sqrt(rr) * cos(0.5 * th), sqrt(rr) * sin(0.5 * th));
     zd l1 = tr2 + sq, l2 = tr2 - sq;
     zd mu = abs2(l1 - dd) < abs2(l2 - dd) ? l1 : l2;
-    if (iter % 11 == 10) mu = dd + Z(zabs(a(hi, hi - 1)), 0.0);   // exceptional shift
+    if (iter % 11 == 10) mu = dd + Z(zabs(a(hi, hi - 1)), 0.0);
     zd x = a(lo, lo) - mu, y = a(lo + 1, lo);
     for (int k = lo; k < hi; ++k) {
-      Rot r = make_rot(x, y);
-      int c0 = k > lo ? k - 1 : lo;
-      for (int j = c0; j < n; ++j) rot_apply(r, a(k, j), a(k + 1, j));
-      int r1 = k + 2 < hi ? k + 2 : hi;
-      for (int i = 0; i <= r1; ++i) rot_apply_right(r, a(i, k), a(i, k + 1));
-      for (int i = 0; i < n; ++i) rot_apply_right(r, q(i, k), q(i, k + 1));
-      if (k > lo) a(k + 1, k - 1) = Z(0.0);
+      const Rot r = make_rot(x, y);
+      const int c0 = k > lo ? k - 1 : lo;
+      T.sync();   // every member has read x, y
+      for (int j = c0 + T.tid; j <= hi; j += T.nt) rot_apply(r, a(k, j), a(k + 1, j));
+      T.sync();
+      const int r1 = k + 2 < hi ? k + 2 : hi;
+      for (int i = lo + T.tid; i <= r1; i += T.nt) rot_apply_right(r, a(i, k), a(i, k + 1));
+      T.sync();
+      if (k > lo && T.tid == 0) a(k + 1, k - 1) = Z(0.0);
       if (k + 1 < hi) { x = a(k + 1, k); y = a(k + 2, k); }
     }
+    T.sync();
   }
   return total;
 }
 
-// Eigenvector of the upper triangular T for eigenvalue T(e, e), mapped back by Q and
-// normalised; written to v[0:n].
-DD_HD inline void schur_eigvec(const zd* T, const zd* Q, int n, int ld, int e, zd* y, zd* v) {
-  double tn = 0;
-  for (int i = 0; i < n; ++i)
-    for (int j = i; j < n; ++j) tn = fmax(tn, zabs(T[i + (long)j * ld]));
-  const double small = 1e-15 * (tn > 0 ? tn : 1.0);
-  zd lam = T[e + (long)e * ld];
-  for (int i = 0; i < n; ++i) y[i] = Z(0.0);
-  y[e] = Z(1.0);
-  for (int i = e - 1; i >= 0; --i) {
-    zd s = Z(0.0);
-    for (int j = i + 1; j <= e; ++j) s = s + T[i + (long)j * ld] * y[j];
-    zd d = T[i + (long)i * ld] - lam;
-    if (zabs(d) < small) d = Z(small);
-    y[i] = -zdiv(s, d);
-  }
-  double nrm = 0;
-  for (int i = 0; i < n; ++i) {
-    zd s = Z(0.0);
-    for (int j = 0; j <= e; ++j) s = s + Q[i + (long)j * ld] * y[j];
-    v[i] = s;
-    nrm += abs2(s);
-  }
-  nrm = sqrt(nrm);
-  for (int i = 0; i < n; ++i) v[i] = (1.0 / nrm) * v[i];
-}
-
-// Solve M x = b (n x n, column-major, overwritten) by Gaussian elimination with
-// partial pivoting.  Returns false if a pivot is exactly zero.
-DD_HD inline bool dense_solve(zd* M, int n, int ld, zd* b) {
-  for (int c = 0; c < n; ++c) {
-    int p = c;
-    double best = -1;
-    for (int r = c; r < n; ++r) if (zabs(M[r + (long)c * ld]) > best) { best = zabs(M[r + (long)c * ld]); p = r; }
-    if (best == 0.0) return false;
-    if (p != c) {
-      for (int j = 0; j < n; ++j) { zd t = M[c + (long)j * ld]; M[c + (long)j * ld] = M[p + (long)j * ld]; M[p + (long)j * ld] = t; }
-      zd t = b[c]; b[c] = b[p]; b[p] = t;
-    }
-    for (int r = c + 1; r < n; ++r) {
-      zd f = zdiv(M[r + (long)c * ld], M[c + (long)c * ld]);
-      for (int j = c; j < n; ++j) M[r + (long)j * ld] = M[r + (long)j * ld] - f * M[c + (long)j * ld];
-      b[r] = b[r] - f * b[c];
-    }
-  }
-  for (int i = n - 1; i >= 0; --i) {
-    zd s = b[i];
-    for (int j = i + 1; j < n; ++j) s = s - M[i + (long)j * ld] * b[j];
-    b[i] = zdiv(s, M[i + (long)i * ld]);
-  }
-  return true;
-}
-
-// Workspace for the deflated restart, sized for DD_MAXM.
+// Workspace of the deflated restart, sized for DD_MAXM.
 struct DeflateWork {
-  zd G[DD_MAXM * DD_MAXM];
-  zd Q[DD_MAXM * DD_MAXM];
-  zd M[DD_MAXM * DD_MAXM];
+  zd G[DD_MAXM * DD_MAXM];    // H_m + |h|^2 f e_m^H, reduced by the QR iteration
+  zd G0[DD_MAXM * DD_MAXM];   // the same matrix, kept for the inverse iteration
+  zd M[DD_MAXM * DD_MAXM];    // LU factors
   zd f[DD_MAXM + 1];
-  zd y[DD_MAXM + 1];
   zd v[DD_MAXM + 1];
   zd cls[DD_MAXM + 1];
+  zd l[DD_MAXM];
+  zd dot[DD_MAXM + 1];
+  double nrm;
+  int piv[DD_MAXM];
   double absth[DD_MAXM];
   int order[DD_MAXM];
 };
 
-// Deflated restart of flexible GMRES-DR.
+// p <- p - sum_t (p_t^H p) p_t over the first nprev columns of P (ld), twice, then p / |p|;
+// returns |p| before the final scaling.
+DD_HD inline double orthonormalise(const Team& T, zd* P, int ld, int nprev, int len, zd* p, DeflateWork& W) {
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int t = T.tid; t < nprev; t += T.nt) {
+      const zd* pt = P + (long)t * ld;
+      zd d = Z(0.0);
+      for (int i = 0; i < len; ++i) d = d + conj(pt[i]) * p[i];
+      W.dot[t] = d;
+    }
+    T.sync();
+    for (int i = T.tid; i < len; i += T.nt) {
+      zd s = p[i];
+      for (int t = 0; t < nprev; ++t) s = s - W.dot[t] * P[i + (long)t * ld];
+      p[i] = s;
+    }
+    T.sync();
+  }
+  if (T.tid == 0) {
+    double n2 = 0;
+    for (int i = 0; i < len; ++i) n2 += abs2(p[i]);
+    W.nrm = sqrt(n2);
+  }
+  T.sync();
+  const double nrm = W.nrm;
+  if (nrm > 0)
+    for (int i = T.tid; i < len; i += T.nt) p[i] = (1.0 / nrm) * p[i];
+  T.sync();
+  return nrm;
+}
+
+// Deflated restart of flexible GMRES-DR (Sec. II-C; Morgan's GMRES-DR with flexible
+// preconditioning).
 // In:  Hbar (m+1) x m (ld = ldh), c (m+1), y (m): the cycle's least-squares solution.
 // Out: P (m+1) x (k+1), ld = ldh: orthonormal basis of the k harmonic Ritz vectors of
 //      smallest |theta| (padded with a zero row) followed by the least-squares residual
 //      vector c - Hbar y; Hn = P^H Hbar P_k ((k+1) x k, ld = ldh); cn = P^H (c - Hbar y);
-//      theta[0:m] harmonic Ritz values sorted by |theta|.
-// Returns 0 on success, nonzero if a step failed (the caller then restarts plainly).
-DD_HD inline int deflate(const zd* Hbar, int ldh, int m, int k, const zd* c, const zd* y, zd* P, zd* Hn, zd* cn,
-                         zd* theta, DeflateWork& W) {
+//      theta[0:m] harmonic Ritz values sorted by |theta| (stable).
+// The harmonic Ritz pairs solve (H_m + |h_{m+1,m}|^2 f e_m^H) g = theta g with
+// f = H_m^{-H} e_m.  Eigenvalues come from the QR iteration, each kept vector from two
+// steps of inverse iteration on the original matrix shifted by its eigenvalue.
+// Returns 0 on success, nonzero if a step failed (the caller then restarts plainly); all
+// members of the team return the same value.
+DD_HD inline int deflate(const Team& T, const zd* Hbar, int ldh, int m, int k, const zd* c, const zd* y, zd* P, zd* Hn,
+                         zd* cn, zd* theta, DeflateWork& W) {
   const int ld = DD_MAXM;
-  // f = H_m^{-H} e_m
+  // f = H_m^{-H} e_m with the Hessenberg LU of H_m
+  for (int q = T.tid; q < m * m; q += T.nt) W.M[q % m + (q / m) * ld] = Hbar[q % m + (long)(q / m) * ldh];
+  for (int i = T.tid; i < m; i += T.nt) W.f[i] = Z(i == m - 1 ? 1.0 : 0.0);
+  T.sync();
+  double hn2 = 0;   // max |H_ij|^2 over the Hessenberg pattern
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i <= j + 1 && i < m; ++i) hn2 = fmax(hn2, abs2(Hbar[i + (long)j * ldh]));
+  const double hn = sqrt(hn2);
+  if (!(hn > 0) || !isfinite(hn)) return 1;
+  hess_lu(T, W.M, m, ld, W.piv, W.l, 0.0);
   for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j) W.M[i + j * ld] = conj(Hbar[j + (long)i * ldh]);
-  for (int i = 0; i < m; ++i) W.f[i] = Z(0.0);
-  W.f[m - 1] = Z(1.0);
-  if (!dense_solve(W.M, m, ld, W.f)) return 1;
-  // G = H_m + |h_{m+1,m}|^2 f e_m^H
-  double h2 = abs2(Hbar[m + (long)(m - 1) * ldh]);
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j) W.G[i + j * ld] = Hbar[i + (long)j * ldh];
-  for (int i = 0; i < m; ++i) W.G[i + (m - 1) * ld] = W.G[i + (m - 1) * ld] + h2 * W.f[i];
-  if (schur(W.G, W.Q, m, ld) < 0) return 2;
-  // order by |theta| (stable insertion sort)
-  for (int i = 0; i < m; ++i) { W.absth[i] = zabs(W.G[i + i * ld]); W.order[i] = i; }
-  for (int i = 1; i < m; ++i) {
-    int o = W.order[i];
-    int j = i - 1;
-    while (j >= 0 && W.absth[W.order[j]] > W.absth[o]) { W.order[j + 1] = W.order[j]; --j; }
-    W.order[j + 1] = o;
+    if (abs2(W.M[i + i * ld]) == 0.0) return 1;
+  hess_solve_adjoint(T, W.M, m, ld, W.piv, W.l, W.f);
+  // G = H_m + |h_{m+1,m}|^2 f e_m^H (still upper Hessenberg: only the last column changes)
+  const double h2 = abs2(Hbar[m + (long)(m - 1) * ldh]);
+  for (int q = T.tid; q < m * m; q += T.nt) {
+    const int i = q % m, j = q / m;
+    zd g = i <= j + 1 ? Hbar[i + (long)j * ldh] : Z(0.0);
+    if (j == m - 1) g = g + h2 * W.f[i];
+    W.G[i + j * ld] = g;
+    W.G0[i + j * ld] = g;
   }
-  for (int i = 0; i < m; ++i) theta[i] = W.G[W.order[i] + W.order[i] * ld];
-  // columns of P: harmonic Ritz vectors (zero last row), orthonormalised twice
+  T.sync();
+  if (hess_eigenvalues(T, W.G, m, ld) < 0) return 2;
+  // order by |theta| (stable insertion sort)
+  if (T.tid == 0) {
+    for (int i = 0; i < m; ++i) { W.absth[i] = zabs(W.G[i + i * ld]); W.order[i] = i; }
+    for (int i = 1; i < m; ++i) {
+      int o = W.order[i];
+      int j = i - 1;
+      while (j >= 0 && W.absth[W.order[j]] > W.absth[o]) { W.order[j + 1] = W.order[j]; --j; }
+      W.order[j + 1] = o;
+    }
+    for (int i = 0; i < m; ++i) theta[i] = W.G[W.order[i] + W.order[i] * ld];
+  }
+  T.sync();
+  // columns of P: eigenvectors of G0 for the k smallest |theta| (zero last row)
+  const double tiny = 1e-15 * hn;
   for (int l = 0; l < k; ++l) {
-    schur_eigvec(W.G, W.Q, m, ld, W.order[l], W.y, W.v);
-    zd* p = P + (long)l * ldh;
-    for (int i = 0; i < m; ++i) p[i] = W.v[i];
-    p[m] = Z(0.0);
-    for (int pass = 0; pass < 2; ++pass)
-      for (int t = 0; t < l; ++t) {
-        const zd* pt = P + (long)t * ldh;
-        zd d = Z(0.0);
-        for (int i = 0; i <= m; ++i) d = d + conj(pt[i]) * p[i];
-        for (int i = 0; i <= m; ++i) p[i] = p[i] - d * pt[i];
+    const zd th = theta[l];
+    for (int q = T.tid; q < m * m; q += T.nt) {
+      const int i = q % m, j = q / m;
+      W.M[i + j * ld] = i == j ? W.G0[i + j * ld] - th : W.G0[i + j * ld];
+    }
+    for (int i = T.tid; i < m; i += T.nt) W.v[i] = Z(1.0);
+    T.sync();
+    hess_lu(T, W.M, m, ld, W.piv, W.l, tiny);
+    for (int it = 0; it < 2; ++it) {
+      if (it == 0) upper_solve(T, W.M, m, ld, W.v);      // U v = (1, ..., 1)
+      else hess_solve(T, W.M, m, ld, W.piv, W.l, W.v);   // (G0 - theta) v = v
+      if (T.tid == 0) {
+        double n2 = 0;
+        for (int i = 0; i < m; ++i) n2 += abs2(W.v[i]);
+        W.nrm = sqrt(n2);
       }
-    double nrm = 0;
-    for (int i = 0; i <= m; ++i) nrm += abs2(p[i]);
-    nrm = sqrt(nrm);
-    if (!(nrm > 1e-12)) return 3;
-    for (int i = 0; i <= m; ++i) p[i] = (1.0 / nrm) * p[i];
+      T.sync();
+      const double nrm = W.nrm;
+      if (!(nrm > 0) || !isfinite(nrm)) return 3;
+      for (int i = T.tid; i < m; i += T.nt) W.v[i] = (1.0 / nrm) * W.v[i];
+      T.sync();
+    }
+    zd* p = P + (long)l * ldh;
+    for (int i = T.tid; i <= m; i += T.nt) p[i] = i < m ? W.v[i] : Z(0.0);
+    T.sync();
+    if (!(orthonormalise(T, P, ldh, l, m + 1, p, W) > 1e-12)) return 3;
   }
   // last column: least-squares residual c - Hbar y
-  for (int i = 0; i <= m; ++i) {
+  for (int i = T.tid; i <= m; i += T.nt) {
     zd s = c[i];
     for (int j = 0; j < m; ++j) s = s - Hbar[i + (long)j * ldh] * y[j];
     W.cls[i] = s;
+    P[i + (long)k * ldh] = s;
   }
-  zd* p = P + (long)k * ldh;
-  for (int i = 0; i <= m; ++i) p[i] = W.cls[i];
-  for (int pass = 0; pass < 2; ++pass)
-    for (int t = 0; t < k; ++t) {
-      const zd* pt = P + (long)t * ldh;
-      zd d = Z(0.0);
-      for (int i = 0; i <= m; ++i) d = d + conj(pt[i]) * p[i];
-      for (int i = 0; i <= m; ++i) p[i] = p[i] - d * pt[i];
-    }
-  double nrm = 0;
-  for (int i = 0; i <= m; ++i) nrm += abs2(p[i]);
-  nrm = sqrt(nrm);
-  if (!(nrm > 0)) return 4;
-  for (int i = 0; i <= m; ++i) p[i] = (1.0 / nrm) * p[i];
+  T.sync();
+  if (!(orthonormalise(T, P, ldh, k, m + 1, P + (long)k * ldh, W) > 0)) return 4;
   // Hn = P^H Hbar P_k, cn = P^H cls
-  for (int a = 0; a <= k; ++a) {
+  for (int q = T.tid; q < (k + 1) * (k + 1); q += T.nt) {
+    const int a = q % (k + 1), b = q / (k + 1);
     const zd* pa = P + (long)a * ldh;
-    for (int b = 0; b < k; ++b) {
+    if (b < k) {
       const zd* pb = P + (long)b * ldh;
       zd s = Z(0.0);
       for (int j = 0; j < m; ++j) {
@@ -301,11 +377,13 @@ DD_HD inline int deflate(const zd* Hbar, int ldh, int m, int k, const zd* c, con
         s = s + hp * pb[j];
       }
       Hn[a + (long)b * ldh] = s;
+    } else {
+      zd s = Z(0.0);
+      for (int i = 0; i <= m; ++i) s = s + conj(pa[i]) * W.cls[i];
+      cn[a] = s;
     }
-    zd s = Z(0.0);
-    for (int i = 0; i <= m; ++i) s = s + conj(pa[i]) * W.cls[i];
-    cn[a] = s;
   }
+  T.sync();
   return 0;
 }
 

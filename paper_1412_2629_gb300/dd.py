@@ -32,6 +32,10 @@ class dd_solve_params(C.Structure):
                 ("sap", dd_sap_params)]
 
 
+class dd_bicgstab_params(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double)]
+
+
 class dd_solve_info(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("restarts", C.c_int),
                 ("reliable_updates", C.c_int), ("deflated_restarts", C.c_int),
@@ -73,6 +77,7 @@ def lib():
             "dd_sap_precondition_lattices": (I, [C.POINTER(P), C.POINTER(P), C.POINTER(P), I,
                                                  C.POINTER(dd_sap_params)]),
             "dd_solve": (I, [P, P, P, I, I, C.POINTER(dd_solve_params), C.POINTER(dd_solve_info)]),
+            "dd_solve_bicgstab": (I, [P, P, P, I, C.POINTER(dd_bicgstab_params), C.POINTER(dd_solve_info)]),
             "dd_spinor_bytes": (C.c_size_t, [P, I, I]),
             "dd_pack_spinor": (I, [P, P, I, P, I]),
             "dd_unpack_spinor": (I, [P, P, I, P, I]),
@@ -166,6 +171,15 @@ class Context:
         p = dd_solve_params(tol, m, k, max_iter, dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site))
         info = dd_solve_info()
         s = lib().dd_solve(self._h, _ptr(f), _ptr(x), nrhs, where, C.byref(p), C.byref(info))
+        if check:
+            self._check(s)
+        return info
+
+    def dd_solve_bicgstab(self, f, x, where=DD_HOST, tol=1e-10, max_iter=10000, precision=DD_PREC_FP64,
+                          inner_tol=1e-5, check=True):
+        p = dd_bicgstab_params(tol, max_iter, precision, inner_tol)
+        info = dd_solve_info()
+        s = lib().dd_solve_bicgstab(self._h, _ptr(f), _ptr(x), where, C.byref(p), C.byref(info))
         if check:
             self._check(s)
         return info
