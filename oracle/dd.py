@@ -18,6 +18,8 @@ Readings of the paper taken here:
   * The multiplicative method is block Gauss-Seidel:
         u_c <- u_c + D_c^{-1} (f - A u)_c,  c = black, then white, u^0 = 0,
     with D_c^{-1} replaced by the even-odd MR approximation.
+  * The additive method (Sec. II-D, Eq. 4) is block Jacobi: every domain solves with the
+    residual of the same iterate, u <- u + D^{-1} (f - A u), u^0 = 0.
 """
 from __future__ import annotations
 
@@ -188,4 +190,16 @@ def sap(U, F, f, kappa, csw, dom: Domains, i_schwarz: int, i_domain: int, solver
         for colour in (0, 1):
             r = f - W.apply_A(U, u, kappa, csw, F)
             u = u + solver.solve(r, colour, i_domain)
+    return u
+
+
+def sap_additive(U, F, f, kappa, csw, dom: Domains, i_schwarz: int, i_domain: int, solver=None):
+    """Additive Schwarz preconditioner (Sec. II-D, Eq. 4; block Jacobi): for s = 1..I_Schwarz,
+    u <- u + D^{-1} (f - A u) with both colours solving from the same residual.  u^0 = 0."""
+    if solver is None:
+        solver = BlockSolver(U, F, kappa, csw, dom)
+    u = np.zeros_like(f)
+    for _ in range(i_schwarz):
+        r = f - W.apply_A(U, u, kappa, csw, F)
+        u = u + solver.solve(r, 0, i_domain) + solver.solve(r, 1, i_domain)
     return u

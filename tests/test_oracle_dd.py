@@ -137,6 +137,32 @@ def test_sap_equals_dense_block_gauss_seidel(small):
     assert np.linalg.norm(got.ravel() - u) <= 1e-12 * np.linalg.norm(u)
 
 
+def test_additive_sap_equals_dense_block_jacobi(small):
+    """The additive form with exact domain solves is block Jacobi on the dense A: every
+    domain solves with the residual of the same iterate (Sec. II-D, Eq. 4)."""
+    U, F, f = small
+    dom = DD.Domains(DIMS, B2)
+    A = DN.assemble_A(U, 0.13, 1.2).toarray()
+    sitedom = np.repeat(dom.domain.ravel(), 12)
+    fv = f.ravel()
+    u = np.zeros_like(fv)
+    for _ in range(3):
+        r = fv - A @ u
+        du = np.zeros_like(u)
+        for d in np.unique(sitedom):
+            idx = np.nonzero(sitedom == d)[0]
+            du[idx] = np.linalg.solve(A[np.ix_(idx, idx)], r[idx])
+        u = u + du
+    ex = DD.ExactBlockSolver(U, F, 0.13, 1.2, dom)
+    got = DD.sap_additive(U, F, f, 0.13, 1.2, dom, 3, None, solver=ex)
+    assert np.linalg.norm(got.ravel() - u) <= 1e-12 * np.linalg.norm(u)
+    # one sweep of either form is the same block solve of f
+    mult = DD.sap(U, F, f, 0.13, 1.2, dom, 1, None, solver=ex)
+    add1 = DD.sap_additive(U, F, f, 0.13, 1.2, dom, 1, None, solver=ex)
+    black = dom.colour == 0
+    assert np.allclose(mult[black], add1[black], rtol=0, atol=1e-14)
+
+
 def test_sap_converges_to_solution_small_kappa(small):
     U, F, f = small
     dom = DD.Domains(DIMS, B2)
