@@ -483,8 +483,9 @@ def kernel_case(args, local):
 
 def lattices_case(args):
     """The uneven batch of the fifth workload: 16^3x32, 24^3x48 and 32^3x64 (kappa 0.134,
-    0.135, 0.1355, c_sw 1.5, 4^4 domains), one Schwarz application each, timed as one
-    launch per half-sweep over all three lattices and as three separate calls."""
+    0.135, 0.1355, c_sw 1.5, 4^4 domains) with --nrhs Gaussian sources each (the workload
+    states 8), one Schwarz application of every source, timed as one launch per half-sweep
+    over all three lattices and as three separate batched calls."""
     import torch
 
     import synth
@@ -502,13 +503,16 @@ def lattices_case(args):
         c.dd_build_clover(kappa, 1.5)
         del U
         nb = c.dd_spinor_bytes(dd.DD_PREC_FP32, dd.DD_LAYOUT_INTERNAL)
-        a = torch.empty(nb, dtype=torch.uint8, device="cuda")
-        c.dd_pack_spinor(torch.view_as_real(torch.from_numpy(f)).float().cuda().contiguous(), dd.DD_PREC_FP32, a,
-                         dd.DD_PREC_FP32)
+        nr = args.nrhs
+        a = torch.empty(nr * nb, dtype=torch.uint8, device="cuda")
+        for r in range(nr):
+            fr = f if r == 0 else synth.gaussian_source(dims, seed + 10 + r)
+            c.dd_pack_spinor(torch.view_as_real(torch.from_numpy(fr)).float().cuda().contiguous(), dd.DD_PREC_FP32,
+                             a[r * nb:(r + 1) * nb], dd.DD_PREC_FP32)
         ctxs.append(c); ins.append(a); outs.append(torch.empty_like(a)); vols.append(int(np.prod(dims)))
-    i_s, i_d = base.i_schwarz, base.i_domain
-    one = lambda: dd.dd_sap_precondition_lattices(ctxs, ins, outs, i_s, i_d)
-    sep = lambda: [c.dd_sap_precondition(a, o, i_s, i_d, dd.DD_PREC_FP16, dd.DD_LAYOUT_INTERNAL)
+    i_s, i_d, nr = base.i_schwarz, base.i_domain, args.nrhs
+    one = lambda: dd.dd_sap_precondition_lattices(ctxs, ins, outs, i_s, i_d, nrhs=nr)
+    sep = lambda: [c.dd_sap_precondition_batch(a, o, nr, i_s, i_d, dd.DD_PREC_FP16)
                    for c, a, o in zip(ctxs, ins, outs)]
     res = {}
     for name, fn in (("one_launch", one), ("separate", sep)):
@@ -523,8 +527,9 @@ def lattices_case(args):
         torch.cuda.synchronize()
         res[name + "_ms"] = e0.elapsed_time(e1) / args.steps
     useful, _ = sap_visit_flops((4, 4, 4, 4), i_d)
-    res["tflops_one_launch"] = useful * sum(vols) * i_s / (res["one_launch_ms"] / 1e3) / 1e12
+    res["tflops_one_launch"] = useful * sum(vols) * i_s * nr / (res["one_launch_ms"] / 1e3) / 1e12
     res["case"] = "sap_lattices 16^3x32 + 24^3x48 + 32^3x64"
+    res["nrhs_per_lattice"] = nr
     print(json.dumps(res))
 
 

@@ -72,6 +72,12 @@ typedef struct {
                            single-precision arithmetic); needs threads_per_site 0 or 2;
                          DD_PREC_FP32: everything FP32 */
   int threads_per_site; /* 1 or 2 GPU threads per lattice site in the domain solve; 0 = default (2) */
+  int additive;       /* 0: multiplicative Schwarz (block Gauss-Seidel over the two colours, the
+                         paper's choice, Table I); 1: additive Schwarz (block Jacobi, Sec. II-D,
+                         Eq. 4): every domain of both colours solves with the residual of the same
+                         iterate, one launch per sweep; needs threads_per_site 0 or 2, and is not
+                         available in dd_sap_precondition_lattices or
+                         dd_sap_precondition_noalloc (DD_ERR_INVALID) */
 } dd_sap_params;
 
 /* Outer solver parameters (flexible GMRES with deflated restarts, Table I). */
@@ -135,11 +141,15 @@ dd_status dd_sap_precondition(dd_ctx* ctx, const float* in, float* out, const dd
  * fields, two right-hand sides per thread, so each link and clover block is loaded once
  * per pair. */
 dd_status dd_sap_precondition_batch(dd_ctx* ctx, const float* in, float* out, int nrhs, const dd_sap_params* p);
-/* Lattices of different volume in one launch per half-sweep: out_l = M_l in_l for the
- * nlat <= 4 contexts ctxs[l] (their own gauge fields, clover and kappa), all with the same
- * domain volume, FP16 storage and two threads per site.  in[l] / out[l]: FP32 internal
- * fields of lattice l.  Work is issued on ctxs[0]'s stream. */
-dd_status dd_sap_precondition_lattices(dd_ctx** ctxs, const float* const* in, float* const* out, int nlat,
+/* Lattices of different volume in one launch per half-sweep (Sec. IV-C: the many
+ * independent solves of an analysis): out_{l,r} = M_l in_{l,r} for the nlat <= 4 contexts
+ * ctxs[l] (their own gauge fields, clover and kappa) and nrhs right-hand sides each, all
+ * with the same domain volume, FP16 storage and two threads per site.  The launch walks a
+ * work list of (lattice, domain) and every CTA loops over the nrhs right-hand sides with
+ * its domain's links and Schwarz matrices staged once.  in[l] / out[l]: nrhs FP32
+ * internal fields of lattice l one after another (stride dd_spinor_bytes(ctxs[l],
+ * DD_PREC_FP32, DD_LAYOUT_INTERNAL)).  Work is issued on ctxs[0]'s stream. */
+dd_status dd_sap_precondition_lattices(dd_ctx** ctxs, const float* const* in, float* const* out, int nlat, int nrhs,
                                        const dd_sap_params* p);
 dd_status dd_apply_D_batch(dd_ctx* ctx, const void* in, void* out, int nrhs, int prec);
 
@@ -239,7 +249,8 @@ double dd_load_model(long long n_domains_per_colour, int slots);
  * 2..6 x threads per site 1, 2 on those shapes; (3) I_Schwarz in {1, 2, 4, 8, 16}, then
  * I_domain again, at the best shape.  On entry, out->i_schwarz, out->i_domain and
  * out->threads_per_site > 0 fix that parameter (threads_per_site 2 is needed for
- * several right-hand sides in lockstep); storage_prec: DD_PREC_FP16, DD_PREC_FP16_H2 or
+ * several right-hand sides in lockstep), and out->additive (0 or 1) selects the Schwarz
+ * form that is tuned; storage_prec: DD_PREC_FP16, DD_PREC_FP16_H2 or
  * DD_PREC_FP32 (else DD_ERR_INVALID).  Writes the best shape to domain_out and its
  * parameters to out.  Temporary device memory (two FP64 fields here, one context per
  * candidate) is released before returning.  Returns the first candidate error other than

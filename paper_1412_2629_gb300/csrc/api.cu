@@ -34,13 +34,14 @@ struct SapBuffers {
   void* u_store = nullptr;
   float* u_norm = nullptr;
   float4* faces = nullptr;
+  float4* faces2 = nullptr;    // second face buffer of the additive form (allocated on first use)
   int cap = 0;                 // right-hand sides the buffers hold
   long long r_bytes = 0, u_bytes = 0;
 };
 
 // A launch sequence of the outer solver captured as a CUDA graph: key = (part, step j,
-// I_Schwarz, I_domain, storage precision, threads per site, m).
-typedef std::array<int, 7> GraphKey;
+// I_Schwarz, I_domain, storage precision, threads per site, m, additive).
+typedef std::array<int, 8> GraphKey;
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   long long kernels = 0;     // kernels per replay
@@ -72,7 +73,7 @@ struct SolverBuffers {
   double* nu2 = nullptr;               // squared norm of the projected vector
   // deflated restart on the device: workspace and flags ([0] deflation status, [1] the
   // recombination gate: deflation succeeded and the residual is above target)
-  DeflateWork* dW = nullptr;
+  void* dW = nullptr;            // deflate_bytes(m) of global scratch (when shared memory is too small)
   int* dflags = nullptr;
 };
 
@@ -380,7 +381,9 @@ static dd_status ensure_sap(dd_ctx* c, int prec, int nrhs = 1) {
   if (b.faces) {
     cudaStreamSynchronize(c->st);
     drop_graphs(c);
-    for (void* q : {(void*)b.r_store, (void*)b.r_norm, (void*)b.u_store, (void*)b.u_norm, (void*)b.faces}) release(c, q);
+    for (void* q : {(void*)b.r_store, (void*)b.r_norm, (void*)b.u_store, (void*)b.u_norm, (void*)b.faces,
+                    (void*)b.faces2})
+      release(c, q);
     b = SapBuffers();
   }
   const Geom& g = c->g;
@@ -429,10 +432,23 @@ static SapState sap_state(dd_ctx* c, int prec, const dd_sap_params* p, int nrhs)
   return S;
 }
 
-static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_params* p, int nrhs = 1) {
-  int prec = sap_prec(p->storage_prec);
-  TRY(ensure_sap(c, prec, nrhs));
-  SapState S = sap_state(c, prec, p, nrhs);
+// The launches of one Schwarz application on state S.  Multiplicative: I_Schwarz x (black,
+// white) half-sweeps on one face buffer.  Additive: I_Schwarz launches over both colours,
+// sweep s reading the faces of sweep s - 1 from one buffer and writing its own to the other.
+static dd_status sap_sweeps(dd_ctx* c, SapState& S, const dd_sap_params* p, const float4* v, float4* z,
+                            float4* faces2) {
+  if (p->additive) {
+    float4* fb[2] = {S.faces, faces2};
+    S.both_colours = true;
+    for (int s = 0; s < p->i_schwarz; ++s) {
+      S.faces = fb[(s + 1) & 1];
+      S.faces_out = fb[s & 1];
+      if (sap_half_sweep(c->g, S, 0, s == 0, s > 0, s == p->i_schwarz - 1, v, z, p->i_domain, c->st))
+        return fail(c, DD_ERR_CUDA, std::string("Schwarz launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+      TRY(launched(c));
+    }
+    return DD_OK;
+  }
   for (int s = 0; s < p->i_schwarz; ++s)
     for (int colour = 0; colour < 2; ++colour) {
       int first = s == 0, use_faces = !(s == 0 && colour == 0), last = s == p->i_schwarz - 1;
@@ -443,11 +459,28 @@ static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_par
   return DD_OK;
 }
 
+// The additive form's second face buffer, allocated on first use.
+static dd_status ensure_faces2(dd_ctx* c, int prec) {
+  SapBuffers& b = c->sap[prec];
+  if (!b.faces2) TRY(dalloc(c, &b.faces2, (size_t)b.cap * c->g.ND * c->g.face_block * 48));
+  return DD_OK;
+}
+
+static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_params* p, int nrhs = 1) {
+  int prec = sap_prec(p->storage_prec);
+  TRY(ensure_sap(c, prec, nrhs));
+  if (p->additive) TRY(ensure_faces2(c, prec));
+  SapState S = sap_state(c, prec, p, nrhs);
+  return sap_sweeps(c, S, p, v, z, c->sap[prec].faces2);
+}
+
 static dd_status check_sap_params(dd_ctx* c, const dd_sap_params* p) {
   if (!p || p->i_schwarz < 1 || p->i_domain < 0 ||
       (p->storage_prec != DD_PREC_FP16 && p->storage_prec != DD_PREC_FP32 && p->storage_prec != DD_PREC_FP16_H2) ||
-      p->threads_per_site < 0 || p->threads_per_site > 2)
+      p->threads_per_site < 0 || p->threads_per_site > 2 || p->additive < 0 || p->additive > 1)
     return fail(c, DD_ERR_INVALID, "bad Schwarz parameters");
+  if (p->additive && p->threads_per_site == 1)
+    return fail(c, DD_ERR_INVALID, "the additive form needs two threads per site");
   if (p->storage_prec == DD_PREC_FP16_H2 && p->threads_per_site == 1)
     return fail(c, DD_ERR_INVALID, "packed FP16 arithmetic needs two threads per site");
   return DD_OK;
@@ -495,13 +528,14 @@ extern "C" dd_status dd_sap_precondition_batch(dd_ctx* c, const float* in, float
 }
 
 extern "C" dd_status dd_sap_precondition_lattices(dd_ctx** ctxs, const float* const* in, float* const* out, int nlat,
-                                                  const dd_sap_params* p) {
-  if (!ctxs || !in || !out || nlat < 1 || nlat > 4) return DD_ERR_INVALID;
+                                                  int nrhs, const dd_sap_params* p) {
+  if (!ctxs || !in || !out || nlat < 1 || nlat > 4 || nrhs < 1) return DD_ERR_INVALID;
   dd_ctx* c0 = ctxs[0];
   if (!c0) return DD_ERR_INVALID;
   TRY(check_sap_params(c0, p));
-  if (p->storage_prec != DD_PREC_FP16 || p->threads_per_site == 1 || p->i_domain < 1)
-    return fail(c0, DD_ERR_INVALID, "lattice batches need FP16 storage, two threads per site and i_domain >= 1");
+  if (p->storage_prec != DD_PREC_FP16 || p->threads_per_site == 1 || p->i_domain < 1 || p->additive)
+    return fail(c0, DD_ERR_INVALID,
+                "lattice batches need FP16 storage, two threads per site, i_domain >= 1 and the multiplicative form");
   Geom gs[4];
   SapState Ss[4];
   for (int l = 0; l < nlat; ++l) {
@@ -510,9 +544,9 @@ extern "C" dd_status dd_sap_precondition_lattices(dd_ctx** ctxs, const float* co
     if (!c->have_clover) return fail(c0, DD_ERR_NO_CLOVER, "clover not built on lattice " + std::to_string(l));
     if (c->g.Vd != c0->g.Vd || c->g.Hd != c0->g.Hd)
       return fail(c0, DD_ERR_DIMS, "lattices of one launch need the same domain volume");
-    TRY(ensure_sap(c, P16, 1));
+    TRY(ensure_sap(c, P16, nrhs));
     gs[l] = c->g;
-    Ss[l] = sap_state(c, P16, p, 1);
+    Ss[l] = sap_state(c, P16, p, nrhs);
     if (Ss[l].mat_in_smem != Ss[0].mat_in_smem) return fail(c0, DD_ERR_DIMS, "mixed domain shapes");
   }
   for (int l = 0; l < nlat; ++l) cudaStreamSynchronize(ctxs[l]->st);   // inputs written on the lattices' streams
@@ -592,11 +626,28 @@ __global__ void plain_restart_kernel(zd* H, zd* R, int ldh, int m, const double2
 }
 
 // The deflated restart's small dense step (harmonic Ritz pairs, P, Hn, cn) by one warp.
+// Its workspace sits in shared memory when deflate_bytes(mm) fits (in_smem), else in the
+// global scratch.
 __global__ void deflate_kernel(const zd* H, int ldh, int mm, int k, const zd* c0, const zd* y, zd* P, zd* Hn, zd* cn,
-                               zd* theta, DeflateWork* W, int* flags) {
+                               zd* theta, void* gscratch, int in_smem, int* flags) {
+  extern __shared__ __align__(16) unsigned char deflate_smem[];
+  DeflateWork W = deflate_work(in_smem ? (void*)deflate_smem : gscratch, mm);
   const Team T{(int)threadIdx.x, (int)blockDim.x};
-  const int rc = deflate(T, H, ldh, mm, k, c0, y, P, Hn, cn, theta, *W);
+  const int rc = deflate(T, H, ldh, mm, k, c0, y, P, Hn, cn, theta, W);
   if (threadIdx.x == 0) flags[0] = rc;
+}
+
+static void launch_deflate(const zd* H, int ldh, int mm, int k, const zd* c0, const zd* y, zd* P, zd* Hn, zd* cn,
+                           zd* theta, void* gscratch, int* flags, cudaStream_t st) {
+  constexpr size_t smem_cap = 200 * 1024;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(deflate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
+    configured = true;
+  }
+  const size_t b = deflate_bytes(mm);
+  const int in_smem = b <= smem_cap;
+  deflate_kernel<<<1, 32, in_smem ? b : 0, st>>>(H, ldh, mm, k, c0, y, P, Hn, cn, theta, gscratch, in_smem, flags);
 }
 
 // flags[1] = 1 when the basis is to be recombined: a deflation was computed and succeeded,
@@ -697,7 +748,7 @@ static dd_status alloc_solver_buffers(dd_ctx* c, SolverBuffers& s, int m, bool s
   TRY(dalloc(c, &s.lsq, sizeof(LsqState)));
   TRY(dalloc(c, &s.flag, 16));
   TRY(dalloc(c, &s.nu2, 16));
-  TRY(dalloc(c, &s.dW, sizeof(DeflateWork)));
+  TRY(dalloc(c, &s.dW, deflate_bytes(m)));
   TRY(dalloc(c, &s.dflags, 16 * sizeof(int)));
   if (cudaMallocHost(&s.h_status, 8 * sizeof(double)) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned status");
   if (streams && (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -804,7 +855,7 @@ static dd_status end_cycle(dd_ctx* c, SolverBuffers& s, int mm, const dd_solve_p
       cudaStreamWaitEvent(s.side, s.ev_fork, 0);
       ds = s.side;
     }
-    deflate_kernel<<<1, 32, 0, ds>>>(s.H, ldh, mm, k, s.c0, s.y, s.P, s.Hn, s.cn, s.theta, s.dW, s.dflags);
+    launch_deflate(s.H, ldh, mm, k, s.c0, s.y, s.P, s.Hn, s.cn, s.theta, s.dW, s.dflags, ds);
     nk++;
     if (ds != c->st) cudaEventRecord(s.ev_join, ds);
   }
@@ -881,7 +932,7 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
       // one Arnoldi step = three device-only launch sequences, each replayed from a CUDA
       // graph once it has been captured (keyed by step and parameters)
       const GraphKey kbase = {0, j, p->sap.i_schwarz, p->sap.i_domain, p->sap.storage_prec,
-                              p->sap.threads_per_site, m};
+                              p->sap.threads_per_site, m, p->sap.additive};
       GraphKey k0 = kbase, k1 = kbase, k2 = kbase;
       k1[0] = 1;
       k2[0] = 2;
@@ -1035,17 +1086,11 @@ static dd_status ensure_lock(dd_ctx* c, int nrhs, int m) {
 static dd_status sap_run_list(dd_ctx* c, const float4* const* vl, float4* const* zl, const dd_sap_params* p, int na) {
   int prec = sap_prec(p->storage_prec);
   TRY(ensure_sap(c, prec, na));
+  if (p->additive) TRY(ensure_faces2(c, prec));
   SapState S = sap_state(c, prec, p, na);
   S.vlist = vl;
   S.zlist = zl;
-  for (int s = 0; s < p->i_schwarz; ++s)
-    for (int colour = 0; colour < 2; ++colour) {
-      int first = s == 0, use_faces = !(s == 0 && colour == 0), last = s == p->i_schwarz - 1;
-      if (sap_half_sweep(c->g, S, colour, first, use_faces, last, nullptr, nullptr, p->i_domain, c->st))
-        return fail(c, DD_ERR_CUDA, std::string("Schwarz launch failed: ") + cudaGetErrorString(cudaGetLastError()));
-      TRY(launched(c));
-    }
-  return DD_OK;
+  return sap_sweeps(c, S, p, nullptr, nullptr, c->sap[prec].faces2);
 }
 
 // Gram-Schmidt of step j and the Hessenberg update for one right-hand side (the sequence
@@ -1552,11 +1597,11 @@ extern "C" dd_status dd_deflate_host(int m, int k, const double* Hbar, const dou
                                      double* P, double* Hn, double* cn, double* theta) {
   if (m < 1 || m >= DD_MAXM || k < 1 || k >= m || !Hbar || !cvec || !yvec || !P || !Hn || !cn || !theta)
     return DD_ERR_INVALID;
-  DeflateWork* W = new DeflateWork();
+  std::vector<double2> buf(deflate_bytes(m) / sizeof(double2) + 1);
+  DeflateWork W = deflate_work(buf.data(), m);
   const Team T{0, 1};
   int rc = deflate(T, (const zd*)Hbar, m + 1, m, k, (const zd*)cvec, (const zd*)yvec, (zd*)P, (zd*)Hn, (zd*)cn,
-                   (zd*)theta, *W);
-  delete W;
+                   (zd*)theta, W);
   return rc == 0 ? DD_OK : DD_ERR_NONFINITE;
 }
 
@@ -1607,11 +1652,12 @@ extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4],
   if (storage_prec != DD_PREC_FP16 && storage_prec != DD_PREC_FP32 && storage_prec != DD_PREC_FP16_H2)
     return fail(c, DD_ERR_INVALID, "autotune: storage_prec must be DD_PREC_FP16, DD_PREC_FP16_H2 or DD_PREC_FP32");
   if (out->i_schwarz < 0 || out->i_domain < 0 || out->threads_per_site < 0 || out->threads_per_site > 2 ||
-      (storage_prec == DD_PREC_FP16_H2 && out->threads_per_site == 1))
+      (storage_prec == DD_PREC_FP16_H2 && out->threads_per_site == 1) || out->additive < 0 || out->additive > 1 ||
+      (out->additive && out->threads_per_site == 1))
     return fail(c, DD_ERR_INVALID, "autotune: bad fixed parameters");
   if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
   const int fix_is = out->i_schwarz, fix_id = out->i_domain;
-  const int fix_tps = storage_prec == DD_PREC_FP16_H2 ? 2 : out->threads_per_site;
+  const int fix_tps = (storage_prec == DD_PREC_FP16_H2 || out->additive) ? 2 : out->threads_per_site;
   const long long nreal = c->g.V * 24;
   double *f = nullptr, *x = nullptr;
   TRY(dalloc(c, &f, (size_t)nreal * 8));
@@ -1634,6 +1680,7 @@ extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4],
     sp.sap.i_domain = cd.i_domain;
     sp.sap.storage_prec = storage_prec;
     sp.sap.threads_per_site = cd.tps;
+    sp.sap.additive = out->additive;
     dd_status s = cuda_check(c, cudaMemsetAsync(x, 0, (size_t)nreal * 8, c->st), "autotune x");
     dd_solve_info info;
     memset(&info, 0, sizeof(info));
@@ -1768,6 +1815,7 @@ extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4],
 extern "C" dd_status dd_sap_precondition_noalloc(dd_ctx* c, const float* in, float* out, const dd_sap_params* p) {
   if (!c || !in || !out) return DD_ERR_INVALID;
   TRY(check_sap_params(c, p));
+  if (p->additive) return fail(c, DD_ERR_INVALID, "the allocation-free entry point runs the multiplicative form only");
   if (p->i_domain == 0) return fail(c, DD_ERR_INVALID, "i_domain must be >= 1");
   const Geom& g = c->g;
   int prec = sap_prec(p->storage_prec);

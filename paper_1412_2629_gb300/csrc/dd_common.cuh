@@ -118,6 +118,50 @@ __host__ __device__ inline int face_index(const Geom& g, const int l[4], int mu)
   return idx;
 }
 
+// Domain shapes the hot kernels are also compiled for (SHAPE 1: 8x4x4x4, 2: 4x4x4x4; 0:
+// shape read at run time).  With the shape known at compile time every local stride, site
+// count and buffer offset is a constant, so addresses fold into immediate offsets and
+// most index arithmetic disappears.
+template <int SHAPE> struct ShapeOf;
+template <> struct ShapeOf<1> {
+  __host__ __device__ static constexpr int b(int mu) { return mu == 0 ? 8 : 4; }
+  __host__ __device__ static constexpr int lg(int mu) { return mu == 0 ? 3 : 2; }
+};
+template <> struct ShapeOf<2> {
+  __host__ __device__ static constexpr int b(int) { return 4; }
+  __host__ __device__ static constexpr int lg(int) { return 2; }
+};
+
+inline int domain_shape_id(const Geom& g) {
+  if (g.b[0] == 8 && g.b[1] == 4 && g.b[2] == 4 && g.b[3] == 4) return 1;
+  if (g.b[0] == 4 && g.b[1] == 4 && g.b[2] == 4 && g.b[3] == 4) return 2;
+  return 0;
+}
+
+// The geometry with the domain fields replaced by compile-time constants (SHAPE != 0).
+template <int SHAPE>
+__device__ __forceinline__ Geom fixed_shape(const Geom& in) {
+  Geom g = in;
+  if constexpr (SHAPE != 0) {
+    using S = ShapeOf<SHAPE>;
+    constexpr int vd = S::b(0) * S::b(1) * S::b(2) * S::b(3);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      g.b[mu] = S::b(mu);
+      g.lgb[mu] = S::lg(mu);
+      g.face_n[mu] = vd / S::b(mu);
+    }
+    g.bstride[0] = 1;
+    g.bstride[1] = S::b(0);
+    g.bstride[2] = S::b(0) * S::b(1);
+    g.bstride[3] = S::b(0) * S::b(1) * S::b(2);
+    g.Vd = vd;
+    g.Hd = vd / 2;
+    g.lgVd = S::lg(0) + S::lg(1) + S::lg(2) + S::lg(3);
+  }
+  return g;
+}
+
 // ------------------------------------------------------------------ complex
 template <typename R> struct cx { R re, im; };
 

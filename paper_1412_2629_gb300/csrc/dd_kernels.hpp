@@ -71,6 +71,10 @@ struct SapState {
   float4* const* zlist = nullptr;
   long long r_bytes = 0;       // bytes of one right-hand side's residual / solution storage
   long long u_bytes = 0;
+  // additive form (block Jacobi): one launch per sweep over both colours, reading the
+  // faces of the previous sweep from `faces` and writing this sweep's to faces_out
+  bool both_colours = false;
+  float4* faces_out = nullptr;
 };
 // One half-sweep: all domains of `colour`.  first: the residual is the input v (both
 // parities) and u = 0; use_faces: subtract the couplings to the other colour from the

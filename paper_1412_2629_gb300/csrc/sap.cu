@@ -308,7 +308,9 @@ struct SapArgs {
   float* r_norm;
   void* u_store;
   float* u_norm;
-  float4* faces;
+  float4* faces;       // face buffers read by the couplings
+  float4* faces_out;   // face buffers written (== faces except in the additive form)
+  int both_colours;    // additive form: the grid covers the domains of both colours
   const float4* v;
   float4* z;
   const float4* const* vptr;   // if set: input / output of right-hand side r at vptr[r] / zptr[r]
@@ -985,50 +987,6 @@ __device__ inline void hops_half_mask(int h, const Geom& g, unsigned fwd, unsign
 // scaled by a power of two, 16 / 2^ceil(log2 max|r|), before it enters the work buffers,
 // and everything that leaves them (the new residual, delta) is scaled back.  The MR
 // iteration is invariant under that scaling and powers of two are exact in FP32.
-// Domain shapes the two-thread kernel is also compiled for (SHAPE 1: 8x4x4x4, 2: 4x4x4x4;
-// 0: shape read at run time).  With the shape known at compile time every local stride,
-// site count and work-buffer offset is a constant, so shared-memory addresses fold into
-// immediate offsets and the index arithmetic of the hop phases disappears.
-template <int SHAPE> struct ShapeOf;
-template <> struct ShapeOf<1> {
-  __host__ __device__ static constexpr int b(int mu) { return mu == 0 ? 8 : 4; }
-  __host__ __device__ static constexpr int lg(int mu) { return mu == 0 ? 3 : 2; }
-};
-template <> struct ShapeOf<2> {
-  __host__ __device__ static constexpr int b(int) { return 4; }
-  __host__ __device__ static constexpr int lg(int) { return 2; }
-};
-
-int sap_shape_id(const Geom& g) {
-  if (g.b[0] == 8 && g.b[1] == 4 && g.b[2] == 4 && g.b[3] == 4) return 1;
-  if (g.b[0] == 4 && g.b[1] == 4 && g.b[2] == 4 && g.b[3] == 4) return 2;
-  return 0;
-}
-
-// The geometry with the domain fields replaced by compile-time constants (SHAPE != 0).
-template <int SHAPE>
-__device__ __forceinline__ Geom fixed_shape(const Geom& in) {
-  Geom g = in;
-  if constexpr (SHAPE != 0) {
-    using S = ShapeOf<SHAPE>;
-    constexpr int vd = S::b(0) * S::b(1) * S::b(2) * S::b(3);
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      g.b[mu] = S::b(mu);
-      g.lgb[mu] = S::lg(mu);
-      g.face_n[mu] = vd / S::b(mu);
-    }
-    g.bstride[0] = 1;
-    g.bstride[1] = S::b(0);
-    g.bstride[2] = S::b(0) * S::b(1);
-    g.bstride[3] = S::b(0) * S::b(1) * S::b(2);
-    g.Vd = vd;
-    g.Hd = vd / 2;
-    g.lgVd = S::lg(0) + S::lg(1) + S::lg(2) + S::lg(3);
-  }
-  return g;
-}
-
 template <typename MT, typename VT, bool MSMEM, bool H2, int SHAPE = 0>
 __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   // hop phases use g (constant domain fields when SHAPE != 0); the face code, which indexes
@@ -1043,15 +1001,19 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   const int h = tid >= Hd;          // MR phases: chirality half and hop directions; ends: parity
   const int i = tid - h * Hd;
 
+  // this CTA's colour and its index among the domains of that colour (the additive form
+  // runs both colours in one launch, colour 0 first)
+  const int colour = a.both_colours ? (cta >= (g.ND >> 1)) : a.colour;
+  const int cidx = a.both_colours ? cta - colour * (g.ND >> 1) : cta;
   int n[4];
   {
     int hx = g.N[0] >> 1;
-    int j = cta % hx;
-    int row = cta / hx;
+    int j = cidx % hx;
+    int row = cidx / hx;
     n[1] = row % g.N[1];
     n[2] = (row / g.N[1]) % g.N[2];
     n[3] = row / (g.N[1] * g.N[2]);
-    n[0] = 2 * j + ((a.colour + n[1] + n[2] + n[3]) & 1);
+    n[0] = 2 * j + ((colour + n[1] + n[2] + n[3]) & 1);
   }
   const long long d = n[0] + (long long)g.dstride[1] * n[1] + (long long)g.dstride[2] * n[2] +
                       (long long)g.dstride[3] * n[3];
@@ -1106,6 +1068,7 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
 #pragma unroll 1
   for (int rhs = 0; rhs < a.nrhs; ++rhs) {
   float4* const fr = a.faces + rhs * a.f_stride;
+  float4* const fw = a.faces_out + rhs * a.f_stride;
   float* const rnr = a.r_norm ? a.r_norm + rhs * a.rn_stride : nullptr;
   float* const unr = a.u_norm ? a.u_norm + rhs * a.un_stride : nullptr;
   float inv_sc = 1.f;   // H2: undoes the domain's scaling on the way out
@@ -1295,9 +1258,10 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   } else {
     ust.store(g, s_site, u);
   }
-  if (!(a.last && a.colour == 1)) {
-    if (h) face_write_rt(a.g, d, lo, fs, bs, r_site, fr, M, dl);
-    else face_write_rt(a.g, d, le, fs, bs, r_site, fr, M, dl);
+  // faces for the next half-sweep (none after the very last one)
+  if (!(a.last && (a.both_colours || colour == 1))) {
+    if (h) face_write_rt(a.g, d, lo, fs, bs, r_site, fw, M, dl);
+    else face_write_rt(a.g, d, le, fs, bs, r_site, fw, M, dl);
   }
   __syncthreads();   // the work buffers are reused by the next right-hand side
   }
@@ -1370,7 +1334,7 @@ template <typename MT, typename VT, bool MSMEM, bool H2 = false>
 static int launch_one(const SapArgs& a, int grid, int pair, cudaStream_t st) {
   size_t smem = sap_smem_bytes(a.g, std::is_same<MT, __half>::value ? P16 : P32, MSMEM);
   if (pair) {
-    switch (sap_shape_id(a.g)) {
+    switch (domain_shape_id(a.g)) {
       case 1: launch_pair<MT, VT, MSMEM, H2, 1>(a, grid, smem, st); break;
       case 2: launch_pair<MT, VT, MSMEM, H2, 2>(a, grid, smem, st); break;
       default: launch_pair<MT, VT, MSMEM, H2, 0>(a, grid, smem, st); break;
@@ -1428,8 +1392,9 @@ int sap_half_sweep(const Geom& g, const SapState& S, int colour, int first, int 
   if (g.Hd > SAP_MAX_THREADS || (g.Hd & 31)) return -1;
   // only the pair kernel loops over right-hand sides and reads pointer lists
   if ((S.nrhs > 1 || S.vlist) && S.threads_per_site != 2) return -1;
+  if (S.both_colours && S.threads_per_site != 2) return -1;   // the additive form: pair kernel only
   SapArgs a = make_args(g, S, colour, first, use_faces, last, v, z, i_domain);
-  int grid = g.ND / 2;
+  int grid = S.both_colours ? g.ND : g.ND / 2;
   bool ms = S.mat_in_smem;
   int pr = S.threads_per_site == 2;
   // matrices and vectors are stored in the same precision (FP16 or FP32)
@@ -1460,6 +1425,8 @@ static SapArgs make_args(const Geom& g, const SapState& S, int colour, int first
   a.u_store = S.u_store;
   a.u_norm = S.u_norm;
   a.faces = S.faces;
+  a.faces_out = S.faces_out ? S.faces_out : S.faces;
+  a.both_colours = S.both_colours ? 1 : 0;
   a.v = v;
   a.z = z;
   a.vptr = S.vlist;

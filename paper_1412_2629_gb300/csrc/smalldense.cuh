@@ -227,21 +227,98 @@ DD_HD inline int hess_eigenvalues(const Team& T, zd* A, int n, int ld) {
   return total;
 }
 
-// Workspace of the deflated restart, sized for DD_MAXM.
+// Dense LU with partial pivoting of A (n x n, ld), applied to b on the way (A is
+// overwritten by U, b by U^{-1} L^{-1} P b); then b <- A^{-1} b by back substitution.
+// Returns false (all members alike) if a pivot is exactly zero.
+DD_HD inline bool dense_solve(const Team& T, zd* A, int n, int ld, zd* b) {
+  auto a = [&](int i, int j) -> zd& { return A[i + (long)j * ld]; };
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    double best = -1.0;
+    for (int r = c; r < n; ++r) {
+      const double v = abs2(a(r, c));
+      if (v > best) { best = v; p = r; }
+    }
+    if (best == 0.0) return false;
+    T.sync();   // every member has read column c
+    if (p != c) {
+      for (int j = c + T.tid; j < n; j += T.nt) { zd t = a(c, j); a(c, j) = a(p, j); a(p, j) = t; }
+      if (T.tid == 0) { zd t = b[c]; b[c] = b[p]; b[p] = t; }
+      T.sync();
+    }
+    for (int r = c + 1 + T.tid; r < n; r += T.nt) {
+      const zd f = zdiv(a(r, c), a(c, c));
+      for (int j = c + 1; j < n; ++j) a(r, j) = a(r, j) - f * a(c, j);
+      b[r] = b[r] - f * b[c];
+    }
+    T.sync();
+  }
+  upper_solve(T, A, n, ld, b);
+  return true;
+}
+
+// Reduction of A (n x n, ld) to upper Hessenberg form by plane rotations, A <- Q^H A Q,
+// with Q (ld) accumulated from the identity.  Only nonzero entries below the first
+// subdiagonal are rotated away (after a deflated restart that is the dense leading block).
+DD_HD inline void hessenberg(const Team& T, zd* A, zd* Q, int n, int ld) {
+  auto a = [&](int i, int j) -> zd& { return A[i + (long)j * ld]; };
+  auto q = [&](int i, int j) -> zd& { return Q[i + (long)j * ld]; };
+  for (int e = T.tid; e < n * n; e += T.nt) q(e % n, e / n) = Z(e % n == e / n ? 1.0 : 0.0);
+  T.sync();
+  for (int j = 0; j + 2 < n; ++j)
+    for (int i = n - 1; i >= j + 2; --i) {
+      if (abs2(a(i, j)) == 0.0) continue;   // same decision for every member
+      const Rot r = make_rot(a(i - 1, j), a(i, j));
+      T.sync();
+      for (int k = T.tid; k < n; k += T.nt) rot_apply(r, a(i - 1, k), a(i, k));
+      T.sync();
+      for (int k = T.tid; k < n; k += T.nt) {
+        rot_apply_right(r, a(k, i - 1), a(k, i));
+        rot_apply_right(r, q(k, i - 1), q(k, i));
+      }
+      T.sync();
+      if (T.tid == 0) a(i, j) = Z(0.0);
+      T.sync();
+    }
+}
+
+// Workspace of the deflated restart for basis size m: four m x m matrices (leading
+// dimension m) and short vectors, carved from one buffer of deflate_bytes(m) bytes
+// (host memory, device global memory or shared memory).
 struct DeflateWork {
-  zd G[DD_MAXM * DD_MAXM];    // H_m + |h|^2 f e_m^H, reduced by the QR iteration
-  zd G0[DD_MAXM * DD_MAXM];   // the same matrix, kept for the inverse iteration
-  zd M[DD_MAXM * DD_MAXM];    // LU factors
-  zd f[DD_MAXM + 1];
-  zd v[DD_MAXM + 1];
-  zd cls[DD_MAXM + 1];
-  zd l[DD_MAXM];
-  zd dot[DD_MAXM + 1];
-  double nrm;
-  int piv[DD_MAXM];
-  double absth[DD_MAXM];
-  int order[DD_MAXM];
+  zd *G, *G0, *M, *Q;
+  zd *f, *v, *w, *cls, *dot;
+  zd* l;
+  double *absth, *nrm;
+  int *order, *piv;
+  int ld;
 };
+DD_HD inline size_t deflate_bytes(int m) {
+  return (size_t)4 * m * m * sizeof(zd) + 6 * (size_t)(DD_MAXM + 1) * sizeof(zd) + (DD_MAXM + 1) * sizeof(double) * 2 +
+         2 * (size_t)(DD_MAXM + 1) * sizeof(int);
+}
+DD_HD inline DeflateWork deflate_work(void* base, int m) {
+  DeflateWork W;
+  zd* z = (zd*)base;
+  W.ld = m;
+  W.G = z; z += m * m;
+  W.G0 = z; z += m * m;
+  W.M = z; z += m * m;
+  W.Q = z; z += m * m;
+  W.f = z; z += DD_MAXM + 1;
+  W.v = z; z += DD_MAXM + 1;
+  W.w = z; z += DD_MAXM + 1;
+  W.cls = z; z += DD_MAXM + 1;
+  W.dot = z; z += DD_MAXM + 1;
+  W.l = z; z += DD_MAXM + 1;
+  double* d = (double*)z;
+  W.absth = d; d += DD_MAXM + 1;
+  W.nrm = d; d += DD_MAXM + 1;
+  int* i = (int*)d;
+  W.order = i; i += DD_MAXM + 1;
+  W.piv = i;
+  return W;
+}
 
 // p <- p - sum_t (p_t^H p) p_t over the first nprev columns of P (ld), twice, then p / |p|;
 // returns |p| before the final scaling.
@@ -264,10 +341,10 @@ DD_HD inline double orthonormalise(const Team& T, zd* P, int ld, int nprev, int 
   if (T.tid == 0) {
     double n2 = 0;
     for (int i = 0; i < len; ++i) n2 += abs2(p[i]);
-    W.nrm = sqrt(n2);
+    W.nrm[0] = sqrt(n2);
   }
   T.sync();
-  const double nrm = W.nrm;
+  const double nrm = W.nrm[0];
   if (nrm > 0)
     for (int i = T.tid; i < len; i += T.nt) p[i] = (1.0 / nrm) * p[i];
   T.sync();
@@ -277,40 +354,43 @@ DD_HD inline double orthonormalise(const Team& T, zd* P, int ld, int nprev, int 
 // Deflated restart of flexible GMRES-DR (Sec. II-C; Morgan's GMRES-DR with flexible
 // preconditioning).
 // In:  Hbar (m+1) x m (ld = ldh), c (m+1), y (m): the cycle's least-squares solution.
+//      After a deflated restart the leading (k+1) x k block of Hbar is dense; the rest is
+//      upper Hessenberg.
 // Out: P (m+1) x (k+1), ld = ldh: orthonormal basis of the k harmonic Ritz vectors of
 //      smallest |theta| (padded with a zero row) followed by the least-squares residual
 //      vector c - Hbar y; Hn = P^H Hbar P_k ((k+1) x k, ld = ldh); cn = P^H (c - Hbar y);
 //      theta[0:m] harmonic Ritz values sorted by |theta| (stable).
 // The harmonic Ritz pairs solve (H_m + |h_{m+1,m}|^2 f e_m^H) g = theta g with
-// f = H_m^{-H} e_m.  Eigenvalues come from the QR iteration, each kept vector from two
-// steps of inverse iteration on the original matrix shifted by its eigenvalue.
-// Returns 0 on success, nonzero if a step failed (the caller then restarts plainly); all
-// members of the team return the same value.
+// f = H_m^{-H} e_m.  That matrix is reduced to Hessenberg form (Q), its eigenvalues come
+// from the QR iteration, and each kept vector from two steps of inverse iteration on the
+// Hessenberg form shifted by its eigenvalue, mapped back by Q.  A vector that is not
+// independent of those already kept (a repeated eigenvalue) is passed over for the next
+// one in the order.  Returns 0 on success, nonzero if a step failed (the caller then
+// restarts plainly); all members of the team return the same value.
 DD_HD inline int deflate(const Team& T, const zd* Hbar, int ldh, int m, int k, const zd* c, const zd* y, zd* P, zd* Hn,
                          zd* cn, zd* theta, DeflateWork& W) {
-  const int ld = DD_MAXM;
-  // f = H_m^{-H} e_m with the Hessenberg LU of H_m
-  for (int q = T.tid; q < m * m; q += T.nt) W.M[q % m + (q / m) * ld] = Hbar[q % m + (long)(q / m) * ldh];
-  for (int i = T.tid; i < m; i += T.nt) W.f[i] = Z(i == m - 1 ? 1.0 : 0.0);
-  T.sync();
-  double hn2 = 0;   // max |H_ij|^2 over the Hessenberg pattern
+  const int ld = W.ld;
+  double hn2 = 0;   // max |H_ij|^2
   for (int j = 0; j < m; ++j)
-    for (int i = 0; i <= j + 1 && i < m; ++i) hn2 = fmax(hn2, abs2(Hbar[i + (long)j * ldh]));
+    for (int i = 0; i <= m; ++i) hn2 = fmax(hn2, abs2(Hbar[i + (long)j * ldh]));
   const double hn = sqrt(hn2);
   if (!(hn > 0) || !isfinite(hn)) return 1;
-  hess_lu(T, W.M, m, ld, W.piv, W.l, 0.0);
-  for (int i = 0; i < m; ++i)
-    if (abs2(W.M[i + i * ld]) == 0.0) return 1;
-  hess_solve_adjoint(T, W.M, m, ld, W.piv, W.l, W.f);
-  // G = H_m + |h_{m+1,m}|^2 f e_m^H (still upper Hessenberg: only the last column changes)
+  // f = H_m^{-H} e_m (dense: the leading block need not be Hessenberg)
+  for (int q = T.tid; q < m * m; q += T.nt) W.M[q % m + (q / m) * ld] = conj(Hbar[q / m + (long)(q % m) * ldh]);
+  for (int i = T.tid; i < m; i += T.nt) W.f[i] = Z(i == m - 1 ? 1.0 : 0.0);
+  T.sync();
+  if (!dense_solve(T, W.M, m, ld, W.f)) return 1;
+  // G = H_m + |h_{m+1,m}|^2 f e_m^H, reduced to Hessenberg form G <- Q^H G Q
   const double h2 = abs2(Hbar[m + (long)(m - 1) * ldh]);
   for (int q = T.tid; q < m * m; q += T.nt) {
     const int i = q % m, j = q / m;
-    zd g = i <= j + 1 ? Hbar[i + (long)j * ldh] : Z(0.0);
+    zd g = Hbar[i + (long)j * ldh];
     if (j == m - 1) g = g + h2 * W.f[i];
     W.G[i + j * ld] = g;
-    W.G0[i + j * ld] = g;
   }
+  T.sync();
+  hessenberg(T, W.G, W.Q, m, ld);
+  for (int q = T.tid; q < m * m; q += T.nt) W.G0[q % m + (q / m) * ld] = W.G[q % m + (q / m) * ld];
   T.sync();
   if (hess_eigenvalues(T, W.G, m, ld) < 0) return 2;
   // order by |theta| (stable insertion sort)
@@ -325,10 +405,11 @@ DD_HD inline int deflate(const Team& T, const zd* Hbar, int ldh, int m, int k, c
     for (int i = 0; i < m; ++i) theta[i] = W.G[W.order[i] + W.order[i] * ld];
   }
   T.sync();
-  // columns of P: eigenvectors of G0 for the k smallest |theta| (zero last row)
+  // columns of P: eigenvectors for the k smallest |theta| (zero last row)
   const double tiny = 1e-15 * hn;
-  for (int l = 0; l < k; ++l) {
-    const zd th = theta[l];
+  int kept = 0;
+  for (int cand = 0; cand < m && kept < k; ++cand) {
+    const zd th = theta[cand];
     for (int q = T.tid; q < m * m; q += T.nt) {
       const int i = q % m, j = q / m;
       W.M[i + j * ld] = i == j ? W.G0[i + j * ld] - th : W.G0[i + j * ld];
@@ -336,25 +417,34 @@ DD_HD inline int deflate(const Team& T, const zd* Hbar, int ldh, int m, int k, c
     for (int i = T.tid; i < m; i += T.nt) W.v[i] = Z(1.0);
     T.sync();
     hess_lu(T, W.M, m, ld, W.piv, W.l, tiny);
-    for (int it = 0; it < 2; ++it) {
+    bool ok = true;
+    for (int it = 0; it < 2 && ok; ++it) {
       if (it == 0) upper_solve(T, W.M, m, ld, W.v);      // U v = (1, ..., 1)
       else hess_solve(T, W.M, m, ld, W.piv, W.l, W.v);   // (G0 - theta) v = v
       if (T.tid == 0) {
         double n2 = 0;
         for (int i = 0; i < m; ++i) n2 += abs2(W.v[i]);
-        W.nrm = sqrt(n2);
+        W.nrm[0] = sqrt(n2);
       }
       T.sync();
-      const double nrm = W.nrm;
-      if (!(nrm > 0) || !isfinite(nrm)) return 3;
+      const double nrm = W.nrm[0];
+      if (!(nrm > 0) || !isfinite(nrm)) { ok = false; break; }
       for (int i = T.tid; i < m; i += T.nt) W.v[i] = (1.0 / nrm) * W.v[i];
       T.sync();
     }
-    zd* p = P + (long)l * ldh;
-    for (int i = T.tid; i <= m; i += T.nt) p[i] = i < m ? W.v[i] : Z(0.0);
+    if (!ok) continue;
+    // back to the basis of H_m: w = Q v
+    zd* p = P + (long)kept * ldh;
+    for (int i = T.tid; i <= m; i += T.nt) {
+      zd s = Z(0.0);
+      if (i < m)
+        for (int j = 0; j < m; ++j) s = s + W.Q[i + j * ld] * W.v[j];
+      p[i] = s;
+    }
     T.sync();
-    if (!(orthonormalise(T, P, ldh, l, m + 1, p, W) > 1e-12)) return 3;
+    if (orthonormalise(T, P, ldh, kept, m + 1, p, W) > 1e-8) ++kept;
   }
+  if (kept < k) return 3;
   // last column: least-squares residual c - Hbar y
   for (int i = T.tid; i <= m; i += T.nt) {
     zd s = c[i];

@@ -24,7 +24,7 @@ DD_LAYOUT_CANONICAL, DD_LAYOUT_INTERNAL = 0, 1
 
 class dd_sap_params(C.Structure):
     _fields_ = [("i_schwarz", C.c_int), ("i_domain", C.c_int), ("storage_prec", C.c_int),
-                ("threads_per_site", C.c_int)]
+                ("threads_per_site", C.c_int), ("additive", C.c_int)]
 
 
 class dd_solve_params(C.Structure):
@@ -74,7 +74,7 @@ def lib():
             "dd_sap_precondition_noalloc": (I, [P, P, P, C.POINTER(dd_sap_params)]),
             "dd_sap_precondition_batch": (I, [P, P, P, I, C.POINTER(dd_sap_params)]),
             "dd_apply_D_batch": (I, [P, P, P, I, I]),
-            "dd_sap_precondition_lattices": (I, [C.POINTER(P), C.POINTER(P), C.POINTER(P), I,
+            "dd_sap_precondition_lattices": (I, [C.POINTER(P), C.POINTER(P), C.POINTER(P), I, I,
                                                  C.POINTER(dd_sap_params)]),
             "dd_solve": (I, [P, P, P, I, I, C.POINTER(dd_solve_params), C.POINTER(dd_solve_info)]),
             "dd_solve_bicgstab": (I, [P, P, P, I, C.POINTER(dd_bicgstab_params), C.POINTER(dd_solve_info)]),
@@ -146,13 +146,14 @@ class Context:
         return self._check(lib().dd_apply_D(self._h, _ptr(inp), _ptr(out), prec, layout))
 
     def dd_sap_precondition(self, inp, out, i_schwarz, i_domain, storage_prec, layout=DD_LAYOUT_CANONICAL,
-                            threads_per_site=0):
-        p = dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site)
+                            threads_per_site=0, additive=0):
+        p = dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site, additive)
         return self._check(lib().dd_sap_precondition(self._h, _ptr(inp), _ptr(out), C.byref(p), layout))
 
-    def dd_sap_precondition_batch(self, inp, out, nrhs, i_schwarz, i_domain, storage_prec, threads_per_site=0):
+    def dd_sap_precondition_batch(self, inp, out, nrhs, i_schwarz, i_domain, storage_prec, threads_per_site=0,
+                                  additive=0):
         """nrhs internal-layout FP32 fields one after another; one launch per half-sweep."""
-        p = dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site)
+        p = dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site, additive)
         return self._check(lib().dd_sap_precondition_batch(self._h, _ptr(inp), _ptr(out), nrhs, C.byref(p)))
 
     def dd_apply_D_batch(self, inp, out, nrhs, prec):
@@ -167,8 +168,9 @@ class Context:
         return self._check(s) if check else s
 
     def dd_solve(self, f, x, nrhs=1, where=DD_HOST, tol=1e-10, m=16, k=0, max_iter=1000, i_schwarz=16,
-                 i_domain=4, storage_prec=DD_PREC_FP16, check=True, threads_per_site=0):
-        p = dd_solve_params(tol, m, k, max_iter, dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site))
+                 i_domain=4, storage_prec=DD_PREC_FP16, check=True, threads_per_site=0, additive=0):
+        p = dd_solve_params(tol, m, k, max_iter,
+                            dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site, additive))
         info = dd_solve_info()
         s = lib().dd_solve(self._h, _ptr(f), _ptr(x), nrhs, where, C.byref(p), C.byref(info))
         if check:
@@ -196,23 +198,24 @@ class Context:
     def dd_launch_count(self):
         return lib().dd_launch_count(self._h)
 
-    def dd_autotune(self, storage_prec=DD_PREC_FP16, i_schwarz=0, i_domain=0, threads_per_site=0):
+    def dd_autotune(self, storage_prec=DD_PREC_FP16, i_schwarz=0, i_domain=0, threads_per_site=0, additive=0):
         """Returns (domain shape, (i_schwarz, i_domain, storage_prec, threads_per_site));
-        a parameter given > 0 is kept fixed."""
+        a parameter given > 0 is kept fixed; `additive` selects the Schwarz form tuned."""
         dom = (C.c_int * 4)()
-        p = dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site)
+        p = dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site, additive)
         self._check(lib().dd_autotune(self._h, storage_prec, dom, C.byref(p)))
         return tuple(dom), (p.i_schwarz, p.i_domain, p.storage_prec, p.threads_per_site)
 
 
-def dd_sap_precondition_lattices(ctxs, ins, outs, i_schwarz, i_domain, storage_prec=DD_PREC_FP16):
-    """One Schwarz launch per half-sweep over several lattices (internal FP32 fields)."""
+def dd_sap_precondition_lattices(ctxs, ins, outs, i_schwarz, i_domain, storage_prec=DD_PREC_FP16, nrhs=1):
+    """One Schwarz launch per half-sweep over several lattices, nrhs internal FP32 fields
+    per lattice one after another."""
     n = len(ctxs)
     hs = (C.c_void_p * n)(*[c._h.value for c in ctxs])
     pi = (C.c_void_p * n)(*[_ptr(x) for x in ins])
     po = (C.c_void_p * n)(*[_ptr(x) for x in outs])
     p = dd_sap_params(i_schwarz, i_domain, storage_prec, 0)
-    s = lib().dd_sap_precondition_lattices(hs, pi, po, n, C.byref(p))
+    s = lib().dd_sap_precondition_lattices(hs, pi, po, n, int(nrhs), C.byref(p))
     if s != DD_OK:
         raise DDError(s, lib().dd_last_error(ctxs[0]._h).decode())
 

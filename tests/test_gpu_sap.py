@@ -132,3 +132,25 @@ def test_sap_several_waves_matches_oracle():
         e = rel(z, u)
         print(f"storage {prec} tps {tps}: rel L2 {e:.2e}")
         assert e <= bars[prec]
+
+
+@pytest.mark.parametrize("case", CASES[:3], ids=lambda c: "x".join(map(str, c[0])) + "_b" + "x".join(map(str, c[1])))
+def test_additive_sap_matches_oracle(case):
+    """The additive form (block Jacobi, Sec. II-D Eq. 4): one launch per sweep over both
+    colours, faces double-buffered; against the oracle's additive SAP with the same
+    domains and MR steps, at the multiplicative form's bars."""
+    dims, dom, width, seed, kappa, csw, anti, i_s, i_d = case
+    if not anti:
+        pytest.skip("the oracle's additive SAP uses the antiperiodic time boundary")
+    U = gauge(dims, width, seed)
+    f = synth.gaussian_source(dims, seed + 7)
+    F = W.field_strength(U)
+    u = DD.sap_additive(U, F, f, kappa, csw, DD.Domains(dims, dom), i_s, i_d)
+    c = ctx_for(dims, dom, U, kappa, csw, anti)
+    for prec, bar in ((dd.DD_PREC_FP32, 1e-5), (dd.DD_PREC_FP16, 5e-3), (dd.DD_PREC_FP16_H2, 5e-3)):
+        src = dev(f, torch.float32)
+        out = torch.empty_like(src)
+        c.dd_sap_precondition(src, out, i_s, i_d, prec, dd.DD_LAYOUT_CANONICAL, additive=1)
+        e = rel(host(out), u)
+        print(f"additive storage {prec}: rel L2 {e:.2e}")
+        assert e <= bar
