@@ -223,7 +223,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-mixed", action="store_true", help="time the mixed solve only (profiling runs)")
     ap.add_argument("--case", default="solve",
-                    choices=["solve", "sap", "dslash", "sap_lattices", "workload_solve", "bicgstab"],
+                    choices=["solve", "sap", "dslash", "sap_lattices", "workload_solve", "bicgstab",
+                             "lattices_solve"],
                     help="sap / dslash: time one kernel alone on --lattice (kernel studies, ncu captures)")
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--domain", default="", help="kernel studies: domain shape (default: the workload's)")
@@ -263,6 +264,8 @@ def main():
         return workload_case(args)
     if args.case == "bicgstab":
         return bicgstab_case(args)
+    if args.case == "lattices_solve":
+        return lattices_solve_case(args)
     if args.case != "solve":
         return kernel_case(args, local)
 
@@ -594,6 +597,58 @@ def workload_case(args):
                      "true_rel_residual": info.true_rel_residual, "solve_s": info.t_total, "wall_s": wall,
                      "split_s": {"A": info.t_A, "M": info.t_M, "GS": info.t_GS, "other": info.t_other}}
     os.environ.pop("DD_SEQUENTIAL_RHS", None)
+    out["device_gb_in_use"] = (lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info())
+    print(json.dumps(out))
+
+
+def lattices_solve_case(args):
+    """The uneven batch of the fifth workload solved: 16^3x32 (kappa 0.134), 24^3x48
+    (0.135) and 32^3x64 (0.1355), c_sw 1.5, --nrhs Gaussian sources each (the workload
+    states 8), 4^4 domains (24 / 8 is odd), in lockstep with one Schwarz launch per
+    half-sweep over all three lattices (dd_solve_lattices), and, for comparison, one
+    lattice after another (dd_solve with its lockstep over that lattice's sources).
+    Settings as on the supercritical 32^3x64 workload: I_S 2, I_d 4, deflation k 8;
+    --m sets the basis (default 24, sized so the 24 solves' bases fit in HBM)."""
+    import torch
+
+    import synth
+    from paper_1412_2629_gb300 import dd
+    base = synth.WORKLOADS[WORKLOAD]
+    st = torch.cuda.current_stream()
+    specs = [((16, 16, 16, 32), 0.1340, 151), ((24, 24, 24, 48), 0.1350, 152), ((32, 32, 32, 64), 0.1355, 153)]
+    nr, m = args.nrhs, args.m or 24
+    kw = dict(tol=1e-10, m=m, k=8, max_iter=20000, i_schwarz=2, i_domain=4)
+    ctxs, fs, xs = [], [], []
+    for dims, kappa, seed in specs:
+        w = synth.Workload("lat", dims, base.width, base.ape_steps, kappa, 1.5, (4, 4, 4, 4), 2, 4, m, 8, seed,
+                           seed + 10)
+        U = synth.make_gauge(w, device="cuda")
+        c = dd.Context(dims, (4, 4, 4, 4), True, st.cuda_stream)
+        c.dd_load_gauge(torch.view_as_real(U).contiguous(), dd.DD_DEVICE)
+        c.dd_build_clover(kappa, 1.5)
+        del U
+        f = np.stack(synth.make_sources(w, nr))
+        fs.append(torch.view_as_real(torch.from_numpy(f)).cuda().contiguous())
+        xs.append(torch.zeros_like(fs[-1]))
+        ctxs.append(c)
+    torch.cuda.empty_cache()
+    out = {"case": "lattices_solve", "lattices": [list(d) for d, _, _ in specs], "kappa": [k for _, k, _ in specs],
+           "nrhs_per_lattice": nr, "domain": [4, 4, 4, 4], "m": m, "k": 8, "i_schwarz": 2, "i_domain": 4}
+    for x in xs:
+        x.zero_()
+    torch.cuda.synchronize()
+    info = dd.dd_solve_lattices(ctxs, fs, xs, nrhs=nr, where=dd.DD_DEVICE, check=False, **kw)
+    out["one_launch"] = {"status": info.status, "iterations": info.iterations, "solve_s": info.t_total,
+                         "true_rel_residual": info.true_rel_residual,
+                         "split_s": {"A": info.t_A, "M": info.t_M, "GS": info.t_GS, "other": info.t_other}}
+    tot, worst, its = 0.0, 0.0, 0
+    for c, f, x in zip(ctxs, fs, xs):
+        x.zero_()
+        i1 = c.dd_solve(f, x, nrhs=nr, where=dd.DD_DEVICE, check=False, **kw)
+        tot += i1.t_total
+        worst = max(worst, i1.true_rel_residual)
+        its += i1.iterations
+    out["per_lattice"] = {"iterations": its, "solve_s": tot, "true_rel_residual": worst}
     out["device_gb_in_use"] = (lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info())
     print(json.dumps(out))
 

@@ -187,6 +187,31 @@ dd_status dd_sap_precondition_noalloc(dd_ctx* ctx, const float* in, float* out, 
 dd_status dd_solve(dd_ctx* ctx, const double* f, double* x, int nrhs, int where, const dd_solve_params* p,
                    dd_solve_info* info);
 
+/* Lockstep solves over nlat <= 4 lattices of different volume (the many independent
+ * solves of an analysis, Sec. IV-C), nrhs right-hand sides each: f[l] / x[l] hold lattice
+ * l's nrhs canonical FP64 fields one after another (host or device per `where`).  Every
+ * (lattice, right-hand side) is solved as by dd_solve (FGMRES-DR with reliable updates,
+ * its own basis, restarts and stopping point); every Arnoldi step applies the Schwarz
+ * preconditioner to all unconverged ones in one launch per half-sweep over the lattices'
+ * (domain, right-hand side) work, and the operator in one launch per lattice.  The
+ * contexts need the same domain volume; FP16 storage, two threads per site and the
+ * multiplicative form (else DD_ERR_INVALID).  All work runs on ctxs[0]'s stream; each
+ * context holds nrhs copies of the solver's buffers.  info sums over all solves;
+ * true_rel_residual is the largest. */
+dd_status dd_solve_lattices(dd_ctx** ctxs, int nlat, const double* const* f, double* const* x, int nrhs, int where,
+                            const dd_solve_params* p, dd_solve_info* info);
+
+/* A x = f with flexible GCR(m) around the same Schwarz preconditioner: the outer solver
+ * of Luescher's SAP-GCR, which the paper contrasts with its FGMRES-DR (Sec. V).  Per step
+ * z_k = M r, w_k = A z_k orthonormalised against w_0..w_{k-1} (classical Gram-Schmidt with
+ * a second pass when the first cancels more than half, FP64-reduced; the coefficients are
+ * applied to z_k too), alpha_k = <w_k, r>, r -= alpha_k w_k.  After at most p->m steps
+ * x += sum alpha_k z_k in FP64 and the residual is recomputed with the FP64 operator
+ * (restart).  FP32 vectors, canonical FP64 f and x (host or device per `where`), one
+ * right-hand side; p->k is ignored.  Uses the context's solver buffers (sized by m). */
+dd_status dd_solve_gcr(dd_ctx* ctx, const double* f, double* x, int where, const dd_solve_params* p,
+                       dd_solve_info* info);
+
 /* Standard (not domain-decomposed) comparison solver, the kind the paper measures its
  * solver against (Sec. IV-C, Table III: BiCGstab in double precision; mixed-precision
  * Richardson iteration around BiCGstab).  Solves A x = f like dd_solve (canonical FP64
@@ -270,6 +295,11 @@ dd_status dd_autotune(dd_ctx* ctx, int storage_prec, int domain_out[4], dd_sap_p
  * DD_ERR_NONFINITE when a step fails (the solver then restarts without deflation). */
 dd_status dd_deflate_host(int m, int k, const double* Hbar, const double* c, const double* y, double* P, double* Hn,
                           double* cn, double* theta);
+/* The same step as dd_solve runs it (one warp on the current device), for checks and
+ * timing: arguments as dd_deflate_host but in device memory; ms (host, may be NULL)
+ * receives the kernel's device time.  Allocates and frees its scratch; synchronous. */
+dd_status dd_deflate_device(int m, int k, const double* Hbar, const double* c, const double* y, double* P, double* Hn,
+                            double* cn, double* theta, double* ms);
 
 #ifdef __cplusplus
 }

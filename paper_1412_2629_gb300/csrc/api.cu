@@ -1297,6 +1297,229 @@ static dd_status solve_lockstep(dd_ctx* c, const double* f, double* x, int nrhs,
   return worst;
 }
 
+// ------------------------------------------------------------------ lattices of different volume
+// Lockstep solves over several lattices (the many independent solves of an analysis,
+// Sec. IV-C): every (lattice, right-hand side) keeps its own basis, restarts and stopping
+// point as in solve_lockstep; every Arnoldi step applies M to all unconverged ones in one
+// launch per half-sweep over the lattices' (domain, right-hand side) work, and A in one
+// launch per lattice.  All work runs on the first context's stream.
+struct LatticeStreams {
+  std::vector<dd_ctx*> ctxs;
+  std::vector<cudaStream_t> saved;
+  ~LatticeStreams() {
+    if (!ctxs.empty()) cudaStreamSynchronize(ctxs[0]->st);
+    for (size_t l = 0; l < ctxs.size(); ++l) ctxs[l]->st = saved[l];
+  }
+};
+
+static dd_status solve_lattices(dd_ctx** ctxs, int nlat, const double* const* f, double* const* x, int nrhs, int where,
+                                const dd_solve_params* p, dd_solve_info* info) {
+  dd_ctx* c0 = ctxs[0];
+  const cudaStream_t st = c0->st;
+  LatticeStreams keep;
+  for (int l = 0; l < nlat; ++l) {
+    keep.ctxs.push_back(ctxs[l]);
+    keep.saved.push_back(ctxs[l]->st);
+    ctxs[l]->st = st;
+  }
+  const int m = p->m;
+  const double tol = p->tol;
+  cudaMemcpyKind in_kind = where == DD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaMemcpyKind out_kind = where == DD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  std::vector<std::vector<LockRhs>> R(nlat, std::vector<LockRhs>(nrhs));
+  for (int l = 0; l < nlat; ++l) {
+    TRY(ensure_lock(ctxs[l], nrhs, m));
+    TRY(ensure_sap(ctxs[l], P16, nrhs));
+  }
+  cudaEvent_t e0, e1, e2, e3, tstart, tend;
+  for (cudaEvent_t* e : {&e0, &e1, &e2, &e3, &tstart, &tend}) cudaEventCreate(e);
+  struct EvFree {
+    cudaEvent_t e[6];
+    ~EvFree() { for (cudaEvent_t q : e) cudaEventDestroy(q); }
+  } evf{{e0, e1, e2, e3, tstart, tend}};
+  cudaEventRecord(tstart, st);
+  double tA = 0, tM = 0, tGS = 0;
+  // set-up: fields in, FP64 residual, first basis vector
+  for (int l = 0; l < nlat; ++l) {
+    dd_ctx* c = ctxs[l];
+    const Geom& g = c->g;
+    const size_t cb = (size_t)g.V * 24 * 8;
+    for (int r = 0; r < nrhs; ++r) {
+      SolverBuffers& s = c->lock[r];
+      LockRhs& Q = R[l][r];
+      TRY(cuda_check(c, cudaMemcpyAsync(s.canon64, f[l] + (size_t)r * g.V * 24, cb, in_kind, st), "copy f"));
+      launch_pack_spinor(g, s.canon64, P64, view(g, s.f64, P64), st);
+      TRY(cuda_check(c, cudaMemcpyAsync(s.canon64, x[l] + (size_t)r * g.V * 24, cb, in_kind, st), "copy x"));
+      launch_pack_spinor(g, s.canon64, P64, view(g, s.x64, P64), st);
+      launch_norm2_64(s.f64, g.V * 12, s.partial, st);
+      launch_reduce_partials(s.partial, 1, s.nrm2, 0, st);
+      TRY(launched(c, 4));
+      double2 h;
+      TRY(cuda_check(c, cudaMemcpyAsync(&h, s.nrm2, sizeof(double2), cudaMemcpyDeviceToHost, st), "norm f"));
+      TRY(cuda_check(c, cudaStreamSynchronize(st), "norm f"));
+      if (h.x == 0.0) {
+        cudaMemsetAsync(s.x64, 0, field_bytes(g, P64), st);
+        Q.done = true;
+        continue;
+      }
+      Q.nf = sqrt(h.x);
+      TRY(true_residual(c, &Q.rho2, &s));
+      Q.reliable++;
+      Q.rel = sqrt(Q.rho2) / Q.nf;
+      if (!isfinite(Q.rel)) {
+        Q.rc = fail(c0, DD_ERR_NONFINITE, "non-finite residual");
+        Q.done = true;
+      } else if (Q.rel <= tol) {
+        Q.done = true;
+      } else {
+        launch_r64_to_v32(s.V, s.r64, g.V * 6, s.nrm2, st);
+        plain_restart_kernel<<<1, 1, 0, st>>>(s.H, s.R, m + 1, m, s.nrm2, s.g, s.c0, s.lsq);
+        TRY(launched(c, 2));
+        Q.rho_cycle = sqrt(Q.rho2);
+      }
+    }
+  }
+  std::vector<std::vector<int>> act(nlat);
+  while (true) {
+    int total = 0, nl = 0;
+    Geom gs[4];
+    SapState Ss[4];
+    int lat_of[4];
+    for (int l = 0; l < nlat; ++l) {
+      act[l].clear();
+      for (int r = 0; r < nrhs; ++r)
+        if (!R[l][r].done) act[l].push_back(r);
+      const int na = (int)act[l].size();
+      total += na;
+      if (!na) continue;
+      dd_ctx* c = ctxs[l];
+      const long long n4 = c->g.V * 6;
+      void** hp = c->h_lock_ptrs;
+      for (int i = 0; i < na; ++i) {
+        SolverBuffers& s = c->lock[act[l][i]];
+        hp[i] = s.V + (long long)R[l][act[l][i]].j * n4;
+        hp[na + i] = s.Z + (long long)R[l][act[l][i]].j * n4;
+        hp[2 * na + i] = s.w;
+      }
+      TRY(cuda_check(c, cudaMemcpyAsync(c->lock_ptrs, hp, 3 * (size_t)na * sizeof(void*), cudaMemcpyHostToDevice, st),
+                     "pointer lists"));
+      gs[nl] = c->g;
+      Ss[nl] = sap_state(c, P16, &p->sap, na);
+      Ss[nl].vlist = (const float4* const*)c->lock_ptrs;
+      Ss[nl].zlist = (float4* const*)(c->lock_ptrs + na);
+      lat_of[nl++] = l;
+    }
+    if (!total) break;
+    const float4* vnull[4] = {nullptr, nullptr, nullptr, nullptr};
+    float4* znull[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEventRecord(e0, st);
+    for (int sw = 0; sw < p->sap.i_schwarz; ++sw)
+      for (int colour = 0; colour < 2; ++colour) {
+        int first = sw == 0, use_faces = !(sw == 0 && colour == 0), last = sw == p->sap.i_schwarz - 1;
+        if (sap_half_sweep_lattices(gs, Ss, nl, colour, first, use_faces, last, vnull, znull, p->sap.i_domain, st))
+          return fail(c0, DD_ERR_CUDA, std::string("Schwarz launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+        TRY(launched(c0));
+      }
+    cudaEventRecord(e1, st);
+    for (int q = 0; q < nl; ++q) {
+      dd_ctx* c = ctxs[lat_of[q]];
+      const int na = (int)act[lat_of[q]].size();
+      launch_apply_A_multi_list(c->g, gauge_view(c, P32), clover_view(c, P32), (const float4* const*)(c->lock_ptrs + na),
+                                (float4* const*)(c->lock_ptrs + 2 * na), na, st);
+      TRY(launched(c));
+    }
+    cudaEventRecord(e2, st);
+    for (int l = 0; l < nlat; ++l)
+      for (int r : act[l]) TRY(lock_gs(ctxs[l], ctxs[l]->lock[r], R[l][r].j, m));
+    cudaEventRecord(e3, st);
+    TRY(cuda_check(c0, cudaStreamSynchronize(st), "lockstep step"));
+    float ms;
+    cudaEventElapsedTime(&ms, e0, e1); tM += ms * 1e-3;
+    cudaEventElapsedTime(&ms, e1, e2); tA += ms * 1e-3;
+    cudaEventElapsedTime(&ms, e2, e3); tGS += ms * 1e-3;
+    for (int l = 0; l < nlat; ++l)
+      for (int r : act[l]) {
+        LockRhs& Q = R[l][r];
+        SolverBuffers& s = ctxs[l]->lock[r];
+        Q.iters++;
+        const double est = s.h_status[0];
+        if (!isfinite(est) || !isfinite(s.h_status[2])) {
+          Q.rc = fail(c0, DD_ERR_NONFINITE, "non-finite Arnoldi step");
+          Q.done = true;
+          continue;
+        }
+        if (est <= 0.5 * tol * Q.nf || est <= 2e-6 * Q.rho_cycle || Q.iters >= p->max_iter || Q.j + 1 == m) {
+          TRY(lock_end_cycle(ctxs[l], s, Q, Q.j + 1, p));
+        } else {
+          Q.j++;
+        }
+      }
+  }
+  cudaEventRecord(tend, st);
+  cudaEventSynchronize(tend);
+  float ms_total = 0;
+  cudaEventElapsedTime(&ms_total, tstart, tend);
+  dd_status worst = DD_OK;
+  for (int l = 0; l < nlat; ++l) {
+    dd_ctx* c = ctxs[l];
+    const Geom& g = c->g;
+    const size_t cb = (size_t)g.V * 24 * 8;
+    for (int r = 0; r < nrhs; ++r) {
+      SolverBuffers& s = c->lock[r];
+      launch_unpack_spinor(g, view(g, s.x64, P64), s.canon64, P64, st);
+      TRY(launched(c));
+      TRY(cuda_check(c, cudaMemcpyAsync(x[l] + (size_t)r * g.V * 24, s.canon64, cb, out_kind, st), "copy x out"));
+      if (R[l][r].rc != DD_OK && worst == DD_OK) worst = R[l][r].rc;
+    }
+  }
+  TRY(cuda_check(c0, cudaStreamSynchronize(st), "solve"));
+  if (info) {
+    for (int l = 0; l < nlat; ++l)
+      for (const LockRhs& Q : R[l]) {
+        info->iterations += Q.iters;
+        info->restarts += Q.restarts;
+        info->reliable_updates += Q.reliable;
+        info->deflated_restarts += Q.deflated;
+        info->true_rel_residual = fmax(info->true_rel_residual, Q.rel);
+        const double V = (double)ctxs[l]->g.V;
+        info->flops_nominal += Q.iters * (1848.0 * V + p->sap.i_schwarz * (p->sap.i_domain + 1) * 1848.0 * V) +
+                               Q.reliable * 1848.0 * V;
+      }
+    info->t_total = ms_total * 1e-3;
+    info->t_A = tA;
+    info->t_M = tM;
+    info->t_GS = tGS;
+    info->t_other = ms_total * 1e-3 - tA - tM - tGS;
+    info->status = worst;
+  }
+  if (worst == DD_OK)
+    for (int l = 0; l < nlat; ++l) TRY(sap_error_flag(ctxs[l]));
+  return worst;
+}
+
+extern "C" dd_status dd_solve_lattices(dd_ctx** ctxs, int nlat, const double* const* f, double* const* x, int nrhs,
+                                       int where, const dd_solve_params* p, dd_solve_info* info) {
+  if (!ctxs || !f || !x || !p || nlat < 1 || nlat > 4 || nrhs < 1) return DD_ERR_INVALID;
+  dd_ctx* c0 = ctxs[0];
+  if (!c0) return DD_ERR_INVALID;
+  if (p->m < 1 || p->m > DD_MAXM - 1 || p->k < 0 || p->k >= p->m || !(p->tol > 0) || p->max_iter < 1)
+    return fail(c0, DD_ERR_INVALID, "bad solver parameters");
+  TRY(check_sap_params(c0, &p->sap));
+  if (p->sap.storage_prec != DD_PREC_FP16 || p->sap.threads_per_site == 1 || p->sap.i_domain < 1 || p->sap.additive)
+    return fail(c0, DD_ERR_INVALID,
+                "lattice batches need FP16 storage, two threads per site, i_domain >= 1 and the multiplicative form");
+  for (int l = 0; l < nlat; ++l) {
+    if (!ctxs[l] || !f[l] || !x[l]) return DD_ERR_INVALID;
+    if (!ctxs[l]->have_clover) return fail(c0, DD_ERR_NO_CLOVER, "clover not built on lattice " + std::to_string(l));
+    if (ctxs[l]->g.Vd != c0->g.Vd || sap_mat_fits_smem(ctxs[l]->g, P16) != sap_mat_fits_smem(c0->g, P16))
+      return fail(c0, DD_ERR_DIMS, "lattices of one launch need the same domain volume");
+    for (int q = 0; q < l; ++q)
+      if (ctxs[q] == ctxs[l]) return fail(c0, DD_ERR_INVALID, "a context appears twice");
+  }
+  if (info) memset(info, 0, sizeof(*info));
+  return solve_lattices(ctxs, nlat, f, x, nrhs, where, p, info);
+}
+
 extern "C" dd_status dd_solve(dd_ctx* c, const double* f, double* x, int nrhs, int where, const dd_solve_params* p,
                               dd_solve_info* info) {
   if (!c || !f || !x || !p || nrhs < 1) return DD_ERR_INVALID;
@@ -1362,6 +1585,172 @@ extern "C" dd_status dd_solve(dd_ctx* c, const double* f, double* x, int nrhs, i
   }
   if (info) info->status = worst;
   return worst;
+}
+
+// ------------------------------------------------------------------ GCR outer solver
+// Flexible GCR(m), the outer iteration of Luescher's SAP-GCR (the alternative to FGMRES-DR
+// that the paper contrasts with its own choice, Sec. V): with r the current residual,
+// z_k = M r, w_k = A z_k made orthonormal to w_0..w_{k-1} (the same coefficients applied
+// to z_k keep A z_k = w_k), alpha_k = <w_k, r>, r -= alpha_k w_k; at the end of a cycle
+// x += sum alpha_k z_k in FP64 and the residual is recomputed with the FP64 operator.
+// W and Z use the solver's V and Z bases; r is the FP32 vector w, scaled by 1 / |r|.
+
+// alpha <- rho alpha for the cycle's coefficients (r was normalised by rho)
+__global__ void scale_by_norm_kernel(zd* a, int n, const double2* nrm2) {
+  const double rho = sqrt(nrm2->x);
+  for (int i = 0; i < n; ++i) a[i] = rho * a[i];
+}
+// status[0] = |r| after the step, status[2] = |w_k| before normalisation
+__global__ void gcr_status_kernel(const double2* nrm_r, const double* nu2, double* status) {
+  status[0] = sqrt(fmax(nrm_r->x, 0.0));
+  status[2] = sqrt(*nu2);
+  status[3] = 0.0;
+}
+
+static dd_status solve_gcr_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_solve_info* info) {
+  SolverBuffers& s = c->sv;
+  const Geom& g = c->g;
+  const long long n4 = g.V * 6;
+  const int m = p->m;
+  const double tol = p->tol, nf = sqrt(nf2);
+  cudaEvent_t e0, e1, e2, e3, tstart, tend;
+  for (cudaEvent_t* e : {&e0, &e1, &e2, &e3, &tstart, &tend}) cudaEventCreate(e);
+  cudaEventRecord(tstart, c->st);
+  double tA = 0, tM = 0, tGS = 0;
+  int iters = 0, restarts = 0, reliable = 0;
+  dd_status rc = DD_OK;
+  double rho2 = 0;
+  auto Wv = [&](int i) { return s.V + (long long)i * n4; };
+  auto Zv = [&](int i) { return s.Z + (long long)i * n4; };
+  float4* r = s.w;
+  float4* wk = s.V + (long long)m * n4;   // the (m+1)-th basis slot: the new direction
+  zd* alpha = s.y;                          // m + 2 entries
+  TRY(true_residual(c, &rho2));
+  reliable++;
+  double rel = sqrt(rho2) / nf;
+  if (!isfinite(rel)) rc = fail(c, DD_ERR_NONFINITE, "non-finite residual");
+  while (rc == DD_OK && rel > tol) {
+    if (iters >= p->max_iter) { rc = fail(c, DD_ERR_NOT_CONVERGED, "iteration limit reached"); break; }
+    launch_r64_to_v32(r, s.r64, n4, s.nrm2, c->st);   // r = r64 / |r64|
+    TRY(launched(c));
+    int mm = 0;
+    for (int k = 0; k < m; ++k) {
+      cudaEventRecord(e0, c->st);
+      TRY(sap_run(c, r, Zv(k), &p->sap));
+      cudaEventRecord(e1, c->st);
+      TRY(apply_internal(c, Zv(k), wk, P32));
+      cudaEventRecord(e2, c->st);
+      // w_k <- w_k - W beta (classical, with the DGKS second pass); z_k <- z_k - Z beta
+      double2* nrm_a = s.nrm2 + 1;
+      double2* nrm_b = s.nrm2 + 2;
+      int nk = launch_gs_dot(Wv(0), k, n4, wk, s.partial, nullptr, 0, c->st);
+      launch_gs_reduce(s.partial, k, (double2*)s.hA, nullptr, 0, c->st);
+      launch_gs_project(Wv(k), wk, Wv(0), k, n4, (const double2*)s.hA, s.partial2, nullptr, 0, c->st);
+      launch_gs_reduce(s.partial2, 0, nrm_a, nullptr, 0, c->st);
+      launch_gs_project(Zv(k), Zv(k), Zv(0), k, n4, (const double2*)s.hA, s.partial2, nullptr, 0, c->st);
+      gs_decide_kernel<<<1, 1, 0, c->st>>>(s.hA, k, nrm_a, s.hB, s.flag, s.nu2);
+      nk += launch_gs_dot(Wv(0), k, n4, Wv(k), s.partial, s.flag, 1, c->st);
+      launch_gs_reduce(s.partial, k, (double2*)s.hB, s.flag, 1, c->st);
+      launch_gs_project(Wv(k), Wv(k), Wv(0), k, n4, (const double2*)s.hB, s.partial2, s.flag, 1, c->st);
+      launch_gs_reduce(s.partial2, 0, nrm_b, s.flag, 1, c->st);
+      launch_gs_project(Zv(k), Zv(k), Zv(0), k, n4, (const double2*)s.hB, s.partial2, s.flag, 1, c->st);
+      gs_decide2_kernel<<<1, 1, 0, c->st>>>(s.flag, nrm_b, s.nu2);
+      launch_scale_inplace(Wv(k), n4, s.nu2, c->st);
+      launch_scale_inplace(Zv(k), n4, s.nu2, c->st);
+      // alpha_k = <w_k, r>; r <- r - alpha_k w_k with its exact norm
+      nk += launch_gs_dot(Wv(k), 1, n4, r, s.partial, nullptr, 0, c->st);
+      launch_gs_reduce(s.partial, 1, (double2*)(alpha + k), nullptr, 0, c->st);
+      launch_gs_project(r, r, Wv(k), 1, n4, (const double2*)(alpha + k), s.partial2, nullptr, 0, c->st);
+      launch_gs_reduce(s.partial2, 0, s.nrm2 + 3, nullptr, 0, c->st);
+      gcr_status_kernel<<<1, 1, 0, c->st>>>(s.nrm2 + 3, s.nu2, s.status);
+      TRY(launched(c, nk + 17));
+      cudaEventRecord(e3, c->st);
+      TRY(read_status(c));
+      float ms;
+      cudaEventElapsedTime(&ms, e0, e1); tM += ms * 1e-3;
+      cudaEventElapsedTime(&ms, e1, e2); tA += ms * 1e-3;
+      cudaEventElapsedTime(&ms, e2, e3); tGS += ms * 1e-3;
+      iters++;
+      mm = k + 1;
+      const double est = s.h_status[0] * sqrt(rho2);
+      if (c->trace) fprintf(stderr, "[dd] gcr it %d k %d est/rho %.3e |w| %.3e\n", iters, k, s.h_status[0], s.h_status[2]);
+      if (!isfinite(est) || !isfinite(s.h_status[2])) { rc = fail(c, DD_ERR_NONFINITE, "non-finite GCR step"); break; }
+      if (est <= 0.5 * tol * nf || s.h_status[0] <= 2e-6 || iters >= p->max_iter) break;
+    }
+    if (rc != DD_OK) break;
+    // x += rho sum alpha_k z_k (FP64), then the FP64 residual
+    scale_by_norm_kernel<<<1, 1, 0, c->st>>>(alpha, mm, s.nrm2);
+    launch_x_update(s.x64, Zv(0), mm, n4, (const double2*)alpha, c->st);
+    TRY(launched(c, 2));
+    TRY(true_residual(c, &rho2));
+    reliable++;
+    rel = sqrt(rho2) / nf;
+    if (!isfinite(rel)) { rc = fail(c, DD_ERR_NONFINITE, "non-finite residual"); break; }
+    if (rel <= tol) break;
+    restarts++;
+    if (c->trace) fprintf(stderr, "[dd] gcr restart: true residual %.3e\n", rel);
+  }
+  cudaEventRecord(tend, c->st);
+  cudaEventSynchronize(tend);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, tstart, tend);
+  if (info) {
+    info->iterations += iters;
+    info->restarts += restarts;
+    info->reliable_updates += reliable;
+    info->true_rel_residual = fmax(info->true_rel_residual, rel);
+    info->t_total += ms * 1e-3;
+    info->t_A += tA;
+    info->t_M += tM;
+    info->t_GS += tGS;
+    info->t_other += ms * 1e-3 - tA - tM - tGS;
+    const double V = (double)g.V;
+    info->flops_nominal += iters * (1848.0 * V + p->sap.i_schwarz * (p->sap.i_domain + 1) * 1848.0 * V) +
+                           reliable * 1848.0 * V;
+  }
+  for (cudaEvent_t e : {e0, e1, e2, e3, tstart, tend}) cudaEventDestroy(e);
+  if (rc == DD_OK) TRY(sap_error_flag(c));
+  return rc;
+}
+
+extern "C" dd_status dd_solve_gcr(dd_ctx* c, const double* f, double* x, int where, const dd_solve_params* p,
+                                  dd_solve_info* info) {
+  if (!c || !f || !x || !p) return DD_ERR_INVALID;
+  if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
+  if (p->m < 1 || p->m > DD_MAXM - 1 || !(p->tol > 0) || p->max_iter < 1)
+    return fail(c, DD_ERR_INVALID, "bad solver parameters");
+  TRY(check_sap_params(c, &p->sap));
+  if (p->sap.i_domain < 1) return fail(c, DD_ERR_INVALID, "i_domain must be >= 1");
+  TRY(ensure_solver(c, p->m));
+  if (info) memset(info, 0, sizeof(*info));
+  const Geom& g = c->g;
+  SolverBuffers& s = c->sv;
+  const size_t cb = (size_t)g.V * 24 * 8;
+  TRY(cuda_check(c, cudaMemcpyAsync(s.canon64, f, cb, where == DD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                    c->st),
+                 "copy f"));
+  launch_pack_spinor(g, s.canon64, P64, view(g, s.f64, P64), c->st);
+  TRY(cuda_check(c, cudaMemcpyAsync(s.canon64, x, cb, where == DD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                    c->st),
+                 "copy x"));
+  launch_pack_spinor(g, s.canon64, P64, view(g, s.x64, P64), c->st);
+  launch_norm2_64(s.f64, g.V * 12, s.partial, c->st);
+  launch_reduce_partials(s.partial, 1, s.nrm2, 0, c->st);
+  TRY(launched(c, 4));
+  double2 h;
+  TRY(cuda_check(c, cudaMemcpyAsync(&h, s.nrm2, sizeof(double2), cudaMemcpyDeviceToHost, c->st), "norm f"));
+  TRY(cuda_check(c, cudaStreamSynchronize(c->st), "norm f"));
+  dd_status st = DD_OK;
+  if (h.x == 0.0) cudaMemsetAsync(s.x64, 0, field_bytes(g, P64), c->st);
+  else st = solve_gcr_one(c, p, h.x, info);
+  launch_unpack_spinor(g, view(g, s.x64, P64), s.canon64, P64, c->st);
+  TRY(launched(c));
+  TRY(cuda_check(c, cudaMemcpyAsync(x, s.canon64, cb, where == DD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                    c->st),
+                 "copy x out"));
+  TRY(cuda_check(c, cudaStreamSynchronize(c->st), "gcr"));
+  if (info) info->status = st;
+  return st;
 }
 
 // ------------------------------------------------------------------ BiCGstab comparison solver
@@ -1602,6 +1991,34 @@ extern "C" dd_status dd_deflate_host(int m, int k, const double* Hbar, const dou
   const Team T{0, 1};
   int rc = deflate(T, (const zd*)Hbar, m + 1, m, k, (const zd*)cvec, (const zd*)yvec, (zd*)P, (zd*)Hn, (zd*)cn,
                    (zd*)theta, W);
+  return rc == 0 ? DD_OK : DD_ERR_NONFINITE;
+}
+
+extern "C" dd_status dd_deflate_device(int m, int k, const double* Hbar, const double* cvec, const double* yvec,
+                                       double* P, double* Hn, double* cn, double* theta, double* ms) {
+  if (m < 1 || m >= DD_MAXM || k < 1 || k >= m || !Hbar || !cvec || !yvec || !P || !Hn || !cn || !theta)
+    return DD_ERR_INVALID;
+  void* scratch = nullptr;
+  int* flags = nullptr;
+  if (cudaMalloc(&scratch, deflate_bytes(m)) != cudaSuccess) return DD_ERR_OOM;
+  if (cudaMalloc(&flags, 16) != cudaSuccess) { cudaFree(scratch); return DD_ERR_OOM; }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, 0);
+  launch_deflate((const zd*)Hbar, m + 1, m, k, (const zd*)cvec, (const zd*)yvec, (zd*)P, (zd*)Hn, (zd*)cn, (zd*)theta,
+                 scratch, flags, 0);
+  cudaEventRecord(e1, 0);
+  int rc = -1;
+  cudaError_t e = cudaMemcpy(&rc, flags, sizeof(int), cudaMemcpyDeviceToHost);
+  float t = 0;
+  cudaEventElapsedTime(&t, e0, e1);
+  if (ms) *ms = t;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(scratch);
+  cudaFree(flags);
+  if (e != cudaSuccess) return DD_ERR_CUDA;
   return rc == 0 ? DD_OK : DD_ERR_NONFINITE;
 }
 

@@ -23,7 +23,9 @@ DD_HD inline zd operator*(zd a, zd b) { return Z(a.re * b.re - a.im * b.im, a.re
 DD_HD inline zd operator*(double s, zd a) { return Z(s * a.re, s * a.im); }
 DD_HD inline zd conj(zd a) { return Z(a.re, -a.im); }
 DD_HD inline double abs2(zd a) { return a.re * a.re + a.im * a.im; }
-DD_HD inline double zabs(zd a) { return hypot(a.re, a.im); }
+// |a| without hypot's scaling: the entries here are far from the FP64 overflow and
+// underflow limits, and a plain square root is several times cheaper on the device
+DD_HD inline double zabs(zd a) { return sqrt(a.re * a.re + a.im * a.im); }
 DD_HD inline zd zdiv(zd a, zd b) {
   double d = abs2(b);
   return Z((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
@@ -38,7 +40,7 @@ DD_HD inline Rot make_rot(zd x, zd y) {
   double ax = zabs(x), ay = zabs(y);
   if (ay == 0.0) { g.c = 1.0; g.s = Z(0.0); return g; }
   if (ax == 0.0) { g.c = 0.0; g.s = Z(1.0); return g; }
-  double nrm = hypot(ax, ay);
+  double nrm = sqrt(ax * ax + ay * ay);
   zd ph = Z(x.re / ax, x.im / ax);
   g.c = ax / nrm;
   g.s = (1.0 / nrm) * (ph * conj(y));
@@ -204,8 +206,10 @@ DD_HD inline int hess_eigenvalues(const Team& T, zd* A, int n, int ld) {
     zd tr2 = 0.5 * (aa + dd);
     zd det = aa * dd - bb * cc;
     zd disc = tr2 * tr2 - det;
-    double rr = zabs(disc), th = atan2(disc.im, disc.re);
-    zd sq = Z(sqrt(rr) * cos(0.5 * th), sqrt(rr) * sin(0.5 * th));
+    // principal square root of disc without trigonometric functions
+    const double rr = zabs(disc);
+    const double sre = sqrt(0.5 * (rr + disc.re)), sim = sqrt(fmax(0.0, 0.5 * (rr - disc.re)));
+    zd sq = Z(sre, disc.im < 0.0 ? -sim : sim);
     zd l1 = tr2 + sq, l2 = tr2 - sq;
     zd mu = abs2(l1 - dd) < abs2(l2 - dd) ? l1 : l2;
     if (iter % 11 == 10) mu = dd + Z(zabs(a(hi, hi - 1)), 0.0);

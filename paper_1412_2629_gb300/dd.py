@@ -78,6 +78,9 @@ def lib():
                                                  C.POINTER(dd_sap_params)]),
             "dd_solve": (I, [P, P, P, I, I, C.POINTER(dd_solve_params), C.POINTER(dd_solve_info)]),
             "dd_solve_bicgstab": (I, [P, P, P, I, C.POINTER(dd_bicgstab_params), C.POINTER(dd_solve_info)]),
+            "dd_solve_gcr": (I, [P, P, P, I, C.POINTER(dd_solve_params), C.POINTER(dd_solve_info)]),
+            "dd_solve_lattices": (I, [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), I, I,
+                                      C.POINTER(dd_solve_params), C.POINTER(dd_solve_info)]),
             "dd_spinor_bytes": (C.c_size_t, [P, I, I]),
             "dd_pack_spinor": (I, [P, P, I, P, I]),
             "dd_unpack_spinor": (I, [P, P, I, P, I]),
@@ -85,6 +88,7 @@ def lib():
             "dd_load_model": (D, [C.c_longlong, I]),
             "dd_autotune": (I, [P, I, C.POINTER(I), C.POINTER(dd_sap_params)]),
             "dd_deflate_host": (I, [I, I, P, P, P, P, P, P, P]),
+            "dd_deflate_device": (I, [I, I, P, P, P, P, P, P, P, C.POINTER(D)]),
             "dd_fp32_peak": (I, [I, C.POINTER(D), C.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
@@ -177,6 +181,16 @@ class Context:
             self._check(s)
         return info
 
+    def dd_solve_gcr(self, f, x, where=DD_HOST, tol=1e-10, m=16, max_iter=1000, i_schwarz=16, i_domain=4,
+                     storage_prec=DD_PREC_FP16, check=True, threads_per_site=0, additive=0):
+        p = dd_solve_params(tol, m, 0, max_iter,
+                            dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site, additive))
+        info = dd_solve_info()
+        s = lib().dd_solve_gcr(self._h, _ptr(f), _ptr(x), where, C.byref(p), C.byref(info))
+        if check:
+            self._check(s)
+        return info
+
     def dd_solve_bicgstab(self, f, x, where=DD_HOST, tol=1e-10, max_iter=10000, precision=DD_PREC_FP64,
                           inner_tol=1e-5, check=True):
         p = dd_bicgstab_params(tol, max_iter, precision, inner_tol)
@@ -229,6 +243,22 @@ def dd_fp32_peak(duration_ms=2000):
     return b.value, s.value
 
 
+def dd_solve_lattices(ctxs, fs, xs, nrhs=1, where=DD_HOST, tol=1e-10, m=16, k=0, max_iter=1000, i_schwarz=16,
+                      i_domain=4, check=True):
+    """Lockstep solves over several lattices (FP16-storage Schwarz, one launch per
+    half-sweep over all of them); fs[l] / xs[l]: nrhs canonical FP64 fields of lattice l."""
+    n = len(ctxs)
+    hs = (C.c_void_p * n)(*[c._h.value for c in ctxs])
+    pf = (C.c_void_p * n)(*[_ptr(a) for a in fs])
+    px = (C.c_void_p * n)(*[_ptr(a) for a in xs])
+    p = dd_solve_params(tol, m, k, max_iter, dd_sap_params(i_schwarz, i_domain, DD_PREC_FP16, 0, 0))
+    info = dd_solve_info()
+    s = lib().dd_solve_lattices(hs, n, pf, px, int(nrhs), where, C.byref(p), C.byref(info))
+    if check and s != DD_OK:
+        raise DDError(s, lib().dd_last_error(ctxs[0]._h).decode())
+    return info
+
+
 def dd_load_model(n_domains_per_colour, slots):
     return lib().dd_load_model(int(n_domains_per_colour), int(slots))
 
@@ -248,3 +278,24 @@ def dd_deflate_host(Hbar, c, y, k):
     if s != DD_OK:
         raise DDError(s, "dd_deflate_host failed")
     return P, Hn[:k + 1], cn, th
+
+
+def dd_deflate_device(Hbar, c, y, k):
+    """The deflated restart's small dense step on the device (one warp), as dd_solve runs
+    it; returns (P, Hn, cn, theta, kernel ms) as numpy arrays."""
+    import torch
+    m = Hbar.shape[1]
+    dev = lambda a: torch.view_as_real(torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128))).cuda()
+    H = dev(Hbar.T.copy())   # column-major
+    cc, yy = dev(c), dev(y)
+    P = torch.zeros(k + 1, m + 1, 2, dtype=torch.float64, device="cuda")
+    Hn = torch.zeros(k, m + 1, 2, dtype=torch.float64, device="cuda")
+    cn = torch.zeros(k + 1, 2, dtype=torch.float64, device="cuda")
+    th = torch.zeros(m, 2, dtype=torch.float64, device="cuda")
+    ms = C.c_double()
+    s = lib().dd_deflate_device(m, k, H.data_ptr(), cc.data_ptr(), yy.data_ptr(), P.data_ptr(), Hn.data_ptr(),
+                                cn.data_ptr(), th.data_ptr(), C.byref(ms))
+    if s != DD_OK:
+        raise DDError(s, "dd_deflate_device failed")
+    cplx = lambda t: torch.view_as_complex(t.cpu()).numpy()
+    return cplx(P).T, cplx(Hn).T[:k + 1], cplx(cn), cplx(th), ms.value

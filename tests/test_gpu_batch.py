@@ -125,3 +125,29 @@ def test_lockstep_solve_equals_sequential(prec, monkeypatch):
     assert not np.any(x_lock[4])
     assert info_l.true_rel_residual <= 1e-10 and info_l.restarts > 0
     assert abs(info_l.iterations - info_s.iterations) <= 2 * len(fs)
+
+
+def test_lockstep_solve_over_lattices():
+    """Three lattices of different volume, two right-hand sides each (one a point source),
+    solved in lockstep by dd_solve_lattices: one Schwarz launch per half-sweep covers every
+    lattice's unconverged (domain, right-hand side) work.  Every true residual, recomputed
+    by the oracle in FP64, is <= 1e-10, and each solution equals the single-lattice
+    dd_solve of the same source to 1e-8."""
+    from oracle import solve as S
+    shapes = [((8, 8, 8, 8), 0.1250, 41), ((8, 8, 8, 16), 0.1300, 42), ((16, 8, 8, 8), 0.1320, 43)]
+    kw = dict(tol=1e-10, m=12, k=4, max_iter=2000, i_schwarz=2, i_domain=4)
+    ctxs, fs, xs, Us = [], [], [], []
+    for dims, kappa, seed in shapes:
+        U = gauge(dims, 0.5, seed, ape=2)
+        ctxs.append(ctx_for(dims, (4, 4, 4, 4), U, kappa, 1.5))
+        fs.append(np.stack([synth.gaussian_source(dims, seed + 1), synth.point_sources(dims)[3]]))
+        xs.append(np.zeros_like(fs[-1]))
+        Us.append(U)
+    info = dd.dd_solve_lattices(ctxs, fs, xs, nrhs=2, **kw)
+    assert info.true_rel_residual <= 1e-10
+    for (dims, kappa, _), c, U, f, x in zip(shapes, ctxs, Us, fs, xs):
+        for r in range(2):
+            assert S.true_residual(U, x[r], f[r], kappa, 1.5) <= 1e-10
+            x1 = np.zeros_like(f[r])
+            c.dd_solve(f[r], x1, storage_prec=dd.DD_PREC_FP16, **kw)
+            assert rel(x[r], x1) <= 1e-8

@@ -155,3 +155,20 @@ def test_solve_with_additive_schwarz():
     x = np.zeros_like(f)
     info = c.dd_solve(f, x, tol=w.tol, m=w.m, k=w.k, i_schwarz=w.i_schwarz, i_domain=w.i_domain, additive=1)
     assert S.true_residual(U, x, f, w.kappa, w.csw) <= 1e-10 and info.true_rel_residual <= 1e-10
+
+
+@pytest.mark.parametrize("additive", [0, 1], ids=["multiplicative", "additive"])
+def test_gcr_solve(additive):
+    """Flexible GCR around the Schwarz preconditioner (SAP-GCR, Sec. V): the oracle's FP64
+    true residual <= 1e-10 and the same solution as FGMRES-DR within the conditioning."""
+    w = synth.WORKLOADS["8^4"]
+    U = synth.make_gauge(w).numpy()
+    f = synth.make_sources(w)[0]
+    c = ctx_for(w.dims, w.domain, U, w.kappa, w.csw)
+    x = np.zeros_like(f)
+    info = c.dd_solve_gcr(f, x, tol=1e-10, m=12, max_iter=500, i_schwarz=w.i_schwarz, i_domain=w.i_domain,
+                          additive=additive)
+    assert S.true_residual(U, x, f, w.kappa, w.csw) <= 1e-10 and info.true_rel_residual <= 1e-10
+    xd = np.zeros_like(f)
+    c.dd_solve(f, xd, tol=1e-12, m=w.m, k=w.k, i_schwarz=w.i_schwarz, i_domain=w.i_domain)
+    assert rel(x, xd) <= 1e-8
