@@ -70,95 +70,57 @@ __global__ void __launch_bounds__(256) apply_A_kernel(Geom g, LinkPtr<T> U, Clov
   out.store(g, s, y);
 }
 
-// ------------------------------------------------------------------ FP32, two threads per site
-// The operator in FP32 with two threads per site: in a block of 256 threads, warps 0-3
-// take the hops along x and y of 128 consecutive sites and warps 4-7 those along z and t
-// of the same sites.  Each thread then keeps one chirality half (spins 2h, 2h+1): it hands
-// the other half of its partial hop sum to its partner through shared memory, applies the
-// clover block of its half (the clover acts within a chirality) and writes its half of
-// the output.  Per thread this halves the serial chain of loads, so twice as many
-// threads (and bytes) are in flight per SM as with one thread per site; every byte is
-// still read once.  SHAPE: the domain shape as compile-time constants (0: run time).
+// ------------------------------------------------------------------ FP32, shape known at compile time
+// The same one-thread-per-site operator for FP32 fields with the domain shape as
+// compile-time constants (SHAPE 1: 8x4x4x4, 2: 4x4x4x4): the site decoding and every
+// neighbour and unit address then fold into shifts and immediate offsets, which takes the
+// integer work off the issue slots that the loads need.
 template <int SHAPE>
-__global__ void __launch_bounds__(256, 4) apply_A_pair_kernel(Geom g0, LinkPtr<float> U, const float4* __restrict__ C,
-                                                                SpinorPtr<float> in, float4* __restrict__ out,
-                                                                const float4* __restrict__ f) {
-  __shared__ float4 xch[2][3][128];   // [half handed over][unit][site]
+__global__ void __launch_bounds__(256) apply_A_shape_kernel(Geom g0, LinkPtr<float> U, CloverPtr<float> C,
+                                                            SpinorPtr<float> in, SpinorPtr<float> out,
+                                                            SpinorPtr<float> f, int residual) {
   const Geom g = fixed_shape<SHAPE>(g0);
-  const int h = threadIdx.x >> 7, i = threadIdx.x & 127;
-  const long long s = blockIdx.x * 128LL + i;   // V is a multiple of 128: no partial blocks
-  const Site st = decode(g, s);
-  Spinor<float> acc;
-  zero(acc);
-  if (h == 0) {
-    hop_pair<0, float>(g, st, s, in, U, acc);
-    hop_pair<1, float>(g, st, s, in, U, acc);
-  } else {
-    hop_pair<2, float>(g, st, s, in, U, acc);
-    hop_pair<3, float>(g, st, s, in, U, acc);
-  }
-  // chirality half 1 - h goes to the partner, half h stays
+  long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  Site st = decode(g, s);
+  Spinor<float> hop;
+  zero(hop);
+  hop_pair<0, float>(g, st, s, in, U, hop);
+  hop_pair<1, float>(g, st, s, in, U, hop);
+  hop_pair<2, float>(g, st, s, in, U, hop);
+  hop_pair<3, float>(g, st, s, in, U, hop);
+  Spinor<float> x, y;
+  in.load(g, s, x);
+  float m[72];
+  C.load(g, s, m);
+  clover_mul(m, x, y);
 #pragma unroll
-  for (int u = 0; u < 3; ++u) {
-    const int k = 6 * (1 - h) + 2 * u;
-    xch[1 - h][u][i] = make_float4(acc.c[k / 3][k % 3].re, acc.c[k / 3][k % 3].im, acc.c[(k + 1) / 3][(k + 1) % 3].re,
-                                   acc.c[(k + 1) / 3][(k + 1) % 3].im);
-  }
-  __syncthreads();
-  cx<float> hop[6], x[6], y[6];
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-  for (int u = 0; u < 3; ++u) {
-    const int k = 6 * h + 2 * u;
-    const float4 q = xch[h][u][i];
-    hop[2 * u] = acc.c[k / 3][k % 3] + mk(q.x, q.y);
-    hop[2 * u + 1] = acc.c[(k + 1) / 3][(k + 1) % 3] + mk(q.z, q.w);
-    const float4 v = in.p[unit_addr(g, s, 6, 3 * h + u)];
-    x[2 * u] = mk(v.x, v.y);
-    x[2 * u + 1] = mk(v.z, v.w);
-  }
-  float m[36];
+    for (int b = 0; b < 3; ++b) y.c[a][b] = y.c[a][b] - 0.5f * hop.c[a][b];
+  if (residual) {
+    Spinor<float> fv;
+    f.load(g, s, fv);
 #pragma unroll
-  for (int u = 0; u < 9; ++u) {
-    const float4 v = __ldg(C + unit_addr(g, s, 18, 9 * h + u));
-    m[4 * u] = v.x;
-    m[4 * u + 1] = v.y;
-    m[4 * u + 2] = v.z;
-    m[4 * u + 3] = v.w;
-  }
-  clover_block_mul(m, x, y);
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-  for (int u = 0; u < 3; ++u) {
-    cx<float> a = y[2 * u] - 0.5f * hop[2 * u], b = y[2 * u + 1] - 0.5f * hop[2 * u + 1];
-    const long long q = unit_addr(g, s, 6, 3 * h + u);
-    if (f) {
-      const float4 fv = f[q];
-      a = mk(fv.x, fv.y) - a;
-      b = mk(fv.z, fv.w) - b;
-    }
-    out[q] = make_float4(a.re, a.im, b.re, b.im);
+      for (int b = 0; b < 3; ++b) y.c[a][b] = fv.c[a][b] - y.c[a][b];
   }
-}
-
-static void launch_pair_f32(const Geom& g, GaugeView U, CloverView C, FieldView in, FieldView out, const FieldView* f,
-                            cudaStream_t st) {
-  const unsigned nb = (unsigned)(g.V / 128);
-  const LinkPtr<float> L{(const float2*)U.links};
-  const SpinorPtr<float> vin{(float4*)in.data};
-  const float4* cm = (const float4*)C.m;
-  float4* o = (float4*)out.data;
-  const float4* fp = f ? (const float4*)f->data : nullptr;
-  switch (domain_shape_id(g)) {
-    case 1: apply_A_pair_kernel<1><<<nb, 256, 0, st>>>(g, L, cm, vin, o, fp); break;
-    case 2: apply_A_pair_kernel<2><<<nb, 256, 0, st>>>(g, L, cm, vin, o, fp); break;
-    default: apply_A_pair_kernel<0><<<nb, 256, 0, st>>>(g, L, cm, vin, o, fp); break;
-  }
+  out.store(g, s, y);
 }
 
 void launch_apply_A(const Geom& g, GaugeView U, CloverView C, FieldView in, FieldView out, const FieldView* f,
                     cudaStream_t st) {
-  if (in.prec == P32 && g.V % 128 == 0) return launch_pair_f32(g, U, C, in, out, f, st);
   unsigned nb = (unsigned)((g.V + 255) / 256);
   int res = f != nullptr;
+  if (in.prec == P32 && domain_shape_id(g) != 0) {
+    const LinkPtr<float> L{(const float2*)U.links};
+    const CloverPtr<float> Cp{(const float4*)C.m};
+    const SpinorPtr<float> vi{(float4*)in.data}, vo{(float4*)out.data}, fi{res ? (float4*)f->data : nullptr};
+    if (domain_shape_id(g) == 1) apply_A_shape_kernel<1><<<nb, 256, 0, st>>>(g, L, Cp, vi, vo, fi, res);
+    else apply_A_shape_kernel<2><<<nb, 256, 0, st>>>(g, L, Cp, vi, vo, fi, res);
+    return;
+  }
   if (in.prec == P64) {
     SpinorPtr<double> fi{res ? (double2*)f->data : nullptr};
     apply_A_kernel<double><<<nb, 256, 0, st>>>(g, LinkPtr<double>{(const double2*)U.links},

@@ -987,7 +987,7 @@ __device__ inline void hops_half_mask(int h, const Geom& g, unsigned fwd, unsign
 // scaled by a power of two, 16 / 2^ceil(log2 max|r|), before it enters the work buffers,
 // and everything that leaves them (the new residual, delta) is scaled back.  The MR
 // iteration is invariant under that scaling and powers of two are exact in FP32.
-template <typename MT, typename VT, bool MSMEM, bool H2, int SHAPE = 0>
+template <typename MT, typename VT, bool MSMEM, bool H2, int SHAPE = 0, bool PERSIST = false>
 __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   // hop phases use g (constant domain fields when SHAPE != 0); the face code, which indexes
   // the face offsets at run time, reads the kernel parameters a.g directly
@@ -1001,22 +1001,8 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   const int h = tid >= Hd;          // MR phases: chirality half and hop directions; ends: parity
   const int i = tid - h * Hd;
 
-  // this CTA's colour and its index among the domains of that colour (the additive form
-  // runs both colours in one launch, colour 0 first)
-  const int colour = a.both_colours ? (cta >= (g.ND >> 1)) : a.colour;
-  const int cidx = a.both_colours ? cta - colour * (g.ND >> 1) : cta;
-  int n[4];
-  {
-    int hx = g.N[0] >> 1;
-    int j = cidx % hx;
-    int row = cidx / hx;
-    n[1] = row % g.N[1];
-    n[2] = (row / g.N[1]) % g.N[2];
-    n[3] = row / (g.N[1] * g.N[2]);
-    n[0] = 2 * j + ((colour + n[1] + n[2] + n[3]) & 1);
-  }
-  const long long d = n[0] + (long long)g.dstride[1] * n[1] + (long long)g.dstride[2] * n[2] +
-                      (long long)g.dstride[3] * n[3];
+  // Domain-independent set-up: this thread's sites (even site i and odd site i), their
+  // local coordinates, hop masks and the shared-memory regions.
   const size_t lk_elems = (size_t)4 * 9 * Vd;
   const size_t lk_bytes = (size_t)MatBlock<MT>::link_bytes_per_site * Vd;
   const size_t cm_bytes = (size_t)MatBlock<MT>::mat_bytes_per_site * Vd;
@@ -1025,32 +1011,12 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   M.Vd = Vd;
   typedef typename std::remove_const<typename std::remove_pointer<decltype(M.lk)>::type>::type LkT;
   typedef typename std::remove_const<typename std::remove_pointer<decltype(M.cm)>::type>::type CmT;
-  const LkT* glk = reinterpret_cast<const LkT*>(a.links) + d * lk_elems;
-  const CmT* gcm = reinterpret_cast<const CmT*>(a.smat) + d * (cm_bytes / sizeof(CmT));
-  float4* sE;
+  float4* sE = MSMEM ? reinterpret_cast<float4*>(sbase + lk_bytes + cm_bytes) : smem;
+  float4* sO = sE + 6 * Hd;
   if (MSMEM) {
     M.lk = reinterpret_cast<const LkT*>(sbase);
     M.cm = reinterpret_cast<const CmT*>(sbase + lk_bytes);
-    sE = reinterpret_cast<float4*>(sbase + lk_bytes + cm_bytes);
-    if (tid == 0) {
-      mbar_init(&mbar, 1);
-      mbar_init(&mbar_inj, 1);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes));
-      bulk_g2s(sbase, glk, (uint32_t)lk_bytes, &mbar);
-      bulk_g2s(sbase + lk_bytes, gcm, (uint32_t)cm_bytes, &mbar);
-      // test hook: bytes that nobody sends, on a barrier of their own
-      if (a.extra_tx) mbar_expect_tx(&mbar_inj, a.extra_tx);
-    }
-  } else {
-    M.lk = glk;
-    M.cm = gcm;
-    sE = smem;
   }
-  float4* sO = sE + 6 * Hd;
-
   int le[4], lo[4];
   local_coords(g, 0, i, le);
   local_coords(g, 1, i, lo);
@@ -1060,9 +1026,61 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   inside_masks(g, le, fe, be);
   inside_masks(g, lo, fo, bo);
   const int r_e = i, r_o = Hd + i;
-  const long long s_site = (d << g.lgVd) + h * Hd + i;
   const int r_site = h * Hd + i;
   const unsigned fs = h ? fo : fe, bs = h ? bo : be;
+
+  // The domains of this launch (the additive form runs both colours, colour 0 first):
+  // one per CTA, or with PERSIST every gridDim.x-th from this CTA's index on.  Domain k's
+  // links and Schwarz matrices arrive on the barrier in phase k & 1; with PERSIST the next
+  // domain's matrices are copied in as soon as the current one's last MR phase is done
+  // and its links after the face output, so the copies overlap the end of one domain and
+  // the start of the next.
+  const int ndom = a.both_colours ? g.ND : (g.ND >> 1);
+  const int dstep = PERSIST ? (int)gridDim.x : ndom;
+  auto domain_of = [&](int k, int* n, int* colour_out) -> long long {
+    const int colour = a.both_colours ? (k >= (g.ND >> 1)) : a.colour;
+    const int cidx = a.both_colours ? k - colour * (g.ND >> 1) : k;
+    int hx = g.N[0] >> 1;
+    int j = cidx % hx;
+    int row = cidx / hx;
+    n[1] = row % g.N[1];
+    n[2] = (row / g.N[1]) % g.N[2];
+    n[3] = row / (g.N[1] * g.N[2]);
+    n[0] = 2 * j + ((colour + n[1] + n[2] + n[3]) & 1);
+    *colour_out = colour;
+    return n[0] + (long long)g.dstride[1] * n[1] + (long long)g.dstride[2] * n[2] + (long long)g.dstride[3] * n[3];
+  };
+  auto glk_of = [&](long long dd) { return reinterpret_cast<const LkT*>(a.links) + dd * lk_elems; };
+  auto gcm_of = [&](long long dd) { return reinterpret_cast<const CmT*>(a.smat) + dd * (cm_bytes / sizeof(CmT)); };
+  if (MSMEM) {
+    if (tid == 0) {
+      mbar_init(&mbar, 1);
+      mbar_init(&mbar_inj, 1);
+    }
+    __syncthreads();
+    if (tid == 0 && cta < ndom) {
+      int n0[4], c0;
+      const long long d0 = domain_of(cta, n0, &c0);
+      mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes));
+      bulk_g2s(sbase, glk_of(d0), (uint32_t)lk_bytes, &mbar);
+      bulk_g2s(sbase + lk_bytes, gcm_of(d0), (uint32_t)cm_bytes, &mbar);
+      // test hook: bytes that nobody sends, on a barrier of their own
+      if (a.extra_tx) mbar_expect_tx(&mbar_inj, a.extra_tx);
+    }
+  }
+  uint32_t phase = 0;
+#pragma unroll 1
+  for (int dom = cta; dom < ndom; dom += dstep, phase ^= 1u) {
+  int n[4], colour;
+  const long long d = domain_of(dom, n, &colour);
+  const bool has_next = PERSIST && dom + dstep < ndom;
+  int n_next[4], colour_next;
+  const long long d_next = has_next ? domain_of(dom + dstep, n_next, &colour_next) : 0;
+  if (!MSMEM) {
+    M.lk = glk_of(d);
+    M.cm = gcm_of(d);
+  }
+  const long long s_site = (d << g.lgVd) + h * Hd + i;
 
   // Right-hand sides share the staged matrices; each has its own input, output and state.
 #pragma unroll 1
@@ -1081,12 +1099,12 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
     else if (h == 0) rst.load(d, Hd, i, r);
     else zero(r);
     if (MSMEM && rhs == 0) {
-      bool ok = mbar_wait(&mbar, 0, a.wait_ns);
-      if (a.extra_tx) ok = mbar_wait(&mbar_inj, 0, a.wait_ns) && ok;
+      bool ok = mbar_wait(&mbar, phase, a.wait_ns);
+      if (a.extra_tx && dom == cta) ok = mbar_wait(&mbar_inj, 0, a.wait_ns) && ok;
       if (__syncthreads_or(!ok)) {
         // as in sap_kernel: flag, then a bounded wait for the real copies before leaving
         if (tid == 0) atomicExch(a.err, 1);
-        mbar_wait(&mbar, 0, a.wait_ns);
+        mbar_wait(&mbar, phase, a.wait_ns);
         return;
       }
     }
@@ -1221,6 +1239,11 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
     }
     __syncthreads();
   }
+  // the Schwarz matrices are not read again for this domain: start the next one's copy
+  if (MSMEM && has_next && rhs == a.nrhs - 1 && tid == 0) {
+    mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes));
+    bulk_g2s(sbase + lk_bytes, gcm_of(d_next), (uint32_t)cm_bytes, &mbar);
+  }
   if (!a.last) {
     if constexpr (H2) {
 #pragma unroll
@@ -1265,11 +1288,16 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   }
   __syncthreads();   // the work buffers are reused by the next right-hand side
   }
+  // the links are not read again for this domain: start the next one's copy
+  if (MSMEM && has_next && tid == 0) bulk_g2s(sbase, glk_of(d_next), (uint32_t)lk_bytes, &mbar);
+  }
 }
 
+// With the matrices staged in shared memory the kernel is persistent: a grid of as many
+// CTAs as fit on the GPU at once, each taking every gridDim.x-th domain.
 template <typename MT, typename VT, bool MSMEM, bool H2, int SHAPE>
 __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArgs a) {
-  sap_pair_body<MT, VT, MSMEM, H2, SHAPE>(a, blockIdx.x);
+  sap_pair_body<MT, VT, MSMEM, H2, SHAPE, MSMEM>(a, blockIdx.x);
 }
 
 // Several lattices of the same domain shape in one launch: the grid is the concatenation
@@ -1326,6 +1354,14 @@ static void launch_pair(const SapArgs& a, int grid, size_t smem, cudaStream_t st
     cudaFuncSetAttribute(sap_kernel_pair<MT, VT, MSMEM, H2, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          smem_optin() - 4096);
     configured = 1;
+  }
+  if (MSMEM) {   // persistent: at most as many CTAs as are resident at once
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sap_kernel_pair<MT, VT, MSMEM, H2, SHAPE>, 2 * a.g.Hd, smem);
+    const int resident = sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > resident) grid = resident;
   }
   sap_kernel_pair<MT, VT, MSMEM, H2, SHAPE><<<grid, 2 * a.g.Hd, smem, st>>>(a);
 }

@@ -32,6 +32,8 @@ def test_device_deflation_matches_oracle_and_host(n, m, k, seed):
         assert np.linalg.norm(proj - Gk) < 1e-9 * np.linalg.norm(Gk)
         assert np.allclose(P @ cn, c - Hbar @ y, atol=1e-12 * np.linalg.norm(c))
         assert np.allclose(Hn, P.conj().T @ Hbar @ P[:mm, :k], atol=1e-12 * np.linalg.norm(Hbar))
+        # the host run of the same code: same Ritz values, same subspace (each eigenvector is
+        # fixed only up to a phase, which rounding may settle differently)
         Ph, Hnh, cnh, thh = dd.dd_deflate_host(Hbar, c, y, k)
         assert np.allclose(th, thh, rtol=1e-9, atol=1e-12)
-        assert np.linalg.norm(P - Ph) <= 1e-8 * np.linalg.norm(Ph)
+        assert np.linalg.norm(P @ P.conj().T - Ph @ Ph.conj().T) <= 1e-8 * (k + 1)
