@@ -928,39 +928,49 @@ __device__ inline void block_apply_pair(const MatBlock<MT>& M, int r, int h, con
 template <int MU, typename MT, bool H2>
 __device__ inline void hop_mask_mu(const Geom& g, unsigned fwd, unsigned bwd, int lex, int p, int r_self,
                                    const float4* src, const MatBlock<MT>& M, Spinor<float>& acc) {
-  Spinor<float> psi;
-  Half<float> h, uh;
-  if ((fwd >> MU) & 1u) {
-    int j = (lex + g.bstride[MU]) >> 1;
-    ld_buf(src, g.Hd, j, psi);
-    project<MU, -1>(psi, h);
-    if constexpr (H2) {
+  const bool hf = (fwd >> MU) & 1u, hb = (bwd >> MU) & 1u;
+  if constexpr (!H2) {
+    // FP32 products: both hops are computed for every site (a missing neighbour reads the
+    // site's own index, in bounds) and added only where they exist, so the two hops'
+    // loads and products interleave instead of sitting in separate branches
+    const int jf = hf ? (lex + g.bstride[MU]) >> 1 : (lex >> 1);
+    const int jb = hb ? (lex - g.bstride[MU]) >> 1 : (lex >> 1);
+    Spinor<float> psf, psb;
+    Half<float> hfw, hbw, uf, ub;
+    ld_buf(src, g.Hd, jf, psf);
+    ld_buf(src, g.Hd, jb, psb);
+    project<MU, -1>(psf, hfw);
+    project<MU, +1>(psb, hbw);
+    Link<float> Lf, Lb;
+    M.link(MU, r_self, Lf);
+    M.link(MU, (1 - p) * g.Hd + jb, Lb);
+    su3_mul(Lf, hfw, uf);
+    su3_dag_mul(Lb, hbw, ub);
+    if (hf) accum_recon<MU, -1>(acc, uf);
+    if (hb) accum_recon<MU, +1>(acc, ub);
+  } else {
+    Spinor<float> psi;
+    Half<float> h, uh;
+    if (hf) {
+      int j = (lex + g.bstride[MU]) >> 1;
+      ld_buf(src, g.Hd, j, psi);
+      project<MU, -1>(psi, h);
       HalfH2 hh, oh;
       pack_h2(h, hh);
       su3_h2<false>(reinterpret_cast<const __half2*>(M.lk) + MU * 9 * g.Vd + r_self, g.Vd, hh, oh);
       unpack_h2(oh, uh);
-    } else {
-      Link<float> L;
-      M.link(MU, r_self, L);
-      su3_mul(L, h, uh);
+      accum_recon<MU, -1>(acc, uh);
     }
-    accum_recon<MU, -1>(acc, uh);
-  }
-  if ((bwd >> MU) & 1u) {
-    int j = (lex - g.bstride[MU]) >> 1;
-    ld_buf(src, g.Hd, j, psi);
-    project<MU, +1>(psi, h);
-    if constexpr (H2) {
+    if (hb) {
+      int j = (lex - g.bstride[MU]) >> 1;
+      ld_buf(src, g.Hd, j, psi);
+      project<MU, +1>(psi, h);
       HalfH2 hh, oh;
       pack_h2(h, hh);
       su3_h2<true>(reinterpret_cast<const __half2*>(M.lk) + MU * 9 * g.Vd + (1 - p) * g.Hd + j, g.Vd, hh, oh);
       unpack_h2(oh, uh);
-    } else {
-      Link<float> L;
-      M.link(MU, (1 - p) * g.Hd + j, L);
-      su3_dag_mul(L, h, uh);
+      accum_recon<MU, +1>(acc, uh);
     }
-    accum_recon<MU, +1>(acc, uh);
   }
 }
 
@@ -987,7 +997,7 @@ __device__ inline void hops_half_mask(int h, const Geom& g, unsigned fwd, unsign
 // scaled by a power of two, 16 / 2^ceil(log2 max|r|), before it enters the work buffers,
 // and everything that leaves them (the new residual, delta) is scaled back.  The MR
 // iteration is invariant under that scaling and powers of two are exact in FP32.
-template <typename MT, typename VT, bool MSMEM, bool H2, int SHAPE = 0, bool PERSIST = false>
+template <typename MT, typename VT, bool MSMEM, bool H2, int SHAPE = 0>
 __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   // hop phases use g (constant domain fields when SHAPE != 0); the face code, which indexes
   // the face offsets at run time, reads the kernel parameters a.g directly
@@ -1029,17 +1039,15 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   const int r_site = h * Hd + i;
   const unsigned fs = h ? fo : fe, bs = h ? bo : be;
 
-  // The domains of this launch (the additive form runs both colours, colour 0 first):
-  // one per CTA, or with PERSIST every gridDim.x-th from this CTA's index on.  Domain k's
-  // links and Schwarz matrices arrive on the barrier in phase k & 1; with PERSIST the next
-  // domain's matrices are copied in as soon as the current one's last MR phase is done
-  // and its links after the face output, so the copies overlap the end of one domain and
-  // the start of the next.
+  // This CTA's domain: the cta-th of the launch (the additive form runs both colours, colour
+  // 0 first).  Its links and Schwarz matrices are copied into shared memory on an mbarrier
+  // while the residual is loaded.
   const int ndom = a.both_colours ? g.ND : (g.ND >> 1);
-  const int dstep = PERSIST ? (int)gridDim.x : ndom;
-  auto domain_of = [&](int k, int* n, int* colour_out) -> long long {
-    const int colour = a.both_colours ? (k >= (g.ND >> 1)) : a.colour;
-    const int cidx = a.both_colours ? k - colour * (g.ND >> 1) : k;
+  int n[4], colour;
+  long long d;
+  {
+    colour = a.both_colours ? (cta >= (g.ND >> 1)) : a.colour;
+    const int cidx = a.both_colours ? cta - colour * (g.ND >> 1) : cta;
     int hx = g.N[0] >> 1;
     int j = cidx % hx;
     int row = cidx / hx;
@@ -1047,38 +1055,27 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
     n[2] = (row / g.N[1]) % g.N[2];
     n[3] = row / (g.N[1] * g.N[2]);
     n[0] = 2 * j + ((colour + n[1] + n[2] + n[3]) & 1);
-    *colour_out = colour;
-    return n[0] + (long long)g.dstride[1] * n[1] + (long long)g.dstride[2] * n[2] + (long long)g.dstride[3] * n[3];
-  };
-  auto glk_of = [&](long long dd) { return reinterpret_cast<const LkT*>(a.links) + dd * lk_elems; };
-  auto gcm_of = [&](long long dd) { return reinterpret_cast<const CmT*>(a.smat) + dd * (cm_bytes / sizeof(CmT)); };
+    d = n[0] + (long long)g.dstride[1] * n[1] + (long long)g.dstride[2] * n[2] + (long long)g.dstride[3] * n[3];
+  }
+  const LkT* glk = reinterpret_cast<const LkT*>(a.links) + d * lk_elems;
+  const CmT* gcm = reinterpret_cast<const CmT*>(a.smat) + d * (cm_bytes / sizeof(CmT));
+  if (cta >= ndom) return;
   if (MSMEM) {
     if (tid == 0) {
       mbar_init(&mbar, 1);
       mbar_init(&mbar_inj, 1);
     }
     __syncthreads();
-    if (tid == 0 && cta < ndom) {
-      int n0[4], c0;
-      const long long d0 = domain_of(cta, n0, &c0);
+    if (tid == 0) {
       mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes));
-      bulk_g2s(sbase, glk_of(d0), (uint32_t)lk_bytes, &mbar);
-      bulk_g2s(sbase + lk_bytes, gcm_of(d0), (uint32_t)cm_bytes, &mbar);
+      bulk_g2s(sbase, glk, (uint32_t)lk_bytes, &mbar);
+      bulk_g2s(sbase + lk_bytes, gcm, (uint32_t)cm_bytes, &mbar);
       // test hook: bytes that nobody sends, on a barrier of their own
       if (a.extra_tx) mbar_expect_tx(&mbar_inj, a.extra_tx);
     }
-  }
-  uint32_t phase = 0;
-#pragma unroll 1
-  for (int dom = cta; dom < ndom; dom += dstep, phase ^= 1u) {
-  int n[4], colour;
-  const long long d = domain_of(dom, n, &colour);
-  const bool has_next = PERSIST && dom + dstep < ndom;
-  int n_next[4], colour_next;
-  const long long d_next = has_next ? domain_of(dom + dstep, n_next, &colour_next) : 0;
-  if (!MSMEM) {
-    M.lk = glk_of(d);
-    M.cm = gcm_of(d);
+  } else {
+    M.lk = glk;
+    M.cm = gcm;
   }
   const long long s_site = (d << g.lgVd) + h * Hd + i;
 
@@ -1099,12 +1096,12 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
     else if (h == 0) rst.load(d, Hd, i, r);
     else zero(r);
     if (MSMEM && rhs == 0) {
-      bool ok = mbar_wait(&mbar, phase, a.wait_ns);
-      if (a.extra_tx && dom == cta) ok = mbar_wait(&mbar_inj, 0, a.wait_ns) && ok;
+      bool ok = mbar_wait(&mbar, 0, a.wait_ns);
+      if (a.extra_tx) ok = mbar_wait(&mbar_inj, 0, a.wait_ns) && ok;
       if (__syncthreads_or(!ok)) {
         // as in sap_kernel: flag, then a bounded wait for the real copies before leaving
         if (tid == 0) atomicExch(a.err, 1);
-        mbar_wait(&mbar, phase, a.wait_ns);
+        mbar_wait(&mbar, 0, a.wait_ns);
         return;
       }
     }
@@ -1239,11 +1236,6 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
     }
     __syncthreads();
   }
-  // the Schwarz matrices are not read again for this domain: start the next one's copy
-  if (MSMEM && has_next && rhs == a.nrhs - 1 && tid == 0) {
-    mbar_expect_tx(&mbar, (uint32_t)(lk_bytes + cm_bytes));
-    bulk_g2s(sbase + lk_bytes, gcm_of(d_next), (uint32_t)cm_bytes, &mbar);
-  }
   if (!a.last) {
     if constexpr (H2) {
 #pragma unroll
@@ -1288,16 +1280,14 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   }
   __syncthreads();   // the work buffers are reused by the next right-hand side
   }
-  // the links are not read again for this domain: start the next one's copy
-  if (MSMEM && has_next && tid == 0) bulk_g2s(sbase, glk_of(d_next), (uint32_t)lk_bytes, &mbar);
-  }
 }
 
-// With the matrices staged in shared memory the kernel is persistent: a grid of as many
-// CTAs as fit on the GPU at once, each taking every gridDim.x-th domain.
+// One CTA per domain (measured faster on GB300 than a persistent grid walking its domains
+// with the next domain's copies in flight: the round-robin tail and the extra live state
+// cost more than the overlap gains).
 template <typename MT, typename VT, bool MSMEM, bool H2, int SHAPE>
 __global__ void __launch_bounds__(2 * SAP_MAX_THREADS, 1) sap_kernel_pair(SapArgs a) {
-  sap_pair_body<MT, VT, MSMEM, H2, SHAPE, MSMEM>(a, blockIdx.x);
+  sap_pair_body<MT, VT, MSMEM, H2, SHAPE>(a, blockIdx.x);
 }
 
 // Several lattices of the same domain shape in one launch: the grid is the concatenation
@@ -1354,14 +1344,6 @@ static void launch_pair(const SapArgs& a, int grid, size_t smem, cudaStream_t st
     cudaFuncSetAttribute(sap_kernel_pair<MT, VT, MSMEM, H2, SHAPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          smem_optin() - 4096);
     configured = 1;
-  }
-  if (MSMEM) {   // persistent: at most as many CTAs as are resident at once
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sap_kernel_pair<MT, VT, MSMEM, H2, SHAPE>, 2 * a.g.Hd, smem);
-    const int resident = sms * (per_sm > 0 ? per_sm : 1);
-    if (grid > resident) grid = resident;
   }
   sap_kernel_pair<MT, VT, MSMEM, H2, SHAPE><<<grid, 2 * a.g.Hd, smem, st>>>(a);
 }

@@ -179,51 +179,88 @@ DD_HD inline void hess_solve(const Team& T, const zd* A, int n, int ld, const in
   upper_solve(T, A, n, ld, x);
 }
 
-// ---------------------------------------------------------------- eigenvalues
+// ---------------------------------------------------------------- FP32 eigenvalue estimates
+// The QR sweeps that locate the harmonic Ritz values run in FP32: each rotation is a short
+// chain of square roots and divisions, and in FP64 on the device (GB300's FP64 rate is a
+// small fraction of its FP32 rate) that chain dominates the whole restart.  The values only
+// order the candidates and shift the inverse iteration, which then computes every kept
+// vector and its Rayleigh quotient in FP64.
+struct zf { float re, im; };
+DD_HD inline zf Zf(float a, float b = 0.f) { zf z; z.re = a; z.im = b; return z; }
+DD_HD inline zf operator+(zf a, zf b) { return Zf(a.re + b.re, a.im + b.im); }
+DD_HD inline zf operator-(zf a, zf b) { return Zf(a.re - b.re, a.im - b.im); }
+DD_HD inline zf operator*(zf a, zf b) { return Zf(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+DD_HD inline zf operator*(float s, zf a) { return Zf(s * a.re, s * a.im); }
+DD_HD inline zf conj(zf a) { return Zf(a.re, -a.im); }
+DD_HD inline float abs2(zf a) { return a.re * a.re + a.im * a.im; }
+DD_HD inline float zabs(zf a) { return sqrtf(a.re * a.re + a.im * a.im); }
+
+struct Rotf { float c; zf s; };
+DD_HD inline Rotf make_rot(zf x, zf y) {
+  Rotf g;
+  const float ax2 = abs2(x), ay2 = abs2(y);
+  if (ay2 == 0.f) { g.c = 1.f; g.s = Zf(0.f); return g; }
+  if (ax2 == 0.f) { g.c = 0.f; g.s = Zf(1.f); return g; }
+  const float ax = sqrtf(ax2), inv = 1.f / sqrtf(ax2 + ay2);
+  g.c = ax * inv;
+  g.s = (inv / ax) * (x * conj(y));
+  return g;
+}
+DD_HD inline void rot_apply(const Rotf& g, zf& a, zf& b) {
+  zf a2 = g.c * a + g.s * b;
+  zf b2 = g.c * b - conj(g.s) * a;
+  a = a2;
+  b = b2;
+}
+DD_HD inline void rot_apply_right(const Rotf& g, zf& a, zf& b) {
+  zf a2 = g.c * a + conj(g.s) * b;
+  zf b2 = g.c * b - g.s * a;
+  a = a2;
+  b = b2;
+}
+
 // Eigenvalues of the upper Hessenberg A (n x n, ld) by the implicit single-shift QR
 // iteration with Wilkinson shifts (an exceptional shift every 11th step), each sweep
-// restricted to the active block [lo, hi]: A's diagonal holds the eigenvalues on return.
+// restricted to the active block [lo, hi], in FP32: A's diagonal holds them on return.
 // Returns the number of sweeps, or -1 if the iteration did not converge.
-DD_HD inline int hess_eigenvalues(const Team& T, zd* A, int n, int ld) {
-  auto a = [&](int i, int j) -> zd& { return A[i + (long)j * ld]; };
-  const double eps = 2.220446049250313e-16;
+DD_HD inline int hess_eigenvalues_f32(const Team& T, zf* A, int n, int ld) {
+  auto a = [&](int i, int j) -> zf& { return A[i + (long)j * ld]; };
+  const float eps = 1.1920929e-7f;
   int total = 0, hi = n - 1, iter = 0;
   while (hi > 0) {
     int lo = hi;
     while (lo > 0) {
-      double s = zabs(a(lo - 1, lo - 1)) + zabs(a(lo, lo));
-      if (s == 0.0) s = 1.0;
+      float s = zabs(a(lo - 1, lo - 1)) + zabs(a(lo, lo));
+      if (s == 0.f) s = 1.f;
       if (zabs(a(lo, lo - 1)) <= eps * s) break;
       --lo;
     }
     T.sync();
-    if (lo > 0 && T.tid == 0) a(lo, lo - 1) = Z(0.0);
+    if (lo > 0 && T.tid == 0) a(lo, lo - 1) = Zf(0.f);
     T.sync();
     if (lo == hi) { --hi; iter = 0; continue; }
     if (++iter > 60 * n) return -1;
     ++total;
-    zd aa = a(hi - 1, hi - 1), bb = a(hi - 1, hi), cc = a(hi, hi - 1), dd = a(hi, hi);
-    zd tr2 = 0.5 * (aa + dd);
-    zd det = aa * dd - bb * cc;
-    zd disc = tr2 * tr2 - det;
-    // principal square root of disc without trigonometric functions
-    const double rr = zabs(disc);
-    const double sre = sqrt(0.5 * (rr + disc.re)), sim = sqrt(fmax(0.0, 0.5 * (rr - disc.re)));
-    zd sq = Z(sre, disc.im < 0.0 ? -sim : sim);
-    zd l1 = tr2 + sq, l2 = tr2 - sq;
-    zd mu = abs2(l1 - dd) < abs2(l2 - dd) ? l1 : l2;
-    if (iter % 11 == 10) mu = dd + Z(zabs(a(hi, hi - 1)), 0.0);
-    zd x = a(lo, lo) - mu, y = a(lo + 1, lo);
+    zf aa = a(hi - 1, hi - 1), bb = a(hi - 1, hi), cc = a(hi, hi - 1), dd = a(hi, hi);
+    zf tr2 = 0.5f * (aa + dd);
+    zf disc = tr2 * tr2 - (aa * dd - bb * cc);
+    const float rr = zabs(disc);
+    const float sre = sqrtf(0.5f * (rr + disc.re)), sim = sqrtf(fmaxf(0.f, 0.5f * (rr - disc.re)));
+    zf sq = Zf(sre, disc.im < 0.f ? -sim : sim);
+    zf l1 = tr2 + sq, l2 = tr2 - sq;
+    zf mu = abs2(l1 - dd) < abs2(l2 - dd) ? l1 : l2;
+    if (iter % 11 == 10) mu = dd + Zf(zabs(a(hi, hi - 1)), 0.f);
+    zf x = a(lo, lo) - mu, y = a(lo + 1, lo);
     for (int k = lo; k < hi; ++k) {
-      const Rot r = make_rot(x, y);
+      const Rotf r = make_rot(x, y);
       const int c0 = k > lo ? k - 1 : lo;
-      T.sync();   // every member has read x, y
+      T.sync();
       for (int j = c0 + T.tid; j <= hi; j += T.nt) rot_apply(r, a(k, j), a(k + 1, j));
       T.sync();
       const int r1 = k + 2 < hi ? k + 2 : hi;
       for (int i = lo + T.tid; i <= r1; i += T.nt) rot_apply_right(r, a(i, k), a(i, k + 1));
       T.sync();
-      if (k > lo && T.tid == 0) a(k + 1, k - 1) = Z(0.0);
+      if (k > lo && T.tid == 0) a(k + 1, k - 1) = Zf(0.f);
       if (k + 1 < hi) { x = a(k + 1, k); y = a(k + 2, k); }
     }
     T.sync();
@@ -291,6 +328,7 @@ DD_HD inline void hessenberg(const Team& T, zd* A, zd* Q, int n, int ld) {
 // (host memory, device global memory or shared memory).
 struct DeflateWork {
   zd *G, *G0, *M, *Q;
+  zf* Gf;                     // FP32 copy for the eigenvalue estimates
   zd *f, *v, *w, *cls, *dot;
   zd* l;
   double *absth, *nrm;
@@ -298,8 +336,8 @@ struct DeflateWork {
   int ld;
 };
 DD_HD inline size_t deflate_bytes(int m) {
-  return (size_t)4 * m * m * sizeof(zd) + 6 * (size_t)(DD_MAXM + 1) * sizeof(zd) + (DD_MAXM + 1) * sizeof(double) * 2 +
-         2 * (size_t)(DD_MAXM + 1) * sizeof(int);
+  return (size_t)4 * m * m * sizeof(zd) + (size_t)m * m * sizeof(zf) + 6 * (size_t)(DD_MAXM + 1) * sizeof(zd) +
+         (DD_MAXM + 1) * sizeof(double) * 2 + 2 * (size_t)(DD_MAXM + 1) * sizeof(int);
 }
 DD_HD inline DeflateWork deflate_work(void* base, int m) {
   DeflateWork W;
@@ -309,6 +347,7 @@ DD_HD inline DeflateWork deflate_work(void* base, int m) {
   W.G0 = z; z += m * m;
   W.M = z; z += m * m;
   W.Q = z; z += m * m;
+  W.Gf = (zf*)z; z += (m * m + 1) / 2;
   W.f = z; z += DD_MAXM + 1;
   W.v = z; z += DD_MAXM + 1;
   W.w = z; z += DD_MAXM + 1;
@@ -365,11 +404,12 @@ DD_HD inline double orthonormalise(const Team& T, zd* P, int ld, int nprev, int 
 //      vector c - Hbar y; Hn = P^H Hbar P_k ((k+1) x k, ld = ldh); cn = P^H (c - Hbar y);
 //      theta[0:m] harmonic Ritz values sorted by |theta| (stable).
 // The harmonic Ritz pairs solve (H_m + |h_{m+1,m}|^2 f e_m^H) g = theta g with
-// f = H_m^{-H} e_m.  That matrix is reduced to Hessenberg form (Q), its eigenvalues come
-// from the QR iteration, and each kept vector from two steps of inverse iteration on the
-// Hessenberg form shifted by its eigenvalue, mapped back by Q.  A vector that is not
-// independent of those already kept (a repeated eigenvalue) is passed over for the next
-// one in the order.  Returns 0 on success, nonzero if a step failed (the caller then
+// f = H_m^{-H} e_m.  That matrix is reduced to Hessenberg form (Q); FP32 QR sweeps give
+// estimates of its eigenvalues, which order the candidates; each kept vector comes from two
+// steps of FP64 inverse iteration on the Hessenberg form shifted by its estimate, mapped
+// back by Q, and its value from the FP64 Rayleigh quotient (theta[0:k] are FP64 accurate,
+// theta[k:m] are the FP32 estimates).  A vector that is not independent of those already
+// kept (a repeated eigenvalue) is passed over for the next one in the order.  Returns 0 on success, nonzero if a step failed (the caller then
 // restarts plainly); all members of the team return the same value.
 DD_HD inline int deflate(const Team& T, const zd* Hbar, int ldh, int m, int k, const zd* c, const zd* y, zd* P, zd* Hn,
                          zd* cn, zd* theta, DeflateWork& W) {
@@ -394,22 +434,31 @@ DD_HD inline int deflate(const Team& T, const zd* Hbar, int ldh, int m, int k, c
   }
   T.sync();
   hessenberg(T, W.G, W.Q, m, ld);
-  for (int q = T.tid; q < m * m; q += T.nt) W.G0[q % m + (q / m) * ld] = W.G[q % m + (q / m) * ld];
+  for (int q = T.tid; q < m * m; q += T.nt) {
+    const zd g = W.G[q % m + (q / m) * ld];
+    W.G0[q % m + (q / m) * ld] = g;
+    W.Gf[q] = Zf((float)g.re, (float)g.im);
+  }
   T.sync();
-  if (hess_eigenvalues(T, W.G, m, ld) < 0) return 2;
-  // order by |theta| (stable insertion sort)
+  // eigenvalue estimates (FP32 QR), ordered by modulus (stable insertion sort)
+  if (hess_eigenvalues_f32(T, W.Gf, m, m) < 0) return 2;
   if (T.tid == 0) {
-    for (int i = 0; i < m; ++i) { W.absth[i] = zabs(W.G[i + i * ld]); W.order[i] = i; }
+    for (int i = 0; i < m; ++i) { W.absth[i] = (double)zabs(W.Gf[i + i * m]); W.order[i] = i; }
     for (int i = 1; i < m; ++i) {
       int o = W.order[i];
       int j = i - 1;
       while (j >= 0 && W.absth[W.order[j]] > W.absth[o]) { W.order[j + 1] = W.order[j]; --j; }
       W.order[j + 1] = o;
     }
-    for (int i = 0; i < m; ++i) theta[i] = W.G[W.order[i] + W.order[i] * ld];
+    for (int i = 0; i < m; ++i) {
+      const zf t = W.Gf[W.order[i] + W.order[i] * m];
+      theta[i] = Z((double)t.re, (double)t.im);
+    }
   }
   T.sync();
-  // columns of P: eigenvectors for the k smallest |theta| (zero last row)
+  // columns of P: for the candidates in that order, two steps of FP64 inverse iteration on
+  // the Hessenberg form shifted by the estimate, the Rayleigh quotient as the refined
+  // value, the vector mapped back by Q; k independent ones are kept
   const double tiny = 1e-15 * hn;
   int kept = 0;
   for (int cand = 0; cand < m && kept < k; ++cand) {
@@ -437,7 +486,19 @@ DD_HD inline int deflate(const Team& T, const zd* Hbar, int ldh, int m, int k, c
       T.sync();
     }
     if (!ok) continue;
-    // back to the basis of H_m: w = Q v
+    // Rayleigh quotient v^H G0 v (|v| = 1)
+    for (int i = T.tid; i < m; i += T.nt) {
+      zd s = Z(0.0);
+      for (int j = (i > 0 ? i - 1 : 0); j < m; ++j) s = s + W.G0[i + j * ld] * W.v[j];
+      W.w[i] = s;
+    }
+    T.sync();
+    if (T.tid == 0) {
+      zd rq = Z(0.0);
+      for (int i = 0; i < m; ++i) rq = rq + conj(W.v[i]) * W.w[i];
+      theta[cand] = rq;
+    }
+    // back to the basis of H_m: p = Q v
     zd* p = P + (long)kept * ldh;
     for (int i = T.tid; i <= m; i += T.nt) {
       zd s = Z(0.0);
@@ -458,24 +519,27 @@ DD_HD inline int deflate(const Team& T, const zd* Hbar, int ldh, int m, int k, c
   }
   T.sync();
   if (!(orthonormalise(T, P, ldh, k, m + 1, P + (long)k * ldh, W) > 0)) return 4;
-  // Hn = P^H Hbar P_k, cn = P^H cls
-  for (int q = T.tid; q < (k + 1) * (k + 1); q += T.nt) {
-    const int a = q % (k + 1), b = q / (k + 1);
+  // Hn = (P^H Hbar) P_k, cn = P^H cls; the product P^H Hbar goes to M ((k+1) x m)
+  for (int q = T.tid; q < (k + 1) * m; q += T.nt) {
+    const int a = q % (k + 1), j = q / (k + 1);
     const zd* pa = P + (long)a * ldh;
-    if (b < k) {
-      const zd* pb = P + (long)b * ldh;
-      zd s = Z(0.0);
-      for (int j = 0; j < m; ++j) {
-        zd hp = Z(0.0);
-        for (int i = 0; i <= m; ++i) hp = hp + conj(pa[i]) * Hbar[i + (long)j * ldh];
-        s = s + hp * pb[j];
-      }
-      Hn[a + (long)b * ldh] = s;
-    } else {
-      zd s = Z(0.0);
-      for (int i = 0; i <= m; ++i) s = s + conj(pa[i]) * W.cls[i];
-      cn[a] = s;
-    }
+    zd s = Z(0.0);
+    for (int i = 0; i <= m; ++i) s = s + conj(pa[i]) * Hbar[i + (long)j * ldh];
+    W.M[a + j * ld] = s;
+  }
+  for (int a = T.tid; a <= k; a += T.nt) {
+    const zd* pa = P + (long)a * ldh;
+    zd s = Z(0.0);
+    for (int i = 0; i <= m; ++i) s = s + conj(pa[i]) * W.cls[i];
+    cn[a] = s;
+  }
+  T.sync();
+  for (int q = T.tid; q < (k + 1) * k; q += T.nt) {
+    const int a = q % (k + 1), b = q / (k + 1);
+    const zd* pb = P + (long)b * ldh;
+    zd s = Z(0.0);
+    for (int j = 0; j < m; ++j) s = s + W.M[a + j * ld] * pb[j];
+    Hn[a + (long)b * ldh] = s;
   }
   T.sync();
   return 0;

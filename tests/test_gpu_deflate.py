@@ -25,7 +25,10 @@ def test_device_deflation_matches_oracle_and_host(n, m, k, seed):
         P, Hn, cn, th, ms = dd.dd_deflate_device(Hbar, c, y, k)
         print(f"m {mm} k {k}: device deflation {ms:.3f} ms")
         theta, G = harmonic_ritz(Hbar, mm)
-        assert np.allclose(np.sort_complex(th), np.sort_complex(theta), rtol=1e-10, atol=1e-12)
+        # the k kept values FP64 accurate, the others FP32 estimates (nearest exact value)
+        scale = np.abs(Hbar).max()
+        for i, t in enumerate(th):
+            assert np.abs(theta - t).min() <= (1e-10 * abs(t) + 1e-12 * scale if i < k else 1e-4 * scale)
         assert np.allclose(P.conj().T @ P, np.eye(k + 1), atol=1e-12)
         Gk = np.vstack([G[:, :k], np.zeros((1, k))])
         proj = P[:, :k] @ (P[:, :k].conj().T @ Gk)
@@ -35,5 +38,5 @@ def test_device_deflation_matches_oracle_and_host(n, m, k, seed):
         # the host run of the same code: same Ritz values, same subspace (each eigenvector is
         # fixed only up to a phase, which rounding may settle differently)
         Ph, Hnh, cnh, thh = dd.dd_deflate_host(Hbar, c, y, k)
-        assert np.allclose(th, thh, rtol=1e-9, atol=1e-12)
+        assert np.allclose(th[:k], thh[:k], rtol=1e-9, atol=1e-12)
         assert np.linalg.norm(P @ P.conj().T - Ph @ Ph.conj().T) <= 1e-8 * (k + 1)

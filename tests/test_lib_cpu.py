@@ -52,6 +52,17 @@ def test_load_model_matches_paper_values(ddmod):
     assert ddmod.dd_load_model(0, 152) == 0.0
 
 
+def _check_ritz_values(th, theta, k, Hbar):
+    """The k kept harmonic Ritz values (smallest modulus) are FP64 accurate, the others FP32
+    estimates: each returned value is matched to the nearest exact one."""
+    order = np.argsort(np.abs(theta), kind="stable")
+    assert np.allclose(np.abs(th[:k]), np.abs(theta[order[:k]]), rtol=1e-10)
+    scale = np.abs(Hbar).max()
+    for i, t in enumerate(th):
+        err = np.abs(theta - t).min()
+        assert err <= (1e-10 * abs(t) + 1e-12 * scale if i < k else 1e-4 * scale)
+
+
 @pytest.mark.parametrize("n,m,k,seed", [(60, 10, 4, 3), (160, 40, 8, 4), (120, 32, 8, 5), (90, 16, 6, 6)])
 def test_host_deflation_matches_oracle(ddmod, n, m, k, seed):
     """The deflated restart's small dense step (the same team code the solver runs as one
@@ -71,8 +82,7 @@ def test_host_deflation_matches_oracle(ddmod, n, m, k, seed):
         mm = Hbar.shape[1]
         P, Hn, cn, th = ddmod.dd_deflate_host(Hbar, c, y, k)
         theta, G = harmonic_ritz(Hbar, mm)
-        assert np.allclose(np.sort_complex(th), np.sort_complex(theta), rtol=1e-10, atol=1e-12)
-        assert np.allclose(np.abs(th), np.sort(np.abs(theta)), rtol=1e-10)
+        _check_ritz_values(th, theta, k, Hbar)
         # P is orthonormal, spans the k kept harmonic Ritz vectors and the LS residual
         assert np.allclose(P.conj().T @ P, np.eye(k + 1), atol=1e-12)
         Gk = np.vstack([G[:, :k], np.zeros((1, k))])
