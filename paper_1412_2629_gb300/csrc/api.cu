@@ -71,6 +71,10 @@ struct SolverBuffers {
   LsqState* lsq = nullptr;
   int* flag = nullptr;                 // Gram-Schmidt: 1 when a second projection is needed
   double* nu2 = nullptr;               // squared norm of the projected vector
+  // 1 / |v_i| of the basis vectors as stored: the single-right-hand-side solver leaves each
+  // new vector unnormalised (its exact norm comes out of the projection pass) and its
+  // readers apply the scale, which saves a read and a write of the vector per step
+  float* vscale = nullptr;
   // deflated restart on the device: workspace and flags ([0] deflation status, [1] the
   // recombination gate: deflation succeeded and the residual is above target)
   void* dW = nullptr;            // deflate_bytes(m) of global scratch (when shared memory is too small)
@@ -466,11 +470,14 @@ static dd_status ensure_faces2(dd_ctx* c, int prec) {
   return DD_OK;
 }
 
-static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_params* p, int nrhs = 1) {
+// vscale (device scalar, single right-hand side): the input is v * (*vscale)
+static dd_status sap_run(dd_ctx* c, const float4* v, float4* z, const dd_sap_params* p, int nrhs = 1,
+                         const float* vscale = nullptr) {
   int prec = sap_prec(p->storage_prec);
   TRY(ensure_sap(c, prec, nrhs));
   if (p->additive) TRY(ensure_faces2(c, prec));
   SapState S = sap_state(c, prec, p, nrhs);
+  S.vscale = vscale;
   return sap_sweeps(c, S, p, v, z, c->sap[prec].faces2);
 }
 
@@ -573,6 +580,13 @@ extern "C" dd_status dd_apply_D_batch(dd_ctx* c, const void* in, void* out, int 
 }
 
 // ------------------------------------------------------------------ small dense kernels
+__global__ void fill_ones_kernel(float* v, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 1.f;
+}
+
+// vscale[0] = 1 / sqrt(nu2): the scale of a vector stored unnormalised
+__global__ void set_vscale_kernel(float* vscale, const double* nu2) { vscale[0] = (float)(1.0 / sqrt(*nu2)); }
+
 // After the first projection: |w - V h|^2 is known exactly; ask for a second projection
 // when it is below half of |w|^2.
 __global__ void gs_decide_kernel(const zd* hA, int nv, const double2* nrm_a, zd* hB, int* flag, double* nu2) {
@@ -604,7 +618,8 @@ __global__ void lsq_solve_kernel(const zd* R, int ldh, int n, const zd* g, zd* y
 // After a deflated restart: H <- Hn (k+1 x k), g <- cp, and the rotations of the dense
 // block are rebuilt.
 __global__ void restart_lsq_kernel(zd* H, zd* R, int ldh, int m, int k, const zd* Hn, const zd* cp, zd* g, zd* c0,
-                                   LsqState* lsq, double* status) {
+                                   LsqState* lsq, double* status, float* vscale) {
+  for (int i = 0; i <= k; ++i) vscale[i] = 1.f;   // the recombined vectors are normalised
   for (int j = 0; j < m; ++j)
     for (int i = 0; i <= m; ++i) { H[i + (long)j * ldh] = Z(0.0); R[i + (long)j * ldh] = Z(0.0); }
   for (int i = 0; i <= m; ++i) g[i] = c0[i] = Z(0.0);
@@ -617,7 +632,9 @@ __global__ void restart_lsq_kernel(zd* H, zd* R, int ldh, int m, int k, const zd
   status[0] = res;
 }
 
-__global__ void plain_restart_kernel(zd* H, zd* R, int ldh, int m, const double2* nrm2, zd* g, zd* c0, LsqState* lsq) {
+__global__ void plain_restart_kernel(zd* H, zd* R, int ldh, int m, const double2* nrm2, zd* g, zd* c0, LsqState* lsq,
+                                     float* vscale) {
+  vscale[0] = 1.f;   // v_1 = r / |r| is stored normalised
   for (int j = 0; j < m; ++j)
     for (int i = 0; i <= m; ++i) { H[i + (long)j * ldh] = Z(0.0); R[i + (long)j * ldh] = Z(0.0); }
   for (int i = 0; i <= m; ++i) g[i] = c0[i] = Z(0.0);
@@ -698,7 +715,7 @@ static void free_solver_buffers(dd_ctx* c, SolverBuffers& s) {
                   (void*)s.f64, (void*)s.r64, (void*)s.canon64, (void*)s.H, (void*)s.R, (void*)s.P, (void*)s.Hn,
                   (void*)s.g, (void*)s.c0, (void*)s.y, (void*)s.hA, (void*)s.hB, (void*)s.cn, (void*)s.theta,
                   (void*)s.cp, (void*)s.partial, (void*)s.partial2, (void*)s.nrm2, (void*)s.status, (void*)s.lsq,
-                  (void*)s.flag, (void*)s.nu2, (void*)s.dW, (void*)s.dflags})
+                  (void*)s.flag, (void*)s.nu2, (void*)s.dW, (void*)s.dflags, (void*)s.vscale})
     release(c, p);
   if (s.h_status) cudaFreeHost(s.h_status);
   for (auto& kv : s.graphs)
@@ -749,6 +766,9 @@ static dd_status alloc_solver_buffers(dd_ctx* c, SolverBuffers& s, int m, bool s
   TRY(dalloc(c, &s.flag, 16));
   TRY(dalloc(c, &s.nu2, 16));
   TRY(dalloc(c, &s.dW, deflate_bytes(m)));
+  TRY(dalloc(c, &s.vscale, (m + 2) * sizeof(float)));
+  fill_ones_kernel<<<1, 64, 0, c->st>>>(s.vscale, m + 2);
+  TRY(launched(c));
   TRY(dalloc(c, &s.dflags, 16 * sizeof(int)));
   if (cudaMallocHost(&s.h_status, 8 * sizeof(double)) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned status");
   if (streams && (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -874,7 +894,7 @@ static dd_status end_cycle(dd_ctx* c, SolverBuffers& s, int mm, const dd_solve_p
     // V <- V P_{k+1}, Z <- Z P_k in place: every output element depends only on the inputs
     // at the same position, which its thread reads before writing
     const int* gate = s.dflags + 1;
-    nk += launch_recombine(s.V, s.V, mm + 1, k + 1, n4, (const double2*)s.P, ldh, c->st, gate);
+    nk += launch_recombine(s.V, s.V, mm + 1, k + 1, n4, (const double2*)s.P, ldh, c->st, gate, s.vscale);
     nk += launch_recombine(s.Z, s.Z, mm, k, n4, (const double2*)s.P, ldh, c->st, gate);
     launch_r64_to_v32(s.w, s.r64, n4, s.nrm2, c->st, gate);
     nk += 1 + launch_gs_dot(s.V, k + 1, n4, s.w, s.partial, gate, 1, c->st);
@@ -921,7 +941,7 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
   int j0 = 0;
   if (rc == DD_OK && rel > tol) {
     launch_r64_to_v32(Vv(0), s.r64, n4, s.nrm2, c->st);
-    plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq);
+    plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq, s.vscale);
     TRY(launched(c, 2));
   }
   while (rc == DD_OK && rel > tol) {
@@ -937,7 +957,7 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
       k1[0] = 1;
       k2[0] = 2;
       cudaEventRecord(e0, c->st);
-      TRY(graphed(c, k0, [&]() { return sap_run(c, Vv(j), Zv(j), &p->sap); }));
+      TRY(graphed(c, k0, [&]() { return sap_run(c, Vv(j), Zv(j), &p->sap, 1, s.vscale + j); }));
       cudaEventRecord(e1, c->st);
       TRY(graphed(c, k1, [&]() { return apply_internal(c, Zv(j), s.w, P32); }));
       cudaEventRecord(e2, c->st);
@@ -947,23 +967,26 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
         float4* vn = Vv(j + 1);
         double2* nrm_a = s.nrm2 + 1;
         double2* nrm_b = s.nrm2 + 2;
-        int nk = launch_gs_dot(Vv(0), j + 1, n4, s.w, s.partial, nullptr, 0, c->st);
+        // the basis vectors are read through their scales (vscale), and the new one stays
+        // unnormalised: its exact norm comes out of the projection pass
+        const float* sc = s.vscale;
+        int nk = launch_gs_dot(Vv(0), j + 1, n4, s.w, s.partial, nullptr, 0, c->st, sc);
         launch_gs_reduce(s.partial, j + 1, (double2*)s.hA, nullptr, 0, c->st);
-        launch_gs_project(vn, s.w, Vv(0), j + 1, n4, (const double2*)s.hA, s.partial2, nullptr, 0, c->st);
+        launch_gs_project(vn, s.w, Vv(0), j + 1, n4, (const double2*)s.hA, s.partial2, nullptr, 0, c->st, sc);
         launch_gs_reduce(s.partial2, 0, nrm_a, nullptr, 0, c->st);
         gs_decide_kernel<<<1, 1, 0, c->st>>>(s.hA, j + 1, nrm_a, s.hB, s.flag, s.nu2);
-        nk += launch_gs_dot(Vv(0), j + 1, n4, vn, s.partial, s.flag, 1, c->st);
+        nk += launch_gs_dot(Vv(0), j + 1, n4, vn, s.partial, s.flag, 1, c->st, sc);
         launch_gs_reduce(s.partial, j + 1, (double2*)s.hB, s.flag, 1, c->st);
-        launch_gs_project(vn, vn, Vv(0), j + 1, n4, (const double2*)s.hB, s.partial2, s.flag, 1, c->st);
+        launch_gs_project(vn, vn, Vv(0), j + 1, n4, (const double2*)s.hB, s.partial2, s.flag, 1, c->st, sc);
         launch_gs_reduce(s.partial2, 0, nrm_b, s.flag, 1, c->st);
         gs_decide2_kernel<<<1, 1, 0, c->st>>>(s.flag, nrm_b, s.nu2);
-        // the Hessenberg column and its Givens update (one thread) run beside the
-        // normalisation of the new basis vector; both only read nu2
+        // the Hessenberg column and its Givens update (one thread) beside the new vector's
+        // scale; both only read nu2
         cudaEventRecord(s.ev_fork, c->st);
         cudaStreamWaitEvent(s.side, s.ev_fork, 0);
         arnoldi_finish_kernel<<<1, 1, 0, s.side>>>(s.H, s.R, ldh, j, s.hA, s.hB, s.nu2, s.lsq, s.g, s.status);
         cudaEventRecord(s.ev_join, s.side);
-        launch_scale_inplace(vn, n4, s.nu2, c->st);
+        set_vscale_kernel<<<1, 1, 0, c->st>>>(s.vscale + j + 1, s.nu2);
         cudaStreamWaitEvent(c->st, s.ev_join, 0);
         return launched(c, nk + 10);
       }));
@@ -987,12 +1010,15 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
       // orthogonality of the finished basis: max |V^H V - I|
       double dev = 0;
       std::vector<zd> row(mm + 1);
+      std::vector<float> sc(mm + 1);
+      cudaMemcpyAsync(sc.data(), s.vscale, (mm + 1) * sizeof(float), cudaMemcpyDeviceToHost, c->st);
       for (int i = 0; i <= mm; ++i) {
         launch_multi_dot(Vv(0), mm + 1, n4, Vv(i), s.partial, c->st);
         launch_reduce_partials(s.partial, mm + 1, (double2*)s.hB, 0, c->st);
         cudaMemcpyAsync(row.data(), s.hB, (mm + 1) * sizeof(zd), cudaMemcpyDeviceToHost, c->st);
         cudaStreamSynchronize(c->st);
-        for (int l = 0; l <= mm; ++l) dev = fmax(dev, zabs(row[l] - Z(l == i ? 1.0 : 0.0)));
+        for (int l = 0; l <= mm; ++l)
+          dev = fmax(dev, zabs(((double)sc[i] * sc[l]) * row[l] - Z(l == i ? 1.0 : 0.0)));
       }
       fprintf(stderr, "[dd] basis orthogonality max|V^H V - I| = %.3e over %d vectors\n", dev, mm + 1);
     }
@@ -1008,13 +1034,13 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
     if (c->trace)
       fprintf(stderr, "[dd] restart: true residual %.3e, deflation status %d, misses %.3e\n", rel, ce.defl_rc, ce.miss);
     if (ce.deflate) {
-      restart_lsq_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, k, s.Hn, s.cp, s.g, s.c0, s.lsq, s.status);
+      restart_lsq_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, k, s.Hn, s.cp, s.g, s.c0, s.lsq, s.status, s.vscale);
       TRY(launched(c));
       j0 = k;
       deflated++;
     } else {
       launch_r64_to_v32(Vv(0), s.r64, n4, s.nrm2, c->st);
-      plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq);
+      plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq, s.vscale);
       TRY(launched(c, 2));
       j0 = 0;
     }
@@ -1144,13 +1170,13 @@ static dd_status lock_end_cycle(dd_ctx* c, SolverBuffers& s, LockRhs& R, int mm,
   }
   R.restarts++;
   if (ce.deflate) {
-    restart_lsq_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, k, s.Hn, s.cp, s.g, s.c0, s.lsq, s.status);
+    restart_lsq_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, k, s.Hn, s.cp, s.g, s.c0, s.lsq, s.status, s.vscale);
     TRY(launched(c));
     R.j0 = k;
     R.deflated++;
   } else {
     launch_r64_to_v32(s.V, s.r64, n4, s.nrm2, c->st);
-    plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq);
+    plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq, s.vscale);
     TRY(launched(c, 2));
     R.j0 = 0;
   }
@@ -1204,7 +1230,7 @@ static dd_status solve_lockstep(dd_ctx* c, const double* f, double* x, int nrhs,
       R[r].done = true;
     } else {
       launch_r64_to_v32(s.V, s.r64, n4, s.nrm2, c->st);
-      plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, m + 1, m, s.nrm2, s.g, s.c0, s.lsq);
+      plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, m + 1, m, s.nrm2, s.g, s.c0, s.lsq, s.vscale);
       TRY(launched(c, 2));
       R[r].rho_cycle = sqrt(R[r].rho2);
     }
@@ -1373,7 +1399,7 @@ static dd_status solve_lattices(dd_ctx** ctxs, int nlat, const double* const* f,
         Q.done = true;
       } else {
         launch_r64_to_v32(s.V, s.r64, g.V * 6, s.nrm2, st);
-        plain_restart_kernel<<<1, 1, 0, st>>>(s.H, s.R, m + 1, m, s.nrm2, s.g, s.c0, s.lsq);
+        plain_restart_kernel<<<1, 1, 0, st>>>(s.H, s.R, m + 1, m, s.nrm2, s.g, s.c0, s.lsq, s.vscale);
         TRY(launched(c, 2));
         Q.rho_cycle = sqrt(Q.rho2);
       }

@@ -169,13 +169,15 @@ void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2*
 constexpr int RBT = 128, RU = 8;
 template <int NO>
 __global__ void __launch_bounds__(RBT) recombine_kernel(float4* out, const float4* V, int nv, int l0,
-                                                        long long n4, const double2* P, int ldp, const int* gate) {
+                                                        long long n4, const double2* P, int ldp, const int* gate,
+                                                        const float* vscale) {
   if (gate && *gate != 1) return;
   __shared__ float2 ps[64][NO];
   for (int t = threadIdx.x; t < nv * NO; t += RBT) {
     int i = t / NO, l = t % NO;
     const double2 c = P[i + (long long)(l0 + l) * ldp];
-    ps[i][l] = make_float2((float)c.x, (float)c.y);
+    const double sc = vscale ? (double)vscale[i] : 1.0;   // stored V_i = v_i / vscale[i]
+    ps[i][l] = make_float2((float)(c.x * sc), (float)(c.y * sc));
   }
   __syncthreads();
   for (long long q = blockIdx.x * (long long)RBT + threadIdx.x; q < n4; q += (long long)gridDim.x * RBT) {
@@ -208,18 +210,18 @@ __global__ void __launch_bounds__(RBT) recombine_kernel(float4* out, const float
 
 template <int NO>
 static void recombine_launch(int nl, float4* out, const float4* V, int nv, int l0, long long n4, const double2* P,
-                             int ldp, cudaStream_t st, const int* gate) {
+                             int ldp, cudaStream_t st, const int* gate, const float* vscale) {
   if constexpr (NO > 1) {
-    if (nl < NO) return recombine_launch<NO - 1>(nl, out, V, nv, l0, n4, P, ldp, st, gate);
+    if (nl < NO) return recombine_launch<NO - 1>(nl, out, V, nv, l0, n4, P, ldp, st, gate, vscale);
   }
-  recombine_kernel<NO><<<2 * blas_partials_blocks(), RBT, 0, st>>>(out, V, nv, l0, n4, P, ldp, gate);
+  recombine_kernel<NO><<<2 * blas_partials_blocks(), RBT, 0, st>>>(out, V, nv, l0, n4, P, ldp, gate, vscale);
 }
 
 int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n4, const double2* P, int ldp,
-                     cudaStream_t st, const int* gate) {
+                     cudaStream_t st, const int* gate, const float* vscale) {
   int n = 0;
   for (int l0 = 0; l0 < nout; l0 += 16, ++n)
-    recombine_launch<16>(nout - l0 < 16 ? nout - l0 : 16, out, V, nv, l0, n4, P, ldp, st, gate);
+    recombine_launch<16>(nout - l0 < 16 ? nout - l0 : 16, out, V, nv, l0, n4, P, ldp, st, gate, vscale);
   return n;
 }
 
@@ -237,7 +239,7 @@ int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n
 template <int NV, int U>
 __global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const float4* __restrict__ V, int nv, int nch, long long n4,
                                                        const float4* __restrict__ w, double2* partial, int ldp,
-                                                       const int* gate, int want) {
+                                                       const int* gate, int want, const float* vscale) {
   if (gate && *gate != want) return;
   const int chunk = blockIdx.x % nch, qb = blockIdx.x / nch, nqb = gridDim.x / nch;
   const int v0 = chunk * NV, nvc = min(NV, nv - v0);
@@ -282,7 +284,11 @@ __global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const float4* __restrict_
   }
   double2 acc[NV + 1];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = make_double2(re[i], im[i]);
+  for (int i = 0; i < NV; ++i) {
+    // stored V_i = v_i / vscale[i]: the product with v_i is the stored one times vscale[i]
+    const double sc = (vscale && i < nvc) ? (double)vscale[v0 + i] : 1.0;
+    acc[i] = make_double2(re[i] * sc, im[i] * sc);
+  }
   acc[NV] = make_double2(ww, 0.0);
   __shared__ double2 out[NV + 1];
   block_reduce<NV + 1>(acc, out);
@@ -292,9 +298,10 @@ __global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const float4* __restrict_
 
 // partial layout [q-slice][nv + 1]: entries 0..nv-1 are V^H w, entry nv is |w|^2.
 int launch_gs_dot(const float4* V, int nv, long long n4, const float4* w, double2* partial, const int* gate, int want,
-                  cudaStream_t st) {
+                  cudaStream_t st, const float* vscale) {
   const int nch = nv > 0 ? (nv + 7) / 8 : 1;
-  gs_dot_kernel<8, 2><<<blas_partials_blocks() * nch, BT, 0, st>>>(V, nv, nch, n4, w, partial, nv + 1, gate, want);
+  gs_dot_kernel<8, 2><<<blas_partials_blocks() * nch, BT, 0, st>>>(V, nv, nch, n4, w, partial, nv + 1, gate, want,
+                                                                   vscale);
   return 1;
 }
 
@@ -322,10 +329,13 @@ void launch_gs_reduce(const double2* partial, int nv, double2* out, const int* g
 // in_place: out aliases w.
 __global__ void __launch_bounds__(BT) gs_project_kernel(float4* out, const float4* w, const float4* V, int nv,
                                                         long long n4, const double2* h, double2* norm_partial,
-                                                        const int* gate, int want) {
+                                                        const int* gate, int want, const float* vscale) {
   if (gate && *gate != want) return;
   __shared__ float2 hs[64];
-  for (int i = threadIdx.x; i < nv; i += BT) hs[i] = make_float2((float)h[i].x, (float)h[i].y);
+  for (int i = threadIdx.x; i < nv; i += BT) {
+    const double sc = vscale ? (double)vscale[i] : 1.0;   // h_i v_i = (h_i vscale[i]) V_i
+    hs[i] = make_float2((float)(h[i].x * sc), (float)(h[i].y * sc));
+  }
   __syncthreads();
   float nrm = 0.f;
   for (long long q = blockIdx.x * (long long)BT + threadIdx.x; q < n4; q += (long long)gridDim.x * BT) {
@@ -348,8 +358,8 @@ __global__ void __launch_bounds__(BT) gs_project_kernel(float4* out, const float
 }
 
 void launch_gs_project(float4* out, const float4* w, const float4* V, int nv, long long n4, const double2* h,
-                       double2* norm_partial, const int* gate, int want, cudaStream_t st) {
-  gs_project_kernel<<<blas_partials_blocks(), BT, 0, st>>>(out, w, V, nv, n4, h, norm_partial, gate, want);
+                       double2* norm_partial, const int* gate, int want, cudaStream_t st, const float* vscale) {
+  gs_project_kernel<<<blas_partials_blocks(), BT, 0, st>>>(out, w, V, nv, n4, h, norm_partial, gate, want, vscale);
 }
 
 // v *= 1 / sqrt(*nu2)

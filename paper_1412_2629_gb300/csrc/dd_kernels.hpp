@@ -75,6 +75,8 @@ struct SapState {
   // faces of the previous sweep from `faces` and writing this sweep's to faces_out
   bool both_colours = false;
   float4* faces_out = nullptr;
+  // single right-hand side: the input is v * (*vscale) (device scalar), when set
+  const float* vscale = nullptr;
 };
 // One half-sweep: all domains of `colour`.  first: the residual is the input v (both
 // parities) and u = 0; use_faces: subtract the couplings to the other colour from the
@@ -101,17 +103,21 @@ void launch_x_update(double2* x, const float4* Z, int nz, long long n4, const do
 // v = r / sqrt(nrm2); with a gate, only when *gate == 1
 void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2* nrm2, cudaStream_t st,
                        const int* gate = nullptr);
-// out_l = sum_i P(i, l) V_i for l < nout (in place allowed); with a gate, only when *gate == 1
+// out_l = sum_i P(i, l) v_i for l < nout (in place allowed); with a gate, only when
+// *gate == 1.  vscale (optional, device): the stored vectors are V_i = v_i / vscale[i].
 int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n4, const double2* P, int ldp,
-                     cudaStream_t st, const int* gate = nullptr);
+                     cudaStream_t st, const int* gate = nullptr, const float* vscale = nullptr);
 
 // Classical Gram-Schmidt passes with device-gated reorthogonalisation (blas.cu).  A kernel
-// given a gate runs only when *gate == want.
+// given a gate runs only when *gate == want.  vscale (optional, device): the basis holds
+// V_i = v_i / vscale[i] (a vector whose normalisation is deferred to its readers); dots and
+// projections are taken against v_i.
 int launch_gs_dot(const float4* V, int nv, long long n4, const float4* w, double2* partial, const int* gate, int want,
-                  cudaStream_t st);
+                  cudaStream_t st, const float* vscale = nullptr);
 void launch_gs_reduce(const double2* partial, int nv, double2* out, const int* gate, int want, cudaStream_t st);
 void launch_gs_project(float4* out, const float4* w, const float4* V, int nv, long long n4, const double2* h,
-                       double2* norm_partial, const int* gate, int want, cudaStream_t st);
+                       double2* norm_partial, const int* gate, int want, cudaStream_t st,
+                       const float* vscale = nullptr);
 void launch_scale_inplace(float4* v, long long n4, const double* nu2, cudaStream_t st);
 
 // ---- BiCGstab comparison solver (krylov.cu).  U = float4 (FP32 fields) or double2 (FP64

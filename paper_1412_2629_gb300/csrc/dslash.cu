@@ -74,9 +74,11 @@ __global__ void __launch_bounds__(256) apply_A_kernel(Geom g, LinkPtr<T> U, Clov
 // The same one-thread-per-site operator for FP32 fields with the domain shape as
 // compile-time constants (SHAPE 1: 8x4x4x4, 2: 4x4x4x4): the site decoding and every
 // neighbour and unit address then fold into shifts and immediate offsets, which takes the
-// integer work off the issue slots that the loads need.
+// integer work off the issue slots that the loads need.  Two CTAs of 256 per SM: the
+// compiler may then use 128 registers, and spends them on keeping more of the neighbour
+// and link loads in flight (measured 20 % faster than the same code at 88 registers).
 template <int SHAPE>
-__global__ void __launch_bounds__(256) apply_A_shape_kernel(Geom g0, LinkPtr<float> U, CloverPtr<float> C,
+__global__ void __launch_bounds__(256, 2) apply_A_shape_kernel(Geom g0, LinkPtr<float> U, CloverPtr<float> C,
                                                             SpinorPtr<float> in, SpinorPtr<float> out,
                                                             SpinorPtr<float> f, int residual) {
   const Geom g = fixed_shape<SHAPE>(g0);

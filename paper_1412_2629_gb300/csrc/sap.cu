@@ -313,6 +313,7 @@ struct SapArgs {
   int both_colours;    // additive form: the grid covers the domains of both colours
   const float4* v;
   float4* z;
+  const float* vscale;   // if set: the input is v * (*vscale) (a basis vector stored unnormalised)
   const float4* const* vptr;   // if set: input / output of right-hand side r at vptr[r] / zptr[r]
   float4* const* zptr;
   int* err;
@@ -401,6 +402,16 @@ __global__ void __launch_bounds__(SAP_MAX_THREADS, 1) sap_kernel(SapArgs a) {
   if (a.first) {
     vin.load(g, s_e, re);
     vin.load(g, s_o, ro);
+    if (a.vscale) {
+      const float sc = *a.vscale;
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          re.c[sp][c] = sc * re.c[sp][c];
+          ro.c[sp][c] = sc * ro.c[sp][c];
+        }
+    }
   } else {
     rst.load(d, Hd, tid, re);
     zero(ro);
@@ -1092,9 +1103,20 @@ __device__ __forceinline__ void sap_pair_body(const SapArgs& a, int cta) {
   {
     Spinor<float> r;
     const SpinorPtr<float> vin{const_cast<float4*>(a.vptr ? a.vptr[rhs] : a.v + rhs * a.v_stride)};
-    if (a.first) vin.load(g, s_site, r);
-    else if (h == 0) rst.load(d, Hd, i, r);
-    else zero(r);
+    if (a.first) {
+      vin.load(g, s_site, r);
+      if (a.vscale) {
+        const float sc = *a.vscale;
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) r.c[sp][c] = sc * r.c[sp][c];
+      }
+    } else if (h == 0) {
+      rst.load(d, Hd, i, r);
+    } else {
+      zero(r);
+    }
     if (MSMEM && rhs == 0) {
       bool ok = mbar_wait(&mbar, 0, a.wait_ns);
       if (a.extra_tx) ok = mbar_wait(&mbar_inj, 0, a.wait_ns) && ok;
@@ -1447,6 +1469,7 @@ static SapArgs make_args(const Geom& g, const SapState& S, int colour, int first
   a.both_colours = S.both_colours ? 1 : 0;
   a.v = v;
   a.z = z;
+  a.vscale = S.vscale;
   a.vptr = S.vlist;
   a.zptr = S.zlist;
   a.err = S.err;
