@@ -939,49 +939,39 @@ __device__ inline void block_apply_pair(const MatBlock<MT>& M, int r, int h, con
 template <int MU, typename MT, bool H2>
 __device__ inline void hop_mask_mu(const Geom& g, unsigned fwd, unsigned bwd, int lex, int p, int r_self,
                                    const float4* src, const MatBlock<MT>& M, Spinor<float>& acc) {
-  const bool hf = (fwd >> MU) & 1u, hb = (bwd >> MU) & 1u;
-  if constexpr (!H2) {
-    // FP32 products: both hops are computed for every site (a missing neighbour reads the
-    // site's own index, in bounds) and added only where they exist, so the two hops'
-    // loads and products interleave instead of sitting in separate branches
-    const int jf = hf ? (lex + g.bstride[MU]) >> 1 : (lex >> 1);
-    const int jb = hb ? (lex - g.bstride[MU]) >> 1 : (lex >> 1);
-    Spinor<float> psf, psb;
-    Half<float> hfw, hbw, uf, ub;
-    ld_buf(src, g.Hd, jf, psf);
-    ld_buf(src, g.Hd, jb, psb);
-    project<MU, -1>(psf, hfw);
-    project<MU, +1>(psb, hbw);
-    Link<float> Lf, Lb;
-    M.link(MU, r_self, Lf);
-    M.link(MU, (1 - p) * g.Hd + jb, Lb);
-    su3_mul(Lf, hfw, uf);
-    su3_dag_mul(Lb, hbw, ub);
-    if (hf) accum_recon<MU, -1>(acc, uf);
-    if (hb) accum_recon<MU, +1>(acc, ub);
-  } else {
-    Spinor<float> psi;
-    Half<float> h, uh;
-    if (hf) {
-      int j = (lex + g.bstride[MU]) >> 1;
-      ld_buf(src, g.Hd, j, psi);
-      project<MU, -1>(psi, h);
+  Spinor<float> psi;
+  Half<float> h, uh;
+  if ((fwd >> MU) & 1u) {
+    int j = (lex + g.bstride[MU]) >> 1;
+    ld_buf(src, g.Hd, j, psi);
+    project<MU, -1>(psi, h);
+    if constexpr (H2) {
       HalfH2 hh, oh;
       pack_h2(h, hh);
       su3_h2<false>(reinterpret_cast<const __half2*>(M.lk) + MU * 9 * g.Vd + r_self, g.Vd, hh, oh);
       unpack_h2(oh, uh);
-      accum_recon<MU, -1>(acc, uh);
+    } else {
+      Link<float> L;
+      M.link(MU, r_self, L);
+      su3_mul(L, h, uh);
     }
-    if (hb) {
-      int j = (lex - g.bstride[MU]) >> 1;
-      ld_buf(src, g.Hd, j, psi);
-      project<MU, +1>(psi, h);
+    accum_recon<MU, -1>(acc, uh);
+  }
+  if ((bwd >> MU) & 1u) {
+    int j = (lex - g.bstride[MU]) >> 1;
+    ld_buf(src, g.Hd, j, psi);
+    project<MU, +1>(psi, h);
+    if constexpr (H2) {
       HalfH2 hh, oh;
       pack_h2(h, hh);
       su3_h2<true>(reinterpret_cast<const __half2*>(M.lk) + MU * 9 * g.Vd + (1 - p) * g.Hd + j, g.Vd, hh, oh);
       unpack_h2(oh, uh);
-      accum_recon<MU, +1>(acc, uh);
+    } else {
+      Link<float> L;
+      M.link(MU, (1 - p) * g.Hd + j, L);
+      su3_dag_mul(L, h, uh);
     }
+    accum_recon<MU, +1>(acc, uh);
   }
 }
 
