@@ -288,7 +288,7 @@ def main():
     ap.add_argument("--only-mixed", action="store_true", help="time the mixed solve only (profiling runs)")
     ap.add_argument("--case", default="solve",
                     choices=["solve", "sap", "dslash", "sap_lattices", "workload_solve", "bicgstab",
-                             "lattices_solve"],
+                             "lattices_solve", "lowmode", "mg"],
                     help="sap / dslash: time one kernel alone on --lattice (kernel studies, ncu captures)")
     ap.add_argument("--lattice", default="32,32,32,64")
     ap.add_argument("--domain", default="", help="kernel studies: domain shape (default: the workload's)")
@@ -300,6 +300,13 @@ def main():
     ap.add_argument("--m", type=int, default=0, help="workload_solve: basis size (0: the workload's)")
     ap.add_argument("--kappa", type=float, default=0.0, help="bicgstab: kappa (0: the workload's)")
     ap.add_argument("--max-iter", type=int, default=4000, help="bicgstab: BiCGstab iterations allowed")
+    ap.add_argument("--mg-ntv", type=int, default=8, help="mg: test vectors")
+    ap.add_argument("--mg-setup-iters", type=int, default=4, help="mg: Schwarz applications per test vector")
+    ap.add_argument("--mg-coarse-m", type=int, default=16, help="mg: GMRES steps per coarse cycle")
+    ap.add_argument("--mg-cycles", type=int, default=1, help="mg: coarse GMRES cycles")
+    ap.add_argument("--mg-smooth", type=int, default=0, help="mg: smoother Schwarz cycles (0: the workload's)")
+    ap.add_argument("--mg-m", type=int, default=16, help="mg: outer basis size")
+    ap.add_argument("--mg-k", type=int, default=4, help="mg: outer deflation vectors")
     args = ap.parse_args()
     if not args.only_mixed:
         args.warmup = max(args.warmup, 3)   # profiling runs (--only-mixed) may skip the warm-up
@@ -330,6 +337,10 @@ def main():
         return bicgstab_case(args)
     if args.case == "lattices_solve":
         return lattices_solve_case(args)
+    if args.case == "lowmode":
+        return lowmode_case(args)
+    if args.case == "mg":
+        return mg_case(args)
     if args.case != "solve":
         return kernel_case(args, local)
 
@@ -457,7 +468,7 @@ def main():
                      "frac_of_unit_count_peak": sap_tflops / fp32_units,
                      "peak_clocks": peak_clocks,
                      "flops_per_launch": sap_flops_launch, "launch_ms": 1e3 * sap_launch_s},
-        "dslash": {"kernel": "apply_A_kernel<float>", "bound": "hbm", "achieved": dsl_gbs, "peak": hbm,
+        "dslash": {"kernel": fp32_operator_kernel(w.domain), "bound": "hbm", "achieved": dsl_gbs, "peak": hbm,
                    "unit": "GB/s", "frac": dsl_gbs / hbm, "traffic": dsl_traffic, "launch_ms": 1e3 * a_launch_s,
                    "bytes_per_launch": dslash_bytes_per_site("fp32") * V, "peak_note": "of measured (MEASURED_PEAKS hbm_gbs)"},
         ("fp16_f32arith_form" if args.sap_prec == "half2" else "half2_form"): {
@@ -545,11 +556,18 @@ def kernel_case(args, local):
     else:
         # per right-hand side the batch reads the links and clover once per pair
         per_site = dslash_bytes_per_site("fp32") if nr == 1 else (72 + 72) * 4 / 2 + 48 * 4
-        out = {"case": "apply_A_kernel<float>" if nr == 1 else "apply_A_multi_kernel<float,2>", "nrhs": nr,
+        out = {"case": fp32_operator_kernel(w.domain) if nr == 1 else "apply_A_multi_kernel<float,2>", "nrhs": nr,
                "lattice": dims, "launch_ms": 1e3 * launch_s,
                "ms_per_rhs": 1e3 * launch_s / nr,
                "gbs_algorithmic": per_site * V * nr / launch_s / 1e9}
     print(json.dumps(out))
+
+
+def fp32_operator_kernel(domain):
+    """Name of the FP32 operator kernel the library launches for this domain shape: the
+    8x4x4x4 and 4x4x4x4 shapes have compile-time specialisations."""
+    shape = {(8, 4, 4, 4): 1, (4, 4, 4, 4): 2}.get(tuple(domain), 0)
+    return f"apply_A_shape_kernel<{shape}>" if shape else "apply_A_kernel<float>"
 
 
 def lattices_case(args):
@@ -721,6 +739,149 @@ def lattices_solve_case(args):
         its += i1.iterations
     out["per_lattice"] = {"iterations": its, "solve_s": tot, "true_rel_residual": worst}
     out["device_gb_in_use"] = (lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info())
+    print(json.dumps(out))
+
+
+def lowmode_case(args):
+    """The smallest |eigenvalue| of the Hermitian gamma5 A of a workload (48^3x96 by
+    default), which the near-critical workload asks to be about 1e-3: power iteration on
+    (gamma5 A)^-2 = (A^dag A)^-1, each step two solves of A (dd_solve, mixed form, the
+    workload's parameters) with gamma5 between them; the Rayleigh quotient after --steps
+    iterations bounds min |lambda(gamma5 A)| from above.  The free-field value at the same
+    mass, antiperiodic time, is reported beside it."""
+    import torch
+
+    import synth
+    from paper_1412_2629_gb300 import dd
+    w = synth.WORKLOADS[args.workload]
+    kappa = args.kappa or w.kappa
+    st = torch.cuda.current_stream()
+    U = synth.make_gauge(w, device="cuda")
+    ctx = dd.Context(w.dims, w.domain, True, st.cuda_stream)
+    ctx.dd_load_gauge(torch.view_as_real(U).contiguous(), dd.DD_DEVICE)
+    ctx.dd_build_clover(kappa, w.csw)
+    del U
+    torch.cuda.empty_cache()
+    g5 = torch.tensor([1.0, 1.0, -1.0, -1.0], dtype=torch.float64, device="cuda").view(4, 1, 1)
+    x = torch.view_as_real(torch.from_numpy(synth.make_sources(w)[0])).cuda().contiguous()
+    x /= x.norm()
+    kw = dict(where=dd.DD_DEVICE, tol=1e-9, m=w.m, k=w.k, max_iter=20000, i_schwarz=w.i_schwarz,
+              i_domain=w.i_domain)
+    hist, iters, t0 = [], 0, time.perf_counter()
+    for _ in range(args.steps):
+        y = torch.zeros_like(x)
+        iters += ctx.dd_solve((g5 * x).contiguous(), y, **kw).iterations      # y = A^-1 g5 x
+        z = torch.zeros_like(x)
+        iters += ctx.dd_solve((g5 * y).contiguous(), z, **kw).iterations      # z = A^-1 g5 y
+        rq = float((x * z).sum())                                              # <x, (A^dag A)^-1 x>, |x| = 1
+        hist.append(1.0 / math.sqrt(rq))
+        x = z / z.norm()
+    L = w.dims
+    m0 = 1.0 / (2.0 * kappa) - 4.0
+    # free field: A(p) = m0 + sum(1 - cos p) + i gamma.sin p, |lambda|^2 = (m0 + sum(1-cos))^2 + sum sin^2
+    free = min(math.sqrt((m0 + sum(1 - math.cos(p) for p in ps)) ** 2 + sum(math.sin(p) ** 2 for p in ps))
+               for ps in [(0.0, 0.0, 0.0, math.pi / L[3]), (0.0, 0.0, 0.0, -math.pi / L[3])])
+    out = {"case": "lowmode", "workload": w.name, "kappa": kappa, "csw": w.csw, "power_steps": args.steps,
+           "min_abs_lambda_g5A_upper_bound": hist[-1], "history": hist, "solve_iterations": iters,
+           "seconds": time.perf_counter() - t0, "free_field_min_abs_lambda": free, "bare_mass": m0}
+    print(json.dumps(out))
+
+
+def mg_case(args):
+    """The Schwarz method as the smoother of a two-level aggregation multigrid (the use of
+    domain-decomposition preconditioners in the paper's related work, Sec. V) on the
+    benchmark's lattice (--workload; default 32^3x64): set-up time, time-to-solution with
+    FGMRES-DR around the two-level method against the benchmark's SAP-FGMRES-DR solve on the
+    same source, and the multigrid kernels alone (CUDA events; HBM roofline of the
+    restriction and prolongation, which stream the interpolation)."""
+    import torch
+
+    import synth
+    from paper_1412_2629_gb300 import dd
+    base = synth.WORKLOADS[args.workload if args.workload in synth.WORKLOADS else WORKLOAD]
+    kappa = args.kappa or base.kappa
+    st = torch.cuda.current_stream()
+    U, f = make_inputs(base, "cuda")
+    ctx = dd.Context(base.dims, base.domain, True, st.cuda_stream)
+    ctx.dd_load_gauge(torch.view_as_real(U).contiguous(), dd.DD_DEVICE)
+    ctx.dd_build_clover(kappa, base.csw)
+    del U
+    torch.cuda.empty_cache()
+    ntv = args.mg_ntv
+    smooth = args.mg_smooth or base.i_schwarz
+    tv = torch.empty((ntv,) + tuple(base.dims[::-1]) + (4, 3, 2), dtype=torch.float64, device="cuda")
+    for k in range(ntv):
+        tv[k].copy_(torch.view_as_real(torch.from_numpy(synth.gaussian_source(base.dims, 1000 + k))))
+    setup_s = ctx.dd_mg_setup(tv, ntv, dd.DD_DEVICE, setup_iters=args.mg_setup_iters, coarse_m=args.mg_coarse_m,
+                              coarse_cycles=args.mg_cycles, i_schwarz=smooth, i_domain=base.i_domain,
+                              storage_prec=dd.DD_PREC_FP16)
+    del tv
+    torch.cuda.empty_cache()
+    fd = torch.view_as_real(torch.from_numpy(f)).cuda().contiguous()
+    xd = torch.zeros_like(fd)
+    out = {"case": "mg", "workload": base.name, "kappa": kappa, "csw": base.csw, "n_tv": ntv,
+           "setup_iters": args.mg_setup_iters, "coarse_m": args.mg_coarse_m, "coarse_cycles": args.mg_cycles,
+           "smoother": {"i_schwarz": smooth, "i_domain": base.i_domain, "storage": "fp16"},
+           "outer": {"m": args.mg_m, "k": args.mg_k}, "setup_s": setup_s}
+    solves = []
+    for rep in range(max(args.steps, 1) + 1):      # the first solve captures the step graphs
+        xd.zero_()
+        torch.cuda.synchronize()
+        info = ctx.dd_solve_mg(fd, xd, where=dd.DD_DEVICE, tol=base.tol, m=args.mg_m, k=args.mg_k,
+                               max_iter=args.max_iter, check=False)
+        if rep > 0:
+            solves.append(info)
+    best = min(solves, key=lambda i: i.t_total)
+    out["mg_solve"] = {"status": best.status, "iterations": best.iterations, "restarts": best.restarts,
+                       "true_rel_residual": best.true_rel_residual, "solve_s": best.t_total,
+                       "t_A_s": best.t_A, "t_M_s": best.t_M, "t_GS_s": best.t_GS,
+                       "median_solve_s": statistics.median(i.t_total for i in solves)}
+    ref = []
+    for rep in range(2):
+        xd.zero_()
+        torch.cuda.synchronize()
+        ref.append(ctx.dd_solve(fd, xd, where=dd.DD_DEVICE, tol=base.tol, m=base.m, k=base.k, max_iter=5000,
+                                i_schwarz=base.i_schwarz, i_domain=base.i_domain, check=False))
+    r = min(ref, key=lambda i: i.t_total)
+    out["sap_solve"] = {"iterations": r.iterations, "true_rel_residual": r.true_rel_residual, "solve_s": r.t_total,
+                        "m": base.m, "k": base.k}
+    out["speedup_mg_over_sap"] = r.t_total / best.t_total
+    # kernels alone
+    V = int(np.prod(base.dims))
+    nd = V // int(np.prod(base.domain))
+    n_f = V * 24
+    a = torch.randn(n_f, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    cvec = torch.randn(nd * 2 * ntv * 2, dtype=torch.float32, device="cuda")
+    cout = torch.empty_like(cvec)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6782.8)
+    t_r = timed(lambda: ctx.dd_mg_restrict(a, cvec))
+    t_p = timed(lambda: ctx.dd_mg_prolong(cvec, b))
+    t_c = timed(lambda: ctx.dd_mg_coarse_apply(cvec, cout))
+    t_s = timed(lambda: ctx.dd_mg_coarse_solve(cvec, cout), reps=5)
+    t_b = timed(lambda: ctx.dd_mg_precondition(a, b, dd.DD_LAYOUT_INTERNAL), reps=5)
+    bytes_rp = (ntv + 1) * V * 96            # interpolation plus one FP32 field
+    dc_bytes = nd * 9 * (2 * ntv) ** 2 * 8
+    out["kernels"] = {
+        "restrict_ms": t_r, "restrict_gbs": bytes_rp / t_r / 1e6, "prolong_ms": t_p,
+        "prolong_gbs": bytes_rp / t_p / 1e6, "hbm_peak_gbs": hbm,
+        "restrict_frac": bytes_rp / t_r / 1e6 / hbm, "prolong_frac": bytes_rp / t_p / 1e6 / hbm,
+        "coarse_apply_ms": t_c, "coarse_operator_bytes": dc_bytes, "coarse_apply_gbs": dc_bytes / t_c / 1e6,
+        "coarse_solve_ms": t_s, "precondition_ms": t_b,
+        "note": "host-synchronous calls: each time includes one launch and stream synchronisation"}
     print(json.dumps(out))
 
 

@@ -237,6 +237,56 @@ typedef struct {
 dd_status dd_solve_bicgstab(dd_ctx* ctx, const double* f, double* x, int where, const dd_bicgstab_params* p,
                             dd_solve_info* info);
 
+/* Two-level aggregation multigrid with the Schwarz method as its smoother.  The paper lists
+ * this use of domain-decomposition preconditioners among related work (Sec. V: algebraic
+ * multigrid solvers whose smoother is a Schwarz method); the method here is the plain
+ * two-level form of those works:
+ *   - aggregates are the context's Schwarz domains; each aggregate and chirality (spins
+ *     0, 1: gamma_5 = +1; spins 2, 3: gamma_5 = -1) has n_tv coarse degrees of freedom, so
+ *     the coarse lattice is the lattice of domains with nc = 2 n_tv unknowns per site;
+ *   - the interpolation P is built from n_tv test vectors, each first replaced by M_sap v
+ *     setup_iters times (M_sap: the smoother's Schwarz method, at least one cycle), then
+ *     made orthonormal in order on every (aggregate, chirality) (Gram-Schmidt: the Q of a
+ *     QR factorisation with positive diagonal);
+ *   - the coarse operator is D_c = P^H A P, a nearest-neighbour stencil of nc x nc blocks
+ *     on the lattice of domains, built in FP32;
+ *   - one application of the preconditioner to v: e_c ~ D_c^{-1} P^H v by coarse_cycles
+ *     cycles of GMRES(coarse_m) from zero (FP32 vectors, FP64 sums and least squares, a
+ *     fixed number of steps), x = P e_c, then z = x + M_sap (v - A x) with the smoother's
+ *     i_schwarz Schwarz cycles (0: no smoothing).
+ * Coarse vectors (device, FP32 complex as re, im pairs): [domain][chirality][k], domains
+ * numbered like the internal layout (x fastest over L_mu / b_mu domains per direction). */
+typedef struct {
+  int n_tv;            /* test vectors, 1..16 */
+  int setup_iters;     /* Schwarz applications to each test vector before P is built (>= 0) */
+  int coarse_m;        /* GMRES steps per coarse cycle, 1..63 */
+  int coarse_cycles;   /* coarse GMRES cycles per application (>= 1) */
+  dd_sap_params smoother;   /* Schwarz form of the smoother and of the set-up; i_schwarz >= 0 */
+} dd_mg_params;
+
+/* Build P and D_c from n_tv test vectors tv (canonical FP64 fields one after another, host
+ * or device per `where`; the caller chooses them, e.g. Gaussian noise) with the context's
+ * gauge field and clover.  Replaces any earlier set-up (and drops the outer solver's
+ * captured steps).  Allocates n_tv + 3 FP32 fields, D_c (9 nc^2 complex per domain) and
+ * the coarse solver's buffers.  seconds (may be NULL): device time of the set-up.
+ * DD_ERR_NONFINITE when the test vectors are linearly dependent on some aggregate. */
+dd_status dd_mg_setup(dd_ctx* ctx, const double* tv, int where, const dd_mg_params* p, double* seconds);
+/* out = P^H in (in: FP32 internal-layout field; out: coarse vector), out = P in (in: coarse
+ * vector; out: FP32 internal field), y = D_c x (coarse vectors, x != y) and x ~ D_c^{-1} b
+ * (the coarse solve of one application).  Device buffers; synchronous. */
+dd_status dd_mg_restrict(dd_ctx* ctx, const float* in, float* out);
+dd_status dd_mg_prolong(dd_ctx* ctx, const float* in, float* out);
+dd_status dd_mg_coarse_apply(dd_ctx* ctx, const float* x, float* y);
+dd_status dd_mg_coarse_solve(dd_ctx* ctx, const float* b, float* x);
+/* out = B in, one application of the two-level preconditioner; FP32 device fields in
+ * `layout`, in != out. */
+dd_status dd_mg_precondition(dd_ctx* ctx, const float* in, float* out, int layout);
+/* A x = f with the outer solver of dd_solve (FGMRES-DR, FP64 reliable updates) and the
+ * two-level preconditioner in place of the Schwarz method; one right-hand side; p->sap is
+ * ignored.  dd_mg_setup must have been called.  t_M in info is the preconditioner's time. */
+dd_status dd_solve_mg(dd_ctx* ctx, const double* f, double* x, int where, const dd_solve_params* p,
+                      dd_solve_info* info);
+
 /* Bytes of one spinor field for a precision and layout (FP16 internal: values and norms). */
 size_t dd_spinor_bytes(const dd_ctx* ctx, int prec, int layout);
 

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["layout_clover.cu", "dslash.cu", "sap.cu", "blas.cu", "api.cu", "peak.cu", "krylov.cu"]
+SOURCES = ["layout_clover.cu", "dslash.cu", "sap.cu", "blas.cu", "api.cu", "peak.cu", "krylov.cu", "mg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -121,6 +121,23 @@ struct dd_ctx {
   void** lock_ptrs = nullptr;
   void** h_lock_ptrs = nullptr;
   int lock_cap = 0;
+  // two-level multigrid (dd_mg_setup): interpolation, coarse operator and the coarse
+  // solver's buffers; mg_active: dd_solve_mg's outer solver applies it instead of M_sap
+  struct Mg {
+    int ntv = 0, nc = 0, mc = 0, cycles = 0;
+    dd_sap_params smoother{};
+    bool ready = false;
+    float4* P = nullptr;                  // ntv FP32 internal fields
+    float2* Dc = nullptr;                 // [domain][9][nc][nc]
+    float4 *cb = nullptr, *cx = nullptr, *ct = nullptr, *cV = nullptr;   // coarse vectors, mc + 1 basis
+    double2 *partial = nullptr, *partial2 = nullptr, *hA = nullptr, *hB = nullptr, *nrm = nullptr;
+    zd *R = nullptr, *gv = nullptr, *y = nullptr;
+    LsqState* lsq = nullptr;
+    double* nu = nullptr;
+    int* state = nullptr;
+    float4 *xf = nullptr, *rf = nullptr, *ef = nullptr;   // fine work fields
+  } mg;
+  bool mg_active = false;
   std::vector<void*> allocs;
 };
 
@@ -914,6 +931,120 @@ static dd_status end_cycle(dd_ctx* c, SolverBuffers& s, int mm, const dd_solve_p
   return DD_OK;
 }
 
+// ------------------------------------------------------------------ two-level multigrid
+// The Schwarz method as the smoother of an aggregation-based two-level method (the use of
+// domain-decomposition preconditioners in the multigrid solvers of the paper's related
+// work, Sec. V).  Aggregates are the Schwarz domains; kernels in mg.cu.
+static void mg_free(dd_ctx* c) {
+  dd_ctx::Mg& M = c->mg;
+  cudaStreamSynchronize(c->st);
+  for (void* p : {(void*)M.P, (void*)M.Dc, (void*)M.cb, (void*)M.cx, (void*)M.ct, (void*)M.cV, (void*)M.partial,
+                  (void*)M.partial2, (void*)M.hA, (void*)M.hB, (void*)M.nrm, (void*)M.R, (void*)M.gv, (void*)M.y,
+                  (void*)M.lsq, (void*)M.nu, (void*)M.state, (void*)M.xf, (void*)M.rf, (void*)M.ef})
+    release(c, p);
+  M = dd_ctx::Mg();
+}
+
+static dd_status mg_alloc(dd_ctx* c, int ntv, int mc) {
+  dd_ctx::Mg& M = c->mg;
+  const Geom& g = c->g;
+  const long long n4 = g.V * 6;
+  const int nc = 2 * ntv;
+  const long long n4c = (long long)g.ND * nc / 2;
+  M.ntv = ntv;
+  M.nc = nc;
+  M.mc = mc;
+  TRY(dalloc(c, &M.P, (size_t)ntv * n4 * 16));
+  TRY(dalloc(c, &M.Dc, (size_t)g.ND * 9 * nc * nc * sizeof(float2)));
+  for (float4** q : {&M.cb, &M.cx, &M.ct}) TRY(dalloc(c, q, (size_t)n4c * 16));
+  TRY(dalloc(c, &M.cV, (size_t)(mc + 1) * n4c * 16));
+  // basis vectors past a breakdown are multiplied by zero coefficients: keep them finite
+  TRY(cuda_check(c, cudaMemsetAsync(M.cV, 0, (size_t)(mc + 1) * n4c * 16, c->st), "coarse basis"));
+  TRY(dalloc(c, &M.partial, (size_t)blas_partials_blocks() * (mc + 2) * sizeof(double2)));
+  TRY(dalloc(c, &M.partial2, (size_t)blas_partials_blocks() * sizeof(double2)));
+  for (double2** q : {&M.hA, &M.hB}) TRY(dalloc(c, q, (size_t)(mc + 2) * sizeof(double2)));
+  TRY(dalloc(c, &M.nrm, 4 * sizeof(double2)));
+  TRY(dalloc(c, &M.R, (size_t)(mc + 1) * (mc + 1) * sizeof(zd)));
+  TRY(dalloc(c, &M.gv, (size_t)(mc + 2) * sizeof(zd)));
+  TRY(dalloc(c, &M.y, (size_t)(mc + 1) * sizeof(zd)));
+  TRY(dalloc(c, &M.lsq, sizeof(LsqState)));
+  TRY(dalloc(c, &M.nu, 16));
+  TRY(dalloc(c, &M.state, 16));
+  for (float4** q : {&M.xf, &M.rf, &M.ef}) TRY(dalloc(c, q, (size_t)n4 * 16));
+  return DD_OK;
+}
+
+// cx ~ D_c^{-1} cb: `cycles` cycles of GMRES(mc) from cx = 0 on the coarse operator, FP32
+// vectors, classical Gram-Schmidt with a second pass (FP64 sums), FP64 Givens least
+// squares.  A fixed launch sequence with no host synchronisation (a cycle that reaches an
+// invariant subspace skips its remaining steps on the device), so it can be captured.
+static dd_status mg_coarse_solve(dd_ctx* c) {
+  dd_ctx::Mg& M = c->mg;
+  const Geom& g = c->g;
+  cudaStream_t st = c->st;
+  const long long n4c = (long long)g.ND * M.nc / 2;
+  auto Vc = [&](int i) { return M.cV + (long long)i * n4c; };
+  const int ldh = M.mc + 1;
+  int nk = 0;
+  for (int cyc = 0; cyc < M.cycles; ++cyc) {
+    if (cyc == 0) {
+      TRY(cuda_check(c, cudaMemcpyAsync(Vc(0), M.cb, (size_t)n4c * 16, cudaMemcpyDeviceToDevice, st), "coarse rhs"));
+    } else {
+      launch_mg_coarse_apply(g, M.Dc, M.nc, (const float2*)M.cx, (float2*)Vc(0), (const float2*)M.cb, nullptr, st);
+      ++nk;
+    }
+    nk += launch_gs_dot(Vc(0), 0, n4c, Vc(0), M.partial, nullptr, 0, st);
+    launch_gs_reduce(M.partial, 0, M.nrm, nullptr, 0, st);
+    launch_mg_beta(M.nrm, M.gv, M.mc + 2, M.nu, M.state, M.lsq, st);
+    launch_mg_scale(Vc(0), n4c, M.nu, M.state, st);
+    nk += 3;
+    for (int j = 0; j < M.mc; ++j) {
+      launch_mg_coarse_apply(g, M.Dc, M.nc, (const float2*)Vc(j), (float2*)M.ct, nullptr, M.state, st);
+      nk += 1 + launch_gs_dot(Vc(0), j + 1, n4c, M.ct, M.partial, M.state, 0, st);
+      launch_gs_reduce(M.partial, j + 1, M.hA, M.state, 0, st);
+      launch_gs_project(M.ct, M.ct, Vc(0), j + 1, n4c, M.hA, M.partial2, M.state, 0, st);
+      nk += 2 + launch_gs_dot(Vc(0), j + 1, n4c, M.ct, M.partial, M.state, 0, st);
+      launch_gs_reduce(M.partial, j + 1, M.hB, M.state, 0, st);
+      launch_gs_project(Vc(j + 1), M.ct, Vc(0), j + 1, n4c, M.hB, M.partial2, M.state, 0, st);
+      launch_gs_reduce(M.partial2, 0, M.nrm, M.state, 0, st);
+      launch_mg_hcol(M.R, ldh, j, M.hA, M.hB, M.nrm, M.lsq, M.gv, M.nu, M.state, st);
+      launch_mg_scale(Vc(j + 1), n4c, M.nu, M.state, st);
+      nk += 5;
+    }
+    launch_mg_lsq(M.R, ldh, M.mc, M.gv, M.state, M.y, st);
+    ++nk;
+    if (cyc == 0) {
+      nk += launch_recombine(M.cx, Vc(0), M.mc, 1, n4c, (const double2*)M.y, M.mc, st);
+    } else {
+      nk += launch_recombine(M.ct, Vc(0), M.mc, 1, n4c, (const double2*)M.y, M.mc, st);
+      launch_mg_axpy(M.cx, M.ct, n4c, st);
+      ++nk;
+    }
+  }
+  return launched(c, nk);
+}
+
+// z = B v, one application of the two-level preconditioner: coarse correction
+// x = P D_c^{-1} P^H v (approximate coarse solve), then the smoother's Schwarz cycles on
+// the remaining residual, z = x + M_sap (v - A x).  vscale (device scalar, optional): the
+// input is v * (*vscale) (B is linear, so the scale is applied to z).
+static dd_status mg_run(dd_ctx* c, const float4* v, float4* z, const float* vscale = nullptr) {
+  dd_ctx::Mg& M = c->mg;
+  const Geom& g = c->g;
+  launch_mg_restrict(g, v, M.P, M.ntv, (float2*)M.cb, nullptr, c->st);
+  TRY(launched(c));
+  TRY(mg_coarse_solve(c));
+  launch_mg_prolong(g, (const float2*)M.cx, M.P, M.ntv, M.xf, c->st);
+  TRY(launched(c));
+  const bool smooth = M.smoother.i_schwarz > 0;
+  if (smooth) {
+    TRY(apply_internal(c, M.xf, M.rf, P32, v));   // rf = v - A xf
+    TRY(sap_run(c, M.rf, M.ef, &M.smoother));
+  }
+  launch_mg_combine(z, M.xf, smooth ? M.ef : nullptr, g.V * 6, vscale, c->st);
+  return launched(c);
+}
+
 static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_solve_info* info) {
   SolverBuffers& s = c->sv;
   const Geom& g = c->g;
@@ -957,7 +1088,12 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
       k1[0] = 1;
       k2[0] = 2;
       cudaEventRecord(e0, c->st);
-      TRY(graphed(c, k0, [&]() { return sap_run(c, Vv(j), Zv(j), &p->sap, 1, s.vscale + j); }));
+      if (c->mg_active) {
+        k0[0] = 7;
+        TRY(graphed(c, k0, [&]() { return mg_run(c, Vv(j), Zv(j), s.vscale + j); }));
+      } else {
+        TRY(graphed(c, k0, [&]() { return sap_run(c, Vv(j), Zv(j), &p->sap, 1, s.vscale + j); }));
+      }
       cudaEventRecord(e1, c->st);
       TRY(graphed(c, k1, [&]() { return apply_internal(c, Zv(j), s.w, P32); }));
       cudaEventRecord(e2, c->st);
@@ -2309,4 +2445,153 @@ extern "C" dd_status dd_sap_precondition_noalloc(dd_ctx* c, const float* in, flo
   TRY(cuda_check(c, cudaStreamSynchronize(c->st), "sap_noalloc"));
   if (e) return fail(c, DD_ERR_TIMEOUT, "a bounded wait for the domain's staged data ran out");
   return DD_OK;
+}
+
+// ------------------------------------------------------------------ two-level multigrid: C ABI
+extern "C" dd_status dd_mg_setup(dd_ctx* c, const double* tv, int where, const dd_mg_params* p, double* seconds) {
+  if (!c || !tv || !p) return DD_ERR_INVALID;
+  if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
+  if (p->n_tv < 1 || p->n_tv > MG_MAXTV || p->setup_iters < 0 || p->coarse_m < 1 || p->coarse_m > DD_MAXM - 1 ||
+      p->coarse_cycles < 1 || p->smoother.i_schwarz < 0)
+    return fail(c, DD_ERR_INVALID, "bad multigrid parameters");
+  // the smoother's Schwarz form (at least one cycle when the set-up smooths test vectors)
+  dd_sap_params sm = p->smoother;
+  if (sm.i_schwarz > 0 || p->setup_iters > 0) {
+    dd_sap_params chk = sm;
+    if (chk.i_schwarz < 1) chk.i_schwarz = 1;
+    TRY(check_sap_params(c, &chk));
+    if (chk.i_domain < 1) return fail(c, DD_ERR_INVALID, "i_domain must be >= 1");
+  }
+  const Geom& g = c->g;
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  cudaEventRecord(t0, c->st);
+  drop_graphs(c);   // captured solver steps may hold the previous set-up's buffers
+  mg_free(c);
+  TRY(mg_alloc(c, p->n_tv, p->coarse_m));
+  dd_ctx::Mg& M = c->mg;
+  M.cycles = p->coarse_cycles;
+  M.smoother = sm;
+  const long long n4 = g.V * 6;
+  const size_t cb = (size_t)g.V * 24 * 8;
+  double* stage = nullptr;
+  TRY(dalloc(c, &stage, cb));
+  dd_status rc = DD_OK;
+  const cudaMemcpyKind kind = where == DD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  for (int k = 0; k < p->n_tv && rc == DD_OK; ++k) {
+    rc = cuda_check(c, cudaMemcpyAsync(stage, tv + (size_t)k * g.V * 24, cb, kind, c->st), "test vector");
+    if (rc == DD_OK) {
+      launch_pack_spinor(g, stage, P64, view(g, M.P + k * n4, P32), c->st);
+      rc = launched(c);
+    }
+  }
+  // test vectors <- M_sap test vectors, setup_iters times
+  dd_sap_params ss = sm;
+  if (ss.i_schwarz < 1) ss.i_schwarz = 1;
+  for (int it = 0; it < p->setup_iters && rc == DD_OK; ++it)
+    for (int k = 0; k < p->n_tv && rc == DD_OK; ++k) {
+      rc = sap_run(c, M.P + k * n4, M.ef, &ss);
+      if (rc == DD_OK)
+        rc = cuda_check(c, cudaMemcpyAsync(M.P + k * n4, M.ef, (size_t)n4 * 16, cudaMemcpyDeviceToDevice, c->st),
+                        "smoothed test vector");
+    }
+  if (rc == DD_OK && p->setup_iters > 0) rc = sap_error_flag(c);
+  int bad = 0;
+  if (rc == DD_OK) rc = cuda_check(c, cudaMemsetAsync(M.state, 0, 16, c->st), "status");
+  if (rc == DD_OK) {
+    launch_mg_orthonormalize(g, M.P, p->n_tv, M.state, c->st);
+    rc = launched(c);
+  }
+  if (rc == DD_OK) rc = cuda_check(c, cudaMemcpyAsync(&bad, M.state, sizeof(int), cudaMemcpyDeviceToHost, c->st), "status");
+  if (rc == DD_OK) rc = cuda_check(c, cudaStreamSynchronize(c->st), "orthonormalise");
+  if (rc == DD_OK && bad) rc = fail(c, DD_ERR_NONFINITE, "test vectors are linearly dependent on a domain");
+  if (rc == DD_OK) {
+    launch_mg_coarse_build(g, c->U32, c->C32, M.P, p->n_tv, M.Dc, c->st);
+    rc = launched(c);
+  }
+  cudaEventRecord(t1, c->st);
+  if (rc == DD_OK) rc = cuda_check(c, cudaStreamSynchronize(c->st), "coarse operator");
+  release(c, stage);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, t0, t1);
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (seconds) *seconds = ms * 1e-3;
+  if (rc != DD_OK) {
+    mg_free(c);
+    return rc;
+  }
+  M.ready = true;
+  return DD_OK;
+}
+
+static dd_status mg_ready(dd_ctx* c) {
+  if (!c->mg.ready) return fail(c, DD_ERR_INVALID, "dd_mg_setup has not been called");
+  return DD_OK;
+}
+
+extern "C" dd_status dd_mg_restrict(dd_ctx* c, const float* in, float* out) {
+  if (!c || !in || !out) return DD_ERR_INVALID;
+  TRY(mg_ready(c));
+  launch_mg_restrict(c->g, (const float4*)in, c->mg.P, c->mg.ntv, (float2*)out, nullptr, c->st);
+  TRY(launched(c));
+  return cuda_check(c, cudaStreamSynchronize(c->st), "restrict");
+}
+
+extern "C" dd_status dd_mg_prolong(dd_ctx* c, const float* in, float* out) {
+  if (!c || !in || !out) return DD_ERR_INVALID;
+  TRY(mg_ready(c));
+  launch_mg_prolong(c->g, (const float2*)in, c->mg.P, c->mg.ntv, (float4*)out, c->st);
+  TRY(launched(c));
+  return cuda_check(c, cudaStreamSynchronize(c->st), "prolong");
+}
+
+extern "C" dd_status dd_mg_coarse_apply(dd_ctx* c, const float* x, float* y) {
+  if (!c || !x || !y || x == y) return DD_ERR_INVALID;
+  TRY(mg_ready(c));
+  launch_mg_coarse_apply(c->g, c->mg.Dc, c->mg.nc, (const float2*)x, (float2*)y, nullptr, nullptr, c->st);
+  TRY(launched(c));
+  return cuda_check(c, cudaStreamSynchronize(c->st), "coarse apply");
+}
+
+extern "C" dd_status dd_mg_coarse_solve(dd_ctx* c, const float* b, float* x) {
+  if (!c || !b || !x) return DD_ERR_INVALID;
+  TRY(mg_ready(c));
+  const size_t bytes = (size_t)c->g.ND * c->mg.nc * sizeof(float2);
+  TRY(cuda_check(c, cudaMemcpyAsync(c->mg.cb, b, bytes, cudaMemcpyDeviceToDevice, c->st), "coarse rhs"));
+  TRY(mg_coarse_solve(c));
+  TRY(cuda_check(c, cudaMemcpyAsync(x, c->mg.cx, bytes, cudaMemcpyDeviceToDevice, c->st), "coarse solution"));
+  return cuda_check(c, cudaStreamSynchronize(c->st), "coarse solve");
+}
+
+extern "C" dd_status dd_mg_precondition(dd_ctx* c, const float* in, float* out, int layout) {
+  if (!c || !in || !out || in == out) return DD_ERR_INVALID;
+  TRY(mg_ready(c));
+  if (layout == DD_LAYOUT_INTERNAL) {
+    TRY(mg_run(c, (const float4*)in, (float4*)out));
+  } else {
+    TRY(ensure_scratch(c));
+    launch_pack_spinor(c->g, in, P32, view(c->g, c->scratch_in, P32), c->st);
+    TRY(launched(c));
+    TRY(mg_run(c, (const float4*)c->scratch_in, (float4*)c->scratch_out));
+    launch_unpack_spinor(c->g, view(c->g, c->scratch_out, P32), out, P32, c->st);
+    TRY(launched(c));
+  }
+  if (c->mg.smoother.i_schwarz > 0) TRY(sap_error_flag(c));
+  return cuda_check(c, cudaStreamSynchronize(c->st), "mg precondition");
+}
+
+extern "C" dd_status dd_solve_mg(dd_ctx* c, const double* f, double* x, int where, const dd_solve_params* p,
+                                 dd_solve_info* info) {
+  if (!c || !f || !x || !p) return DD_ERR_INVALID;
+  TRY(mg_ready(c));
+  dd_solve_params q = *p;
+  // the smoother's parameters key the captured steps; the preconditioner is the two-level method
+  q.sap = c->mg.smoother;
+  if (q.sap.i_schwarz < 1) q.sap = dd_sap_params{1, 1, DD_PREC_FP16, 0, 0};
+  c->mg_active = true;
+  dd_status st = dd_solve(c, f, x, 1, where, &q, info);
+  c->mg_active = false;
+  return st;
 }

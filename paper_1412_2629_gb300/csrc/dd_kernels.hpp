@@ -137,4 +137,27 @@ struct BicgKernels {
 };
 void launch_bicg_scalars(zd* sc, int stage, cudaStream_t st);
 void launch_bicg_reset(zd* sc, cudaStream_t st);
+// ---- two-level multigrid with the Schwarz smoother (mg.cu).  Aggregates are the domains;
+// P: n_tv FP32 internal fields (column (chirality c, k) of a domain in field k's units
+// 3c..3c+2); coarse vectors float2 [domain][chirality][k]; D_c float2 [domain][9][j][i].
+constexpr int MG_MAXTV = 16;
+void launch_mg_restrict(const Geom& g, const float4* in, const float4* P, int ntv, float2* rc, const float* vscale,
+                        cudaStream_t st);
+void launch_mg_prolong(const Geom& g, const float2* ec, const float4* P, int ntv, float4* out, cudaStream_t st);
+void launch_mg_orthonormalize(const Geom& g, float4* P, int ntv, int* status, cudaStream_t st);
+void launch_mg_coarse_build(const Geom& g, const float2* U32, const float4* C32, const float4* P, int ntv, float2* Dc,
+                            cudaStream_t st);
+// y = D_c x, or y = b - D_c x when b != nullptr; skipped when gate && *gate != 0
+void launch_mg_coarse_apply(const Geom& g, const float2* Dc, int nc, const float2* x, float2* y, const float2* b,
+                            const int* gate, cudaStream_t st);
+// coarse GMRES: one-thread small steps (state[0] != 0 stops a cycle, state[1] = columns done)
+void launch_mg_beta(const double2* nrm, zd* g, int ng, double* nu, int* state, LsqState* lsq, cudaStream_t st);
+void launch_mg_hcol(zd* R, int ldh, int j, const double2* hA, const double2* hB, const double2* nrm, LsqState* lsq,
+                    zd* g, double* nu, int* state, cudaStream_t st);
+void launch_mg_lsq(const zd* R, int ldh, int mc, const zd* g, const int* state, zd* y, cudaStream_t st);
+void launch_mg_scale(float4* v, long long n4, const double* nu, const int* gate, cudaStream_t st);
+void launch_mg_axpy(float4* x, const float4* t, long long n4, cudaStream_t st);
+// z = vscale (x + e); e and vscale optional
+void launch_mg_combine(float4* z, const float4* x, const float4* e, long long n4, const float* vscale,
+                       cudaStream_t st);
 }  // namespace dd

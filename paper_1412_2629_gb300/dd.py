@@ -36,6 +36,11 @@ class dd_bicgstab_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int), ("inner_tol", C.c_double)]
 
 
+class dd_mg_params(C.Structure):
+    _fields_ = [("n_tv", C.c_int), ("setup_iters", C.c_int), ("coarse_m", C.c_int), ("coarse_cycles", C.c_int),
+                ("smoother", dd_sap_params)]
+
+
 class dd_solve_info(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("restarts", C.c_int),
                 ("reliable_updates", C.c_int), ("deflated_restarts", C.c_int),
@@ -90,6 +95,13 @@ def lib():
             "dd_deflate_host": (I, [I, I, P, P, P, P, P, P, P]),
             "dd_deflate_device": (I, [I, I, P, P, P, P, P, P, P, C.POINTER(D)]),
             "dd_fp32_peak": (I, [I, C.POINTER(D), C.POINTER(D)]),
+            "dd_mg_setup": (I, [P, P, I, C.POINTER(dd_mg_params), C.POINTER(D)]),
+            "dd_mg_restrict": (I, [P, P, P]),
+            "dd_mg_prolong": (I, [P, P, P]),
+            "dd_mg_coarse_apply": (I, [P, P, P]),
+            "dd_mg_coarse_solve": (I, [P, P, P]),
+            "dd_mg_precondition": (I, [P, P, P, I]),
+            "dd_solve_mg": (I, [P, P, P, I, C.POINTER(dd_solve_params), C.POINTER(dd_solve_info)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -196,6 +208,39 @@ class Context:
         p = dd_bicgstab_params(tol, max_iter, precision, inner_tol)
         info = dd_solve_info()
         s = lib().dd_solve_bicgstab(self._h, _ptr(f), _ptr(x), where, C.byref(p), C.byref(info))
+        if check:
+            self._check(s)
+        return info
+
+    def dd_mg_setup(self, tv, n_tv, where=DD_HOST, setup_iters=4, coarse_m=16, coarse_cycles=1, i_schwarz=2,
+                    i_domain=4, storage_prec=DD_PREC_FP16, threads_per_site=0):
+        """Two-level multigrid set-up from n_tv canonical FP64 test vectors; returns the
+        set-up's device time in seconds."""
+        p = dd_mg_params(n_tv, setup_iters, coarse_m, coarse_cycles,
+                         dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site, 0))
+        sec = C.c_double()
+        self._check(lib().dd_mg_setup(self._h, _ptr(tv), where, C.byref(p), C.byref(sec)))
+        return sec.value
+
+    def dd_mg_restrict(self, inp, out):
+        return self._check(lib().dd_mg_restrict(self._h, _ptr(inp), _ptr(out)))
+
+    def dd_mg_prolong(self, inp, out):
+        return self._check(lib().dd_mg_prolong(self._h, _ptr(inp), _ptr(out)))
+
+    def dd_mg_coarse_apply(self, x, y):
+        return self._check(lib().dd_mg_coarse_apply(self._h, _ptr(x), _ptr(y)))
+
+    def dd_mg_coarse_solve(self, b, x):
+        return self._check(lib().dd_mg_coarse_solve(self._h, _ptr(b), _ptr(x)))
+
+    def dd_mg_precondition(self, inp, out, layout=DD_LAYOUT_CANONICAL):
+        return self._check(lib().dd_mg_precondition(self._h, _ptr(inp), _ptr(out), layout))
+
+    def dd_solve_mg(self, f, x, where=DD_HOST, tol=1e-10, m=16, k=0, max_iter=1000, check=True):
+        p = dd_solve_params(tol, m, k, max_iter, dd_sap_params(1, 1, DD_PREC_FP16, 0, 0))
+        info = dd_solve_info()
+        s = lib().dd_solve_mg(self._h, _ptr(f), _ptr(x), where, C.byref(p), C.byref(info))
         if check:
             self._check(s)
         return info
