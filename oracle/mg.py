@@ -12,8 +12,10 @@ restate the two-level aggregation method of those works in its plainest form:
     and each chirality (spins 0, 1: gamma_5 = +1; spins 2, 3: gamma_5 = -1 in the chiral
     basis of the operator) carries n_tv coarse degrees of freedom, so the interpolation
     commutes with gamma_5;
-  * test vectors: n_tv fields v_k, each replaced by M_sap v_k `setup_iters` times (the
-    Schwarz method as an approximate inverse moves them towards the low modes of A);
+  * test vectors: n_tv fields v_k, each replaced `setup_iters` times either by M_sap v_k
+    (mode "inverse": the Schwarz method as an approximate inverse) or by v_k - M_sap A v_k
+    (mode "nullspace": one Schwarz cycle set on A v = 0 from v_k, the smoother's error
+    propagator, which removes what the smoother resolves and keeps the low modes of A);
   * interpolation P: on every (aggregate, chirality) the pieces of v_1 .. v_n made
     orthonormal in order (the Q of a QR factorisation whose R has a positive diagonal);
   * coarse operator: D_c = P^H A P (Galerkin);
@@ -147,16 +149,31 @@ def two_level(U, kappa, csw, P, agg: Aggregates, Dc, b, dom: DD.Domains, i_schwa
     return x
 
 
-def setup(U, kappa, csw, tv0, agg: Aggregates, setup_iters: int, dom: DD.Domains, i_schwarz: int, i_domain: int,
-          F=None, solver=None):
-    """Test vectors smoothed by the Schwarz method, the interpolation and D_c.
-    Returns (P, Dc)."""
+def smooth_test_vectors(U, kappa, csw, tv0, setup_iters: int, dom: DD.Domains, i_schwarz: int, i_domain: int,
+                        mode: str = "inverse", F=None, solver=None):
+    """The test vectors after `setup_iters` smoothing steps (see the module docstring)."""
+    if mode not in ("inverse", "nullspace"):
+        raise ValueError(mode)
     if F is None and csw != 0.0:
         F = W.field_strength(U)
     if solver is None and setup_iters > 0:
         solver = DD.BlockSolver(U, F, kappa, csw, dom)
     tv = [np.array(v, dtype=np.complex128) for v in tv0]
     for _ in range(setup_iters):
-        tv = [DD.sap(U, F, v, kappa, csw, dom, i_schwarz, i_domain, solver=solver) for v in tv]
+        if mode == "inverse":
+            tv = [DD.sap(U, F, v, kappa, csw, dom, i_schwarz, i_domain, solver=solver) for v in tv]
+        else:
+            tv = [v - DD.sap(U, F, W.apply_A(U, v, kappa, csw, F), kappa, csw, dom, i_schwarz, i_domain,
+                             solver=solver) for v in tv]
+    return tv
+
+
+def setup(U, kappa, csw, tv0, agg: Aggregates, setup_iters: int, dom: DD.Domains, i_schwarz: int, i_domain: int,
+          F=None, solver=None, mode: str = "inverse"):
+    """Test vectors smoothed by the Schwarz method, the interpolation and D_c.
+    Returns (P, Dc)."""
+    if F is None and csw != 0.0:
+        F = W.field_strength(U)
+    tv = smooth_test_vectors(U, kappa, csw, tv0, setup_iters, dom, i_schwarz, i_domain, mode, F, solver)
     P = interpolation(tv, agg)
     return P, coarse_matrix(U, kappa, csw, P, agg, F)

@@ -175,3 +175,25 @@ def test_smoothed_test_vectors_are_sap_images(lat4):
         s = DD.sap(U, F, v, KAPPA, CSW, dom, 2, 3).ravel()
         assert np.abs(Pm @ (Pm.conj().T @ s) - s).max() < 1e-12 * np.abs(s).max()
     assert Dc.shape == (agg.n * 2 * len(tv),) * 2
+
+
+def test_nullspace_smoothing_is_schwarz_iteration_on_zero_rhs(lat4):
+    """Mode "nullspace": v - M_sap A v equals the multiplicative Schwarz iteration on
+    A x = 0 started from x = v, written out as block Gauss-Seidel with exact block solves
+    (dense blocks of the site-by-site sparse A)."""
+    dims, U, F, tv = lat4
+    dom = DD.Domains(dims, (2, 2, 2, 2))
+    ex = DD.ExactBlockSolver(U, F, KAPPA, CSW, dom)
+    got = MG.smooth_test_vectors(U, KAPPA, CSW, tv[:1], 1, dom, 2, 0, "nullspace", F, solver=ex)[0]
+    A = DN.assemble_A(U, KAPPA, CSW).toarray()
+    x = tv[0].ravel().copy()
+    blocks = {}
+    for colour in (0, 1):
+        for d in np.unique(dom.domain[dom.colour == colour]):
+            blocks.setdefault(colour, []).append(np.nonzero(np.repeat((dom.domain == d).ravel(), 12))[0])
+    for _ in range(2):
+        for colour in (0, 1):
+            r = -A @ x
+            for idx in blocks[colour]:
+                x[idx] += np.linalg.solve(A[np.ix_(idx, idx)], r[idx])
+    assert np.abs(got.ravel() - x).max() < 1e-11 * np.abs(x).max()
