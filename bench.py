@@ -216,6 +216,72 @@ def oracle_time_sap(w):
     return time.perf_counter() - t0
 
 
+def _oracle_worker(job, barrier, out):
+    """One process of the all-cores oracle sample: load the sample fields, then (all
+    processes together, behind a barrier with a time limit) time one A and one Schwarz
+    application; the result or the error goes to the queue `out`."""
+    path_a, path_s, sap_dims, kappa, csw, domain, i_s, i_d = job
+    try:
+        from oracle import dd as DD
+        from oracle import wilson as W
+        a, sp = np.load(path_a), np.load(path_s)
+        Ua, fa, Us, fs = a["U"], a["f"], sp["U"], sp["f"]
+        Fa, Fs = W.field_strength(Ua), W.field_strength(Us)
+        dom = DD.Domains(sap_dims, domain)
+        solver = DD.BlockSolver(Us, Fs, kappa, csw, dom)
+        barrier.wait(timeout=300)
+        t0 = time.perf_counter()
+        W.apply_A(Ua, fa, kappa, csw, Fa)
+        t_a = time.perf_counter() - t0
+        barrier.wait(timeout=300)
+        t0 = time.perf_counter()
+        DD.sap(Us, Fs, fs, kappa, csw, dom, i_s, i_d, solver=solver)
+        out.put(("ok", t_a, time.perf_counter() - t0))
+    except Exception as e:   # release the others and report
+        barrier.abort()
+        out.put(("error", repr(e), 0.0))
+
+
+def oracle_all_cores(w, fields_a, fields_s):
+    """The oracle on every host core at once: one process per core (spawned, so no forked
+    CUDA state), each timing the same A and Schwarz samples concurrently.  Returns
+    (cores, seconds of A, seconds of the Schwarz application), each the slowest process's.
+    Raises RuntimeError if a process fails or the samples do not finish within 10 minutes."""
+    import multiprocessing as mp
+    import queue
+    import tempfile
+    n = os.cpu_count() or 1
+    tmp = tempfile.mkdtemp(prefix="oracle_sample_")
+    pa, ps = os.path.join(tmp, "a.npz"), os.path.join(tmp, "s.npz")
+    np.savez(pa, U=fields_a[0], f=fields_a[2])
+    np.savez(ps, U=fields_s[0], f=fields_s[2])
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(n), ctx.Queue()
+    job = (pa, ps, tuple(fields_s[2].shape[:4][::-1]), w.kappa, w.csw, w.domain, w.i_schwarz, w.i_domain)
+    procs = [ctx.Process(target=_oracle_worker, args=(job, barrier, out)) for _ in range(n)]
+    res = []
+    try:
+        for p in procs:
+            p.start()
+        deadline = time.time() + 600
+        for _ in range(n):
+            res.append(out.get(timeout=max(1.0, deadline - time.time())))
+    except queue.Empty:
+        raise RuntimeError("oracle processes did not finish within 10 minutes")
+    finally:
+        for p in procs:
+            p.join(timeout=10)
+            if p.is_alive():
+                p.kill()
+        for p in (pa, ps):
+            os.remove(p)
+        os.rmdir(tmp)
+    bad = [r for r in res if r[0] != "ok"]
+    if bad:
+        raise RuntimeError(f"oracle process failed: {bad[0][1]}")
+    return n, max(r[1] for r in res), max(r[2] for r in res)
+
+
 def oracle_solve_estimate(w, t_a, t_sap, iters, reliable):
     """Oracle seconds for the whole solve: per outer iteration one A and one Schwarz
     application, plus the FP64 residuals, each scaled per site to the workload's volume."""
@@ -305,6 +371,7 @@ def main():
     ap.add_argument("--mg-coarse-m", type=int, default=16, help="mg: GMRES steps per coarse cycle")
     ap.add_argument("--mg-cycles", type=int, default=1, help="mg: coarse GMRES cycles")
     ap.add_argument("--mg-smooth", type=int, default=0, help="mg: smoother Schwarz cycles (0: the workload's)")
+    ap.add_argument("--mg-setup-mode", type=int, default=0, help="mg: 0 v <- M v, 1 v <- v - M A v")
     ap.add_argument("--mg-m", type=int, default=16, help="mg: outer basis size")
     ap.add_argument("--mg-k", type=int, default=4, help="mg: outer deflation vectors")
     args = ap.parse_args()
@@ -440,16 +507,26 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        t_a = oracle_time_A(w, oracle_fields(w, A_SAMPLE))
+        fa = oracle_fields(w, A_SAMPLE)
+        t_a = oracle_time_A(w, fa)
         t_sap = oracle_time_sap(w)
         rel_up = mean("reliable_updates", infos)
         host = host_cpu()
-        cpu = {"value": oracle_solve_estimate(w, t_a, t_sap, iters, rel_up), "unit": "s", "cores": 1,
-               "kind": "oracle", "host": host,
-               "sample": f"FP64 oracle (numpy, one thread; host {host['model']}, {host['nproc']} cores): A on a "
-                         f"{'x'.join(map(str, A_SAMPLE))} slab ({t_a:.2f} s) and one Schwarz application on a "
-                         f"{'x'.join(map(str, SAP_SAMPLE))} slab ({t_sap:.1f} s), scaled per site to {WORKLOAD} and "
-                         f"to this solve's {iters:.0f} iterations and {rel_up:.0f} FP64 residuals"}
+        one = oracle_solve_estimate(w, t_a, t_sap, iters, rel_up)
+        # all cores: every process runs the same samples at once; n of them finish n samples
+        try:
+            n, ta_n, ts_n = oracle_all_cores(w, fa, oracle_fields(w, SAP_SAMPLE))
+        except RuntimeError as e:
+            n, ta_n, ts_n = 1, t_a, t_sap
+            print(f"all-cores oracle sample unavailable ({e}); one thread reported", file=sys.stderr)
+        alln = oracle_solve_estimate(w, ta_n / n, ts_n / n, iters, rel_up)
+        cpu = {"value": alln, "unit": "s", "cores": n, "kind": "oracle", "host": host,
+               "sample": f"FP64 oracle (numpy) on {n} processes at once (host {host['model']}, {host['nproc']} "
+                         f"cores), each timing A on a {'x'.join(map(str, A_SAMPLE))} slab ({ta_n:.2f} s) and one "
+                         f"Schwarz application on a {'x'.join(map(str, SAP_SAMPLE))} slab ({ts_n:.1f} s) "
+                         f"concurrently; the slowest process's time / {n}, scaled per site to {WORKLOAD} and to "
+                         f"this solve's {iters:.0f} iterations and {rel_up:.0f} FP64 residuals",
+               "one_thread": {"value": one, "cores": 1, "a_s": t_a, "sap_s": t_sap}}
 
     value = ms_mixed / 1e3
     out = {
@@ -814,13 +891,13 @@ def mg_case(args):
         tv[k].copy_(torch.view_as_real(torch.from_numpy(synth.gaussian_source(base.dims, 1000 + k))))
     setup_s = ctx.dd_mg_setup(tv, ntv, dd.DD_DEVICE, setup_iters=args.mg_setup_iters, coarse_m=args.mg_coarse_m,
                               coarse_cycles=args.mg_cycles, i_schwarz=smooth, i_domain=base.i_domain,
-                              storage_prec=dd.DD_PREC_FP16)
+                              storage_prec=dd.DD_PREC_FP16, setup_mode=args.mg_setup_mode)
     del tv
     torch.cuda.empty_cache()
     fd = torch.view_as_real(torch.from_numpy(f)).cuda().contiguous()
     xd = torch.zeros_like(fd)
     out = {"case": "mg", "workload": base.name, "kappa": kappa, "csw": base.csw, "n_tv": ntv,
-           "setup_iters": args.mg_setup_iters, "coarse_m": args.mg_coarse_m, "coarse_cycles": args.mg_cycles,
+           "setup_iters": args.mg_setup_iters, "setup_mode": args.mg_setup_mode, "coarse_m": args.mg_coarse_m, "coarse_cycles": args.mg_cycles,
            "smoother": {"i_schwarz": smooth, "i_domain": base.i_domain, "storage": "fp16"},
            "outer": {"m": args.mg_m, "k": args.mg_k}, "setup_s": setup_s}
     solves = []

@@ -244,10 +244,11 @@ dd_status dd_solve_bicgstab(dd_ctx* ctx, const double* f, double* x, int where, 
  *   - aggregates are the context's Schwarz domains; each aggregate and chirality (spins
  *     0, 1: gamma_5 = +1; spins 2, 3: gamma_5 = -1) has n_tv coarse degrees of freedom, so
  *     the coarse lattice is the lattice of domains with nc = 2 n_tv unknowns per site;
- *   - the interpolation P is built from n_tv test vectors, each first replaced by M_sap v
- *     setup_iters times (M_sap: the smoother's Schwarz method, at least one cycle), then
- *     made orthonormal in order on every (aggregate, chirality) (Gram-Schmidt: the Q of a
- *     QR factorisation with positive diagonal);
+ *   - the interpolation P is built from n_tv test vectors, each first replaced setup_iters
+ *     times by M_sap v (setup_mode 0: inverse iteration with the smoother's Schwarz method,
+ *     at least one cycle) or by v - M_sap A v (setup_mode 1: the smoother run on A v = 0,
+ *     which keeps the low modes of A), then made orthonormal in order on every (aggregate,
+ *     chirality) (Gram-Schmidt: the Q of a QR factorisation with positive diagonal);
  *   - the coarse operator is D_c = P^H A P, a nearest-neighbour stencil of nc x nc blocks
  *     on the lattice of domains, built in FP32;
  *   - one application of the preconditioner to v: e_c ~ D_c^{-1} P^H v by coarse_cycles
@@ -262,6 +263,7 @@ typedef struct {
   int coarse_m;        /* GMRES steps per coarse cycle, 1..63 */
   int coarse_cycles;   /* coarse GMRES cycles per application (>= 1) */
   dd_sap_params smoother;   /* Schwarz form of the smoother and of the set-up; i_schwarz >= 0 */
+  int setup_mode;      /* 0: v <- M_sap v; 1: v <- v - M_sap A v */
 } dd_mg_params;
 
 /* Build P and D_c from n_tv test vectors tv (canonical FP64 fields one after another, host

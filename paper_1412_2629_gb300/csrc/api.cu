@@ -135,6 +135,7 @@ struct dd_ctx {
     LsqState* lsq = nullptr;
     double* nu = nullptr;
     int* state = nullptr;
+    int* ticket = nullptr;                // last-block ticket of the coarse Gram-Schmidt passes
     float4 *xf = nullptr, *rf = nullptr, *ef = nullptr;   // fine work fields
   } mg;
   bool mg_active = false;
@@ -940,7 +941,8 @@ static void mg_free(dd_ctx* c) {
   cudaStreamSynchronize(c->st);
   for (void* p : {(void*)M.P, (void*)M.Dc, (void*)M.cb, (void*)M.cx, (void*)M.ct, (void*)M.cV, (void*)M.partial,
                   (void*)M.partial2, (void*)M.hA, (void*)M.hB, (void*)M.nrm, (void*)M.R, (void*)M.gv, (void*)M.y,
-                  (void*)M.lsq, (void*)M.nu, (void*)M.state, (void*)M.xf, (void*)M.rf, (void*)M.ef})
+                  (void*)M.lsq, (void*)M.nu, (void*)M.state, (void*)M.ticket, (void*)M.xf, (void*)M.rf,
+                  (void*)M.ef})
     release(c, p);
   M = dd_ctx::Mg();
 }
@@ -970,6 +972,8 @@ static dd_status mg_alloc(dd_ctx* c, int ntv, int mc) {
   TRY(dalloc(c, &M.lsq, sizeof(LsqState)));
   TRY(dalloc(c, &M.nu, 16));
   TRY(dalloc(c, &M.state, 16));
+  TRY(dalloc(c, &M.ticket, 16));
+  TRY(cuda_check(c, cudaMemsetAsync(M.ticket, 0, 16, c->st), "ticket"));
   for (float4** q : {&M.xf, &M.rf, &M.ef}) TRY(dalloc(c, q, (size_t)n4 * 16));
   return DD_OK;
 }
@@ -985,6 +989,7 @@ static dd_status mg_coarse_solve(dd_ctx* c) {
   const long long n4c = (long long)g.ND * M.nc / 2;
   auto Vc = [&](int i) { return M.cV + (long long)i * n4c; };
   const int ldh = M.mc + 1;
+  double* nrm_part = (double*)M.partial2;   // per-block |v|^2 shares of a projection
   int nk = 0;
   for (int cyc = 0; cyc < M.cycles; ++cyc) {
     if (cyc == 0) {
@@ -993,23 +998,23 @@ static dd_status mg_coarse_solve(dd_ctx* c) {
       launch_mg_coarse_apply(g, M.Dc, M.nc, (const float2*)M.cx, (float2*)Vc(0), (const float2*)M.cb, nullptr, st);
       ++nk;
     }
-    nk += launch_gs_dot(Vc(0), 0, n4c, Vc(0), M.partial, nullptr, 0, st);
-    launch_gs_reduce(M.partial, 0, M.nrm, nullptr, 0, st);
+    launch_mg_cdot(Vc(0), 0, n4c, Vc(0), M.partial, M.nrm, M.ticket, nullptr, st);   // |r|^2
     launch_mg_beta(M.nrm, M.gv, M.mc + 2, M.nu, M.state, M.lsq, st);
     launch_mg_scale(Vc(0), n4c, M.nu, M.state, st);
     nk += 3;
+    // one step: w = D_c v_j; two classical Gram-Schmidt passes (coefficients, then the
+    // projection); the second projection also forms the Hessenberg column, its Givens
+    // update and 1 / h_{j+1,j}; then v_{j+1} is scaled
     for (int j = 0; j < M.mc; ++j) {
       launch_mg_coarse_apply(g, M.Dc, M.nc, (const float2*)Vc(j), (float2*)M.ct, nullptr, M.state, st);
-      nk += 1 + launch_gs_dot(Vc(0), j + 1, n4c, M.ct, M.partial, M.state, 0, st);
-      launch_gs_reduce(M.partial, j + 1, M.hA, M.state, 0, st);
-      launch_gs_project(M.ct, M.ct, Vc(0), j + 1, n4c, M.hA, M.partial2, M.state, 0, st);
-      nk += 2 + launch_gs_dot(Vc(0), j + 1, n4c, M.ct, M.partial, M.state, 0, st);
-      launch_gs_reduce(M.partial, j + 1, M.hB, M.state, 0, st);
-      launch_gs_project(Vc(j + 1), M.ct, Vc(0), j + 1, n4c, M.hB, M.partial2, M.state, 0, st);
-      launch_gs_reduce(M.partial2, 0, M.nrm, M.state, 0, st);
-      launch_mg_hcol(M.R, ldh, j, M.hA, M.hB, M.nrm, M.lsq, M.gv, M.nu, M.state, st);
+      launch_mg_cdot(Vc(0), j + 1, n4c, M.ct, M.partial, M.hA, M.ticket, M.state, st);
+      launch_mg_cproject(M.ct, M.ct, Vc(0), j + 1, n4c, M.hA, nrm_part, nullptr, M.ticket, M.state, 0, M.R, ldh, j,
+                         M.hA, M.hB, M.lsq, M.gv, M.nu, M.state, st);
+      launch_mg_cdot(Vc(0), j + 1, n4c, M.ct, M.partial, M.hB, M.ticket, M.state, st);
+      launch_mg_cproject(Vc(j + 1), M.ct, Vc(0), j + 1, n4c, M.hB, nrm_part, nullptr, M.ticket, M.state, 1, M.R,
+                         ldh, j, M.hA, M.hB, M.lsq, M.gv, M.nu, M.state, st);
       launch_mg_scale(Vc(j + 1), n4c, M.nu, M.state, st);
-      nk += 5;
+      nk += 6;
     }
     launch_mg_lsq(M.R, ldh, M.mc, M.gv, M.state, M.y, st);
     ++nk;
@@ -1017,7 +1022,7 @@ static dd_status mg_coarse_solve(dd_ctx* c) {
       nk += launch_recombine(M.cx, Vc(0), M.mc, 1, n4c, (const double2*)M.y, M.mc, st);
     } else {
       nk += launch_recombine(M.ct, Vc(0), M.mc, 1, n4c, (const double2*)M.y, M.mc, st);
-      launch_mg_axpy(M.cx, M.ct, n4c, st);
+      launch_mg_axpy(M.cx, M.ct, n4c, 1.f, st);
       ++nk;
     }
   }
@@ -2452,7 +2457,7 @@ extern "C" dd_status dd_mg_setup(dd_ctx* c, const double* tv, int where, const d
   if (!c || !tv || !p) return DD_ERR_INVALID;
   if (!c->have_clover) return fail(c, DD_ERR_NO_CLOVER, "clover not built");
   if (p->n_tv < 1 || p->n_tv > MG_MAXTV || p->setup_iters < 0 || p->coarse_m < 1 || p->coarse_m > DD_MAXM - 1 ||
-      p->coarse_cycles < 1 || p->smoother.i_schwarz < 0)
+      p->coarse_cycles < 1 || p->smoother.i_schwarz < 0 || p->setup_mode < 0 || p->setup_mode > 1)
     return fail(c, DD_ERR_INVALID, "bad multigrid parameters");
   // the smoother's Schwarz form (at least one cycle when the set-up smooths test vectors)
   dd_sap_params sm = p->smoother;
@@ -2486,15 +2491,26 @@ extern "C" dd_status dd_mg_setup(dd_ctx* c, const double* tv, int where, const d
       rc = launched(c);
     }
   }
-  // test vectors <- M_sap test vectors, setup_iters times
+  // test vectors <- M_sap v (inverse iteration) or v - M_sap A v (the smoother on A v = 0),
+  // setup_iters times
   dd_sap_params ss = sm;
   if (ss.i_schwarz < 1) ss.i_schwarz = 1;
   for (int it = 0; it < p->setup_iters && rc == DD_OK; ++it)
     for (int k = 0; k < p->n_tv && rc == DD_OK; ++k) {
-      rc = sap_run(c, M.P + k * n4, M.ef, &ss);
-      if (rc == DD_OK)
-        rc = cuda_check(c, cudaMemcpyAsync(M.P + k * n4, M.ef, (size_t)n4 * 16, cudaMemcpyDeviceToDevice, c->st),
-                        "smoothed test vector");
+      float4* v = M.P + k * n4;
+      if (p->setup_mode == 0) {
+        rc = sap_run(c, v, M.ef, &ss);
+        if (rc == DD_OK)
+          rc = cuda_check(c, cudaMemcpyAsync(v, M.ef, (size_t)n4 * 16, cudaMemcpyDeviceToDevice, c->st),
+                          "smoothed test vector");
+      } else {
+        rc = apply_internal(c, v, M.xf, P32);
+        if (rc == DD_OK) rc = sap_run(c, M.xf, M.ef, &ss);
+        if (rc == DD_OK) {
+          launch_mg_axpy(v, M.ef, n4, -1.f, c->st);
+          rc = launched(c);
+        }
+      }
     }
   if (rc == DD_OK && p->setup_iters > 0) rc = sap_error_flag(c);
   int bad = 0;

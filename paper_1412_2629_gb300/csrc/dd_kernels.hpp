@@ -150,13 +150,23 @@ void launch_mg_coarse_build(const Geom& g, const float2* U32, const float4* C32,
 // y = D_c x, or y = b - D_c x when b != nullptr; skipped when gate && *gate != 0
 void launch_mg_coarse_apply(const Geom& g, const float2* Dc, int nc, const float2* x, float2* y, const float2* b,
                             const int* gate, cudaStream_t st);
-// coarse GMRES: one-thread small steps (state[0] != 0 stops a cycle, state[1] = columns done)
+// coarse-vector Gram-Schmidt passes, one launch each (the last block reduces the partial
+// sums in FP64): h_out[0..nv-1] = V^H w, h_out[nv] = |w|^2; the projection out = w - V h
+// leaves |out|^2 in *n2_out (if not null) and, with hcol != 0, runs the Hessenberg column
+// j's update (Givens, nu = 1 / h_{j+1,j}, state).  ticket: a device int, zero between
+// launches.  partial: 2 blas_partials_blocks() (nv + 1) double2; norm_partial: as many doubles.
+void launch_mg_cdot(const float4* V, int nv, long long n4, const float4* w, double2* partial, double2* h_out,
+                    int* ticket, const int* gate, cudaStream_t st);
+void launch_mg_cproject(float4* out, const float4* w, const float4* V, int nv, long long n4, const double2* h,
+                        double* norm_partial, double* n2_out, int* ticket, const int* gate, int hcol, zd* R, int ldh,
+                        int j, const double2* hA, const double2* hB, LsqState* lsq, zd* g, double* nu, int* state,
+                        cudaStream_t st);
+// coarse GMRES one-thread steps: start of a cycle (state[0] != 0 stops a cycle, state[1] =
+// columns done) and the final least squares
 void launch_mg_beta(const double2* nrm, zd* g, int ng, double* nu, int* state, LsqState* lsq, cudaStream_t st);
-void launch_mg_hcol(zd* R, int ldh, int j, const double2* hA, const double2* hB, const double2* nrm, LsqState* lsq,
-                    zd* g, double* nu, int* state, cudaStream_t st);
 void launch_mg_lsq(const zd* R, int ldh, int mc, const zd* g, const int* state, zd* y, cudaStream_t st);
 void launch_mg_scale(float4* v, long long n4, const double* nu, const int* gate, cudaStream_t st);
-void launch_mg_axpy(float4* x, const float4* t, long long n4, cudaStream_t st);
+void launch_mg_axpy(float4* x, const float4* t, long long n4, float a, cudaStream_t st);   // x += a t
 // z = vscale (x + e); e and vscale optional
 void launch_mg_combine(float4* z, const float4* x, const float4* e, long long n4, const float* vscale,
                        cudaStream_t st);

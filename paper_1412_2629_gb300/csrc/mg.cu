@@ -321,34 +321,210 @@ void launch_mg_coarse_build(const Geom& g, const float2* U32, const float4* C32,
 
 // ------------------------------------------------------------------ coarse operator
 // y = D_c x (b == nullptr) or y = b - D_c x; one thread per coarse row (domain, i).
-// Skipped when *gate != 0.
-__global__ void __launch_bounds__(256) mg_coarse_apply_kernel(Geom g, const float2* __restrict__ Dc, int nc,
+// Skipped when *gate != 0.  NC > 0: the row length is a compile-time constant, so each
+// block's loads are all in flight at once; NC = 0 reads nc at run time.
+template <int NC>
+__global__ void __launch_bounds__(256) mg_coarse_apply_kernel(Geom g, const float2* __restrict__ Dc, int nc_rt,
                                                               const float2* __restrict__ x, float2* y,
                                                               const float2* b, const int* gate) {
   if (gate && *gate) return;
+  const int nc = NC > 0 ? NC : nc_rt;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)g.ND * nc) return;
   const int d = (int)(t / nc), i = (int)(t % nc);
   int n[4];
   domain_coords(g, d, n);
-  float ar = 0.f, ai = 0.f;
+  float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
   for (int dir = 0; dir < 9; ++dir) {
     const int dn = dir == 0 ? d : neighbour_domain(g, d, n, (dir - 1) >> 1, ((dir - 1) & 1) ? -1 : +1);
     const float2* D = Dc + ((long long)d * 9 + dir) * nc * nc + i;
     const float2* xv = x + (long long)dn * nc;
-    for (int j = 0; j < nc; ++j) {
-      const float2 a = D[(long long)j * nc], v = xv[j];
-      ar += a.x * v.x - a.y * v.y;
-      ai += a.x * v.y + a.y * v.x;
+    if constexpr (NC > 0) {
+#pragma unroll
+      for (int j = 0; j < NC; j += 2) {
+        const float2 a0 = D[(long long)j * NC], v0 = xv[j];
+        const float2 a1 = D[(long long)(j + 1) * NC], v1 = xv[j + 1];
+        ar += a0.x * v0.x - a0.y * v0.y;
+        ai += a0.x * v0.y + a0.y * v0.x;
+        br += a1.x * v1.x - a1.y * v1.y;
+        bi += a1.x * v1.y + a1.y * v1.x;
+      }
+    } else {
+      for (int j = 0; j < nc; ++j) {
+        const float2 a = D[(long long)j * nc], v = xv[j];
+        ar += a.x * v.x - a.y * v.y;
+        ai += a.x * v.y + a.y * v.x;
+      }
     }
   }
+  ar += br;
+  ai += bi;
   y[t] = b ? make_float2(b[t].x - ar, b[t].y - ai) : make_float2(ar, ai);
 }
 
 void launch_mg_coarse_apply(const Geom& g, const float2* Dc, int nc, const float2* x, float2* y, const float2* b,
                             const int* gate, cudaStream_t st) {
   const long long n = (long long)g.ND * nc;
-  mg_coarse_apply_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, Dc, nc, x, y, b, gate);
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  switch (nc) {
+    case 8: mg_coarse_apply_kernel<8><<<nb, 256, 0, st>>>(g, Dc, nc, x, y, b, gate); break;
+    case 16: mg_coarse_apply_kernel<16><<<nb, 256, 0, st>>>(g, Dc, nc, x, y, b, gate); break;
+    case 24: mg_coarse_apply_kernel<24><<<nb, 256, 0, st>>>(g, Dc, nc, x, y, b, gate); break;
+    case 32: mg_coarse_apply_kernel<32><<<nb, 256, 0, st>>>(g, Dc, nc, x, y, b, gate); break;
+    default: mg_coarse_apply_kernel<0><<<nb, 256, 0, st>>>(g, Dc, nc, x, y, b, gate); break;
+  }
+}
+
+// ------------------------------------------------------------------ coarse-vector BLAS
+// Coarse vectors are short (ND nc complex numbers), so a Gram-Schmidt pass costs mostly
+// launches and reductions.  Each pass is one launch: every block stores its partial sums,
+// and the last block to finish (a device-scope ticket taken after a fence; nobody waits)
+// reduces them in block order in FP64 and runs the pass's scalar step.  The ticket is
+// reset by that last block, so consecutive launches on one stream reuse it.
+constexpr int CT = 256;
+
+// The Hessenberg column j from the two passes' coefficients and |v_{j+1}|^2, its Givens
+// update, and nu = 1 / h_{j+1,j}; a column whose subdiagonal entry vanishes against |w|
+// (invariant subspace) is the last one: state[0] = 1 stops the remaining steps.
+__device__ inline void hcol_step(zd* R, int ldh, int j, const double2* hA, const double2* hB, double n2,
+                                 LsqState* lsq, zd* g, double* nu, int* state) {
+  zd* col = R + (long)j * ldh;
+  for (int i = 0; i <= j; ++i) col[i] = Z(hA[i].x + hB[i].x, hA[i].y + hB[i].y);
+  const double h = sqrt(fmax(n2, 0.0));
+  col[j + 1] = Z(h);
+  lsq_add_column(*lsq, R, ldh, j, j + 2, g);
+  state[1] = j + 1;
+  const double w2 = hA[j + 1].x;   // |w|^2 before the projection
+  if (!(h * h > 1e-24 * w2) || !isfinite(h)) state[0] = 1;
+  nu[0] = state[0] == 0 ? 1.0 / h : 0.0;
+}
+
+// h_out[i] = conj(V_i) . w for i < nv and h_out[nv] = |w|^2 (FP64 over blocks).  partial:
+// gridDim.x (nv + 1) double2.  Skipped when *gate != 0.
+__global__ void __launch_bounds__(CT) mg_cdot_kernel(const float4* __restrict__ V, int nv, long long n4,
+                                                     const float4* __restrict__ w, double2* partial,
+                                                     double2* h_out, int* ticket, const int* gate) {
+  if (gate && *gate) return;
+  const long long stride = (long long)gridDim.x * CT;
+  const int ld = nv + 1;
+  const int nch = nv > 0 ? (nv + 7) / 8 : 1;
+  for (int ch = 0; ch < nch; ++ch) {
+    const int v0 = ch * 8, nvc = min(8, nv - v0);
+    float re[9], im[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) re[i] = im[i] = 0.f;
+    for (long long q = blockIdx.x * (long long)CT + threadIdx.x; q < n4; q += stride) {
+      const float4 wq = w[q];
+      float4 vq[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i < nvc) vq[i] = V[(long long)(v0 + i) * n4 + q];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i < nvc) cdot_acc(re[i], im[i], vq[i], wq);
+      if (ch == 0) re[8] += wq.x * wq.x + wq.y * wq.y + wq.z * wq.z + wq.w * wq.w;
+    }
+    float sr, si;
+    block_sum_cplx<9>(re, im, 9, sr, si);
+    const int t = threadIdx.x;
+    if (t < nvc) partial[(long long)blockIdx.x * ld + v0 + t] = make_double2(sr, si);
+    if (ch == 0 && t == 8) partial[(long long)blockIdx.x * ld + nv] = make_double2(sr, 0.0);
+  }
+  __threadfence();   // this block's partial sums are visible before its ticket is taken
+  __syncthreads();
+  __shared__ int last;
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i <= nv; i += CT) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      const double2 p = __ldcg(partial + (long long)b * ld + i);   // other blocks' sums, not through L1
+      s.x += p.x;
+      s.y += p.y;
+    }
+    h_out[i] = s;
+  }
+  if (threadIdx.x == 0) *ticket = 0;
+}
+
+// out = w - V h (in place allowed: out may alias w); |out|^2 over blocks in FP64 into
+// n2_out; with hc != 0 the last block also runs hcol_step for column j.  norm_partial:
+// gridDim.x doubles.  Skipped when *gate != 0.
+struct HcolArgs {
+  int hc, j, ldh;
+  zd* R;
+  const double2 *hA, *hB;
+  LsqState* lsq;
+  zd* g;
+  double* nu;
+  int* state;
+};
+__global__ void __launch_bounds__(CT) mg_cproject_kernel(float4* out, const float4* w, const float4* __restrict__ V,
+                                                         int nv, long long n4, const double2* h, double* norm_partial,
+                                                         double* n2_out, int* ticket, const int* gate, HcolArgs hc) {
+  if (gate && *gate) return;
+  __shared__ float2 hs[64];
+  for (int i = threadIdx.x; i < nv; i += CT) hs[i] = make_float2((float)h[i].x, (float)h[i].y);
+  __syncthreads();
+  float nrm = 0.f;
+  for (long long q = blockIdx.x * (long long)CT + threadIdx.x; q < n4; q += (long long)gridDim.x * CT) {
+    float4 a = w[q];
+    int i = 0;
+    for (; i + 4 <= nv; i += 4) {
+      float4 v[4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) v[b] = V[(long long)(i + b) * n4 + q];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float2 c = hs[i + b];
+        a.x -= c.x * v[b].x - c.y * v[b].y;
+        a.y -= c.x * v[b].y + c.y * v[b].x;
+        a.z -= c.x * v[b].z - c.y * v[b].w;
+        a.w -= c.x * v[b].w + c.y * v[b].z;
+      }
+    }
+    for (; i < nv; ++i) {
+      const float4 v = V[(long long)i * n4 + q];
+      const float2 c = hs[i];
+      a.x -= c.x * v.x - c.y * v.y;
+      a.y -= c.x * v.y + c.y * v.x;
+      a.z -= c.x * v.z - c.y * v.w;
+      a.w -= c.x * v.w + c.y * v.z;
+    }
+    out[q] = a;
+    nrm += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+  }
+  const double2 s = block_sum_d2(make_double2(nrm, 0.0));
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = s.x;
+  __threadfence();
+  __syncthreads();
+  __shared__ int last;
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double n2 = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) n2 += __ldcg(norm_partial + b);
+  if (n2_out) *n2_out = n2;
+  if (hc.hc && hc.state[0] == 0) hcol_step(hc.R, hc.ldh, hc.j, hc.hA, hc.hB, n2, hc.lsq, hc.g, hc.nu, hc.state);
+  *ticket = 0;
+}
+
+static int coarse_blocks() { return blas_partials_blocks() / 2; }   // 2 per SM
+
+void launch_mg_cdot(const float4* V, int nv, long long n4, const float4* w, double2* partial, double2* h_out,
+                    int* ticket, const int* gate, cudaStream_t st) {
+  mg_cdot_kernel<<<coarse_blocks(), CT, 0, st>>>(V, nv, n4, w, partial, h_out, ticket, gate);
+}
+
+void launch_mg_cproject(float4* out, const float4* w, const float4* V, int nv, long long n4, const double2* h,
+                        double* norm_partial, double* n2_out, int* ticket, const int* gate, int hcol, zd* R, int ldh,
+                        int j, const double2* hA, const double2* hB, LsqState* lsq, zd* g, double* nu, int* state,
+                        cudaStream_t st) {
+  HcolArgs a{hcol, j, ldh, R, hA, hB, lsq, g, nu, state};
+  mg_cproject_kernel<<<coarse_blocks(), CT, 0, st>>>(out, w, V, nv, n4, h, norm_partial, n2_out, ticket, gate, a);
 }
 
 // ------------------------------------------------------------------ coarse GMRES small steps
@@ -362,24 +538,6 @@ __global__ void mg_beta_kernel(const double2* nrm, zd* g, int ng, double* nu, in
   state[0] = (b > 0.0 && isfinite(b)) ? 0 : 1;
   state[1] = 0;
   nu[0] = state[0] == 0 ? 1.0 / b : 0.0;
-}
-
-// Column j of the Hessenberg matrix from the two Gram-Schmidt passes and the exact norm
-// of the projected vector, its Givens update, and nu = 1 / h_{j+1,j} for the new basis
-// vector.  A column whose subdiagonal entry vanishes against |w| (invariant subspace)
-// is the last one: state[0] = 1 stops the remaining steps.
-__global__ void mg_hcol_kernel(zd* R, int ldh, int j, const double2* hA, const double2* hB, const double2* nrm,
-                               LsqState* lsq, zd* g, double* nu, int* state) {
-  if (state[0]) return;
-  zd* col = R + (long)j * ldh;
-  for (int i = 0; i <= j; ++i) col[i] = Z(hA[i].x + hB[i].x, hA[i].y + hB[i].y);
-  const double h = sqrt(fmax(nrm[0].x, 0.0));
-  col[j + 1] = Z(h);
-  lsq_add_column(*lsq, R, ldh, j, j + 2, g);
-  state[1] = j + 1;
-  const double w2 = hA[j + 1].x;   // |w|^2 before the projection
-  if (!(h * h > 1e-24 * w2) || !isfinite(h)) state[0] = 1;
-  nu[0] = state[0] == 0 ? 1.0 / h : 0.0;
 }
 
 // y = R^{-1} g over the completed columns; the rest of y is zero.
@@ -399,11 +557,11 @@ __global__ void mg_scale_kernel(float4* v, long long n4, const double* nu, const
   }
 }
 
-// x += t
-__global__ void mg_axpy_kernel(float4* x, const float4* t, long long n4) {
+// x += a t
+__global__ void mg_axpy_kernel(float4* x, const float4* t, long long n4, float a) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
-    const float4 a = x[q], b = t[q];
-    x[q] = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+    const float4 u = x[q], v = t[q];
+    x[q] = make_float4(u.x + a * v.x, u.y + a * v.y, u.z + a * v.z, u.w + a * v.w);
   }
 }
 
@@ -429,18 +587,14 @@ static unsigned grid_for(long long n4) {
 void launch_mg_beta(const double2* nrm, zd* g, int ng, double* nu, int* state, LsqState* lsq, cudaStream_t st) {
   mg_beta_kernel<<<1, 1, 0, st>>>(nrm, g, ng, nu, state, lsq);
 }
-void launch_mg_hcol(zd* R, int ldh, int j, const double2* hA, const double2* hB, const double2* nrm, LsqState* lsq,
-                    zd* g, double* nu, int* state, cudaStream_t st) {
-  mg_hcol_kernel<<<1, 1, 0, st>>>(R, ldh, j, hA, hB, nrm, lsq, g, nu, state);
-}
 void launch_mg_lsq(const zd* R, int ldh, int mc, const zd* g, const int* state, zd* y, cudaStream_t st) {
   mg_lsq_kernel<<<1, 1, 0, st>>>(R, ldh, mc, g, state, y);
 }
 void launch_mg_scale(float4* v, long long n4, const double* nu, const int* gate, cudaStream_t st) {
   mg_scale_kernel<<<grid_for(n4), 256, 0, st>>>(v, n4, nu, gate);
 }
-void launch_mg_axpy(float4* x, const float4* t, long long n4, cudaStream_t st) {
-  mg_axpy_kernel<<<grid_for(n4), 256, 0, st>>>(x, t, n4);
+void launch_mg_axpy(float4* x, const float4* t, long long n4, float a, cudaStream_t st) {
+  mg_axpy_kernel<<<grid_for(n4), 256, 0, st>>>(x, t, n4, a);
 }
 void launch_mg_combine(float4* z, const float4* x, const float4* e, long long n4, const float* vscale,
                        cudaStream_t st) {

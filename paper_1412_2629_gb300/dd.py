@@ -38,7 +38,7 @@ class dd_bicgstab_params(C.Structure):
 
 class dd_mg_params(C.Structure):
     _fields_ = [("n_tv", C.c_int), ("setup_iters", C.c_int), ("coarse_m", C.c_int), ("coarse_cycles", C.c_int),
-                ("smoother", dd_sap_params)]
+                ("smoother", dd_sap_params), ("setup_mode", C.c_int)]
 
 
 class dd_solve_info(C.Structure):
@@ -213,11 +213,11 @@ class Context:
         return info
 
     def dd_mg_setup(self, tv, n_tv, where=DD_HOST, setup_iters=4, coarse_m=16, coarse_cycles=1, i_schwarz=2,
-                    i_domain=4, storage_prec=DD_PREC_FP16, threads_per_site=0):
+                    i_domain=4, storage_prec=DD_PREC_FP16, threads_per_site=0, setup_mode=0):
         """Two-level multigrid set-up from n_tv canonical FP64 test vectors; returns the
         set-up's device time in seconds."""
         p = dd_mg_params(n_tv, setup_iters, coarse_m, coarse_cycles,
-                         dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site, 0))
+                         dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site, 0), setup_mode)
         sec = C.c_double()
         self._check(lib().dd_mg_setup(self._h, _ptr(tv), where, C.byref(p), C.byref(sec)))
         return sec.value

@@ -41,13 +41,14 @@ def _tv(dims, seed):
     return [synth.gaussian_source(dims, seed + 100 + k) for k in range(NTV)]
 
 
-def _setup(dims, dom, seed, setup_iters=0, i_schwarz=1, coarse_m=32, cycles=3):
+def _setup(dims, dom, seed, setup_iters=0, i_schwarz=1, coarse_m=32, cycles=3, mode=0):
     U = gauge(dims, 0.5, seed, ape=2)
     c = ctx_for(dims, dom, U, KAPPA, CSW)
     tv = _tv(dims, seed)
     t = torch.stack([dev(v) for v in tv]).contiguous()
     c.dd_mg_setup(t, NTV, dd.DD_DEVICE, setup_iters=setup_iters, coarse_m=coarse_m, coarse_cycles=cycles,
-                  i_schwarz=i_schwarz, i_domain=4, storage_prec=dd.DD_PREC_FP32, threads_per_site=2)
+                  i_schwarz=i_schwarz, i_domain=4, storage_prec=dd.DD_PREC_FP32, threads_per_site=2,
+                  setup_mode=mode)
     return U, c, tv
 
 
@@ -129,17 +130,19 @@ def test_precondition_matches_oracle(case):
     assert rel(host(out), ref) <= 2e-4
 
 
-def test_smoothed_setup_matches_oracle():
-    """Two Schwarz applications per test vector before the interpolation is built (FP32
-    storage): the GPU's coarse operator acts like the oracle's within 1e-3 (the smoothed
-    vectors agree to the Schwarz bar of 1e-5; the Gram-Schmidt of vectors that the
-    smoothing has turned towards the same low modes amplifies that difference)."""
+@pytest.mark.parametrize("mode", [0, 1], ids=["inverse", "nullspace"])
+def test_smoothed_setup_matches_oracle(mode):
+    """Two smoothing steps per test vector before the interpolation is built (FP32 storage;
+    mode 0: v <- M_sap v, mode 1: v <- v - M_sap A v): the GPU's interpolation and coarse
+    operator act like the oracle's within 1e-3 (the smoothed vectors agree to the Schwarz
+    bar of 1e-5; the Gram-Schmidt of vectors that the smoothing has turned towards the same
+    low modes amplifies that difference)."""
     dims, dom, seed = CASES[0]
-    U, c, tv = _setup(dims, dom, seed, setup_iters=2)
+    U, c, tv = _setup(dims, dom, seed, setup_iters=2, mode=mode)
     agg = MG.Aggregates(dims, dom)
     doms = DD.Domains(dims, dom)
     F = W.field_strength(U)
-    P, Dc = MG.setup(U, KAPPA, CSW, tv, agg, 2, doms, 1, 4, F)
+    P, Dc = MG.setup(U, KAPPA, CSW, tv, agg, 2, doms, 1, 4, F, mode=("inverse", "nullspace")[mode])
     r = synth.gaussian_source(dims, seed + 70)
     rc = torch.empty(agg.n * 2 * NTV, 2, dtype=torch.float32, device="cuda")
     c.dd_mg_restrict(_internal(c, r), rc)
@@ -184,7 +187,8 @@ def test_mg_setup_rejects_bad_parameters():
     U = gauge(dims, 0.5, 25)
     c = ctx_for(dims, dom, U, KAPPA, CSW)
     tv = torch.zeros(17, *dims[::-1], 4, 3, 2, dtype=torch.float64, device="cuda")
-    for kw in (dict(n_tv=0), dict(n_tv=17), dict(n_tv=2, coarse_m=0), dict(n_tv=2, coarse_cycles=0)):
+    for kw in (dict(n_tv=0), dict(n_tv=17), dict(n_tv=2, coarse_m=0), dict(n_tv=2, coarse_cycles=0),
+               dict(n_tv=2, setup_mode=2)):
         n = kw.pop("n_tv")
         with pytest.raises(dd.DDError) as e:
             c.dd_mg_setup(tv, n, dd.DD_DEVICE, **kw)
