@@ -87,6 +87,10 @@ typedef struct {
   int k;              /* deflation vectors kept at a restart, 0 <= k < m */
   int max_iter;       /* total Arnoldi steps allowed */
   dd_sap_params sap;
+  int basis_fp16;     /* dd_solve with one right-hand side at a time: 1 stores the basis V in FP16
+                         (one power-of-two scale for the whole basis; Gram-Schmidt, recombination and
+                         the preconditioner's input read it in FP32 arithmetic), halving its bytes;
+                         0 (default) FP32.  Not part of the paper.  Other solvers ignore it */
 } dd_solve_params;
 
 /* Result of dd_solve (for nrhs > 1: summed counts and times, worst residual). */

@@ -75,6 +75,14 @@ struct SolverBuffers {
   // new vector unnormalised (its exact norm comes out of the projection pass) and its
   // readers apply the scale, which saves a read and a write of the vector per step
   float* vscale = nullptr;
+  // FP16 basis (dd_solve_params.basis_fp16): V16 replaces V, holding s v_i in FP16 with one
+  // power-of-two scale s for the whole basis (vscale[i] = 1 / s); vin is the FP32 copy of
+  // the newest basis vector, the next preconditioner application's input
+  bool v16 = false;
+  float v16_scale = 1.f;
+  uint2* V16 = nullptr;
+  float4* vin = nullptr;
+  double* one = nullptr;          // device 1.0
   // deflated restart on the device: workspace and flags ([0] deflation status, [1] the
   // recombination gate: deflation succeeded and the residual is above target)
   void* dW = nullptr;            // deflate_bytes(m) of global scratch (when shared memory is too small)
@@ -598,6 +606,10 @@ extern "C" dd_status dd_apply_D_batch(dd_ctx* c, const void* in, void* out, int 
 }
 
 // ------------------------------------------------------------------ small dense kernels
+__global__ void fill_value_kernel(float* v, int n, float x) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = x;
+}
+
 __global__ void fill_ones_kernel(float* v, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 1.f;
 }
@@ -733,7 +745,8 @@ static void free_solver_buffers(dd_ctx* c, SolverBuffers& s) {
                   (void*)s.f64, (void*)s.r64, (void*)s.canon64, (void*)s.H, (void*)s.R, (void*)s.P, (void*)s.Hn,
                   (void*)s.g, (void*)s.c0, (void*)s.y, (void*)s.hA, (void*)s.hB, (void*)s.cn, (void*)s.theta,
                   (void*)s.cp, (void*)s.partial, (void*)s.partial2, (void*)s.nrm2, (void*)s.status, (void*)s.lsq,
-                  (void*)s.flag, (void*)s.nu2, (void*)s.dW, (void*)s.dflags, (void*)s.vscale})
+                  (void*)s.flag, (void*)s.nu2, (void*)s.dW, (void*)s.dflags, (void*)s.vscale, (void*)s.V16,
+                  (void*)s.vin, (void*)s.one})
     release(c, p);
   if (s.h_status) cudaFreeHost(s.h_status);
   for (auto& kv : s.graphs)
@@ -758,11 +771,23 @@ static void release_solver(dd_ctx* c) {
 
 // Krylov basis, FP64 fields and small dense buffers for basis size m; streams and events
 // only for the context's own solver (the lockstep right-hand sides run on its stream).
-static dd_status alloc_solver_buffers(dd_ctx* c, SolverBuffers& s, int m, bool streams) {
+static dd_status alloc_solver_buffers(dd_ctx* c, SolverBuffers& s, int m, bool streams, bool v16 = false) {
   const Geom& g = c->g;
   long long n4 = g.V * 6;
   size_t vb = (size_t)n4 * 16;
-  TRY(dalloc(c, &s.V, vb * (m + 1)));
+  if (v16) {
+    TRY(dalloc(c, &s.V16, (size_t)n4 * 8 * (m + 1)));
+    TRY(dalloc(c, &s.vin, vb));
+    TRY(dalloc(c, &s.one, 16));
+    const double one = 1.0;
+    TRY(cuda_check(c, cudaMemcpy(s.one, &one, sizeof(double), cudaMemcpyHostToDevice), "constant"));
+    // components of a unit vector have rms 1 / sqrt(24 V); s puts them near 2^-4, far from
+    // both ends of the FP16 range
+    s.v16_scale = ldexpf(1.f, (int)lrint(0.5 * log2(24.0 * (double)g.V)) - 4);
+  } else {
+    TRY(dalloc(c, &s.V, vb * (m + 1)));
+  }
+  s.v16 = v16;
   TRY(dalloc(c, &s.Z, vb * m));
   TRY(dalloc(c, &s.w, vb));
   TRY(dalloc(c, &s.x64, field_bytes(g, P64)));
@@ -785,7 +810,7 @@ static dd_status alloc_solver_buffers(dd_ctx* c, SolverBuffers& s, int m, bool s
   TRY(dalloc(c, &s.nu2, 16));
   TRY(dalloc(c, &s.dW, deflate_bytes(m)));
   TRY(dalloc(c, &s.vscale, (m + 2) * sizeof(float)));
-  fill_ones_kernel<<<1, 64, 0, c->st>>>(s.vscale, m + 2);
+  fill_value_kernel<<<1, 64, 0, c->st>>>(s.vscale, m + 2, v16 ? 1.f / s.v16_scale : 1.f);
   TRY(launched(c));
   TRY(dalloc(c, &s.dflags, 16 * sizeof(int)));
   if (cudaMallocHost(&s.h_status, 8 * sizeof(double)) != cudaSuccess) return fail(c, DD_ERR_OOM, "pinned status");
@@ -799,10 +824,13 @@ static dd_status alloc_solver_buffers(dd_ctx* c, SolverBuffers& s, int m, bool s
   return DD_OK;
 }
 
-static dd_status ensure_solver(dd_ctx* c, int m) {
-  if (c->sv.m >= m) return DD_OK;
-  if (c->sv.m) release_solver(c);
-  return alloc_solver_buffers(c, c->sv, m, true);
+static dd_status ensure_solver(dd_ctx* c, int m, bool v16 = false) {
+  if (c->sv.m >= m && c->sv.v16 == v16) return DD_OK;
+  if (c->sv.m) {
+    drop_graphs(c);   // captured steps hold the old buffers
+    release_solver(c);
+  }
+  return alloc_solver_buffers(c, c->sv, m, true, v16);
 }
 
 // Run a launch sequence of the outer solver: directly on its first use, captured into a
@@ -912,10 +940,17 @@ static dd_status end_cycle(dd_ctx* c, SolverBuffers& s, int mm, const dd_solve_p
     // V <- V P_{k+1}, Z <- Z P_k in place: every output element depends only on the inputs
     // at the same position, which its thread reads before writing
     const int* gate = s.dflags + 1;
-    nk += launch_recombine(s.V, s.V, mm + 1, k + 1, n4, (const double2*)s.P, ldh, c->st, gate, s.vscale);
+    if (s.v16)
+      nk += launch_recombine(s.V16, s.V16, mm + 1, k + 1, n4, (const double2*)s.P, ldh, c->st, gate, s.vscale,
+                             s.v16_scale);
+    else
+      nk += launch_recombine(s.V, s.V, mm + 1, k + 1, n4, (const double2*)s.P, ldh, c->st, gate, s.vscale);
     nk += launch_recombine(s.Z, s.Z, mm, k, n4, (const double2*)s.P, ldh, c->st, gate);
     launch_r64_to_v32(s.w, s.r64, n4, s.nrm2, c->st, gate);
-    nk += 1 + launch_gs_dot(s.V, k + 1, n4, s.w, s.partial, gate, 1, c->st);
+    if (s.v16)
+      nk += 1 + launch_gs_dot(s.V16, k + 1, n4, s.w, s.partial, gate, 1, c->st, s.vscale);
+    else
+      nk += 1 + launch_gs_dot(s.V, k + 1, n4, s.w, s.partial, gate, 1, c->st);
     launch_gs_reduce(s.partial, k + 1, (double2*)s.cp, gate, 1, c->st);
     nk++;
   }
@@ -1069,17 +1104,30 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
   double rho2 = 0;
   auto Vv = [&](int i) { return s.V + (long long)i * n4; };
   auto Zv = [&](int i) { return s.Z + (long long)i * n4; };
+  // FP16 basis: V16 holds s v_i (vscale[i] = 1 / s), vin the FP32 copy of the newest v
+  const bool h16 = s.v16;
+  const float vs16 = s.v16_scale;
+  auto V16 = [&](int i) { return s.V16 + (long long)i * n4; };
+  // v_1 = r / |r| (FP16 basis: into vin and, scaled, into V16)
+  auto first_vector = [&]() -> dd_status {
+    if (!h16) {
+      launch_r64_to_v32(Vv(0), s.r64, n4, s.nrm2, c->st);
+      plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq, s.vscale);
+      return launched(c, 2);
+    }
+    launch_r64_to_v32(s.vin, s.r64, n4, s.nrm2, c->st);
+    launch_basis16_store(V16(0), nullptr, s.vin, n4, s.one, vs16, c->st);
+    plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq, s.vscale);
+    fill_value_kernel<<<1, 64, 0, c->st>>>(s.vscale, m + 2, 1.f / vs16);
+    return launched(c, 4);
+  };
 
   TRY(true_residual(c, &rho2));
   reliable++;
   double rel = sqrt(rho2) / nf;
   if (!isfinite(rel)) rc = fail(c, DD_ERR_NONFINITE, "non-finite residual");
   int j0 = 0;
-  if (rc == DD_OK && rel > tol) {
-    launch_r64_to_v32(Vv(0), s.r64, n4, s.nrm2, c->st);
-    plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq, s.vscale);
-    TRY(launched(c, 2));
-  }
+  if (rc == DD_OK && rel > tol) TRY(first_vector());
   while (rc == DD_OK && rel > tol) {
     if (iters >= p->max_iter) { rc = fail(c, DD_ERR_NOT_CONVERGED, "iteration limit reached"); break; }
     int mm = m;
@@ -1090,19 +1138,48 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
       const GraphKey kbase = {0, j, p->sap.i_schwarz, p->sap.i_domain, p->sap.storage_prec,
                               p->sap.threads_per_site, m, p->sap.additive};
       GraphKey k0 = kbase, k1 = kbase, k2 = kbase;
-      k1[0] = 1;
-      k2[0] = 2;
+      const int part0 = h16 ? 20 : 0;   // the FP16-basis steps are other launch sequences
+      k0[0] = part0;
+      k1[0] = part0 + 1;
+      k2[0] = part0 + 2;
+      // the preconditioner's input: the stored v_j with its scale, or the FP32 copy
+      const float4* vj = h16 ? s.vin : Vv(j);
+      const float* vjs = h16 ? nullptr : s.vscale + j;
       cudaEventRecord(e0, c->st);
       if (c->mg_active) {
-        k0[0] = 7;
-        TRY(graphed(c, k0, [&]() { return mg_run(c, Vv(j), Zv(j), s.vscale + j); }));
+        k0[0] = part0 + 7;
+        TRY(graphed(c, k0, [&]() { return mg_run(c, vj, Zv(j), vjs); }));
       } else {
-        TRY(graphed(c, k0, [&]() { return sap_run(c, Vv(j), Zv(j), &p->sap, 1, s.vscale + j); }));
+        TRY(graphed(c, k0, [&]() { return sap_run(c, vj, Zv(j), &p->sap, 1, vjs); }));
       }
       cudaEventRecord(e1, c->st);
       TRY(graphed(c, k1, [&]() { return apply_internal(c, Zv(j), s.w, P32); }));
       cudaEventRecord(e2, c->st);
       TRY(graphed(c, k2, [&]() {
+        if (h16) {
+          // the same Gram-Schmidt over the FP16 basis, projecting w in place; the new basis
+          // vector is normalised on its way into V16 (and into vin for the next step)
+          double2* nrm_a = s.nrm2 + 1;
+          double2* nrm_b = s.nrm2 + 2;
+          const float* sc = s.vscale;
+          int nk = launch_gs_dot(V16(0), j + 1, n4, s.w, s.partial, nullptr, 0, c->st, sc);
+          launch_gs_reduce(s.partial, j + 1, (double2*)s.hA, nullptr, 0, c->st);
+          launch_gs_project(s.w, s.w, V16(0), j + 1, n4, (const double2*)s.hA, s.partial2, nullptr, 0, c->st, sc);
+          launch_gs_reduce(s.partial2, 0, nrm_a, nullptr, 0, c->st);
+          gs_decide_kernel<<<1, 1, 0, c->st>>>(s.hA, j + 1, nrm_a, s.hB, s.flag, s.nu2);
+          nk += launch_gs_dot(V16(0), j + 1, n4, s.w, s.partial, s.flag, 1, c->st, sc);
+          launch_gs_reduce(s.partial, j + 1, (double2*)s.hB, s.flag, 1, c->st);
+          launch_gs_project(s.w, s.w, V16(0), j + 1, n4, (const double2*)s.hB, s.partial2, s.flag, 1, c->st, sc);
+          launch_gs_reduce(s.partial2, 0, nrm_b, s.flag, 1, c->st);
+          gs_decide2_kernel<<<1, 1, 0, c->st>>>(s.flag, nrm_b, s.nu2);
+          cudaEventRecord(s.ev_fork, c->st);
+          cudaStreamWaitEvent(s.side, s.ev_fork, 0);
+          arnoldi_finish_kernel<<<1, 1, 0, s.side>>>(s.H, s.R, ldh, j, s.hA, s.hB, s.nu2, s.lsq, s.g, s.status);
+          cudaEventRecord(s.ev_join, s.side);
+          launch_basis16_store(V16(j + 1), s.vin, s.w, n4, s.nu2, vs16, c->st);
+          cudaStreamWaitEvent(c->st, s.ev_join, 0);
+          return launched(c, nk + 10);
+        }
         // Gram-Schmidt: classical projection with the exact norm of the result, repeated
         // once when it cancels more than half of |w| (Daniel-Gragg-Kaufman-Stewart test)
         float4* vn = Vv(j + 1);
@@ -1147,7 +1224,7 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
       if (est <= 0.5 * tol * nf || est <= 2e-6 * rho_cycle || iters >= p->max_iter) { mm = j + 1; break; }
     }
     if (rc != DD_OK) break;
-    if (c->trace && getenv("DD_TRACE")[0] == '2') {
+    if (c->trace && getenv("DD_TRACE")[0] == '2' && !h16) {
       // orthogonality of the finished basis: max |V^H V - I|
       double dev = 0;
       std::vector<zd> row(mm + 1);
@@ -1177,12 +1254,16 @@ static dd_status solve_one(dd_ctx* c, const dd_solve_params* p, double nf2, dd_s
     if (ce.deflate) {
       restart_lsq_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, k, s.Hn, s.cp, s.g, s.c0, s.lsq, s.status, s.vscale);
       TRY(launched(c));
+      if (h16) {
+        // the recombined basis is stored s v_i; the step at j = k reads v_k in FP32
+        fill_value_kernel<<<1, 64, 0, c->st>>>(s.vscale, m + 2, 1.f / vs16);
+        launch_basis16_load(s.vin, V16(k), n4, 1.f / vs16, c->st);
+        TRY(launched(c, 2));
+      }
       j0 = k;
       deflated++;
     } else {
-      launch_r64_to_v32(Vv(0), s.r64, n4, s.nrm2, c->st);
-      plain_restart_kernel<<<1, 1, 0, c->st>>>(s.H, s.R, ldh, m, s.nrm2, s.g, s.c0, s.lsq, s.vscale);
-      TRY(launched(c, 2));
+      TRY(first_vector());
       j0 = 0;
     }
   }
@@ -1695,7 +1776,11 @@ extern "C" dd_status dd_solve(dd_ctx* c, const double* f, double* x, int nrhs, i
     return fail(c, DD_ERR_INVALID, "bad solver parameters");
   TRY(check_sap_params(c, &p->sap));
   if (p->sap.i_domain < 1) return fail(c, DD_ERR_INVALID, "i_domain must be >= 1");
-  TRY(ensure_solver(c, p->m));
+  if (p->basis_fp16 < 0 || p->basis_fp16 > 1) return fail(c, DD_ERR_INVALID, "basis_fp16 must be 0 or 1");
+  const char* seq0 = getenv("DD_SEQUENTIAL_RHS");
+  if (p->basis_fp16 && nrhs > 1 && p->sap.threads_per_site != 1 && !(seq0 && seq0[0] == '1'))
+    return fail(c, DD_ERR_INVALID, "the FP16 basis is not available for right-hand sides in lockstep");
+  TRY(ensure_solver(c, p->m, p->basis_fp16 != 0));
   if (info) memset(info, 0, sizeof(*info));
   SolverBuffers& s = c->sv;
   // Run on the solver's own stream (capturable into CUDA graphs even when the caller
@@ -2253,6 +2338,7 @@ extern "C" dd_status dd_autotune(dd_ctx* c, int storage_prec, int domain_out[4],
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   dd_solve_params sp;
+  memset(&sp, 0, sizeof(sp));
   sp.tol = 1e-7;
   sp.m = 16;
   sp.k = 4;

@@ -27,6 +27,22 @@ __device__ inline cx<float> dot4(float4 v, float4 w) {  // conj(v) . w over two 
   return mk(v.x * w.x + v.y * w.y + v.z * w.z + v.w * w.w, v.x * w.y - v.y * w.x + v.z * w.w - v.w * w.z);
 }
 
+// Basis vectors in FP32 (float4: two complex numbers) or FP16 (uint2: the same two complex
+// numbers as two half2); every kernel that reads or writes a basis does its arithmetic in
+// FP32 on float4 values.
+__device__ inline float4 ldv(const float4* p, long long q) { return p[q]; }
+__device__ inline float4 ldv(const uint2* p, long long q) {
+  const uint2 u = p[q];
+  const float2 a = h2f(u.x), b = h2f(u.y);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ inline void stv(float4* p, long long q, float4 v, float s) {
+  p[q] = make_float4(v.x * s, v.y * s, v.z * s, v.w * s);
+}
+__device__ inline void stv(uint2* p, long long q, float4 v, float s) {
+  p[q] = make_uint2(f2h(v.x * s, v.y * s), f2h(v.z * s, v.w * s));
+}
+
 // Block reduction of NV complex doubles; thread 0 of the block ends with the sums in s[].
 template <int NV>
 __device__ inline void block_reduce(double2 (&v)[NV], double2* s_out) {
@@ -167,10 +183,10 @@ void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2*
 // V itself (in-place recombination): a thread reads all inputs at q before it writes
 // the outputs at q, and no other thread touches q.
 constexpr int RBT = 128, RU = 8;
-template <int NO>
-__global__ void __launch_bounds__(RBT) recombine_kernel(float4* out, const float4* V, int nv, int l0,
-                                                        long long n4, const double2* P, int ldp, const int* gate,
-                                                        const float* vscale) {
+template <int NO, typename VT>
+__global__ void __launch_bounds__(RBT) recombine_kernel(VT* out, const VT* V, int nv, int l0, long long n4,
+                                                        const double2* P, int ldp, const int* gate,
+                                                        const float* vscale, float oscale) {
   if (gate && *gate != 1) return;
   __shared__ float2 ps[64][NO];
   for (int t = threadIdx.x; t < nv * NO; t += RBT) {
@@ -198,30 +214,40 @@ __global__ void __launch_bounds__(RBT) recombine_kernel(float4* out, const float
     for (; i + RU <= nv; i += RU) {
       float4 v[RU];
 #pragma unroll
-      for (int u = 0; u < RU; ++u) v[u] = V[(long long)(i + u) * n4 + q];
+      for (int u = 0; u < RU; ++u) v[u] = ldv(V, (long long)(i + u) * n4 + q);
 #pragma unroll
       for (int u = 0; u < RU; ++u) fma_in(i + u, v[u]);
     }
-    for (; i < nv; ++i) fma_in(i, V[(long long)i * n4 + q]);
+    for (; i < nv; ++i) fma_in(i, ldv(V, (long long)i * n4 + q));
 #pragma unroll
-    for (int l = 0; l < NO; ++l) out[(long long)(l0 + l) * n4 + q] = a[l];
+    for (int l = 0; l < NO; ++l) stv(out, (long long)(l0 + l) * n4 + q, a[l], oscale);
   }
 }
 
-template <int NO>
-static void recombine_launch(int nl, float4* out, const float4* V, int nv, int l0, long long n4, const double2* P,
-                             int ldp, cudaStream_t st, const int* gate, const float* vscale) {
+template <int NO, typename VT>
+static void recombine_launch(int nl, VT* out, const VT* V, int nv, int l0, long long n4, const double2* P, int ldp,
+                             cudaStream_t st, const int* gate, const float* vscale, float oscale) {
   if constexpr (NO > 1) {
-    if (nl < NO) return recombine_launch<NO - 1>(nl, out, V, nv, l0, n4, P, ldp, st, gate, vscale);
+    if (nl < NO) return recombine_launch<NO - 1, VT>(nl, out, V, nv, l0, n4, P, ldp, st, gate, vscale, oscale);
   }
-  recombine_kernel<NO><<<2 * blas_partials_blocks(), RBT, 0, st>>>(out, V, nv, l0, n4, P, ldp, gate, vscale);
+  recombine_kernel<NO, VT><<<2 * blas_partials_blocks(), RBT, 0, st>>>(out, V, nv, l0, n4, P, ldp, gate, vscale,
+                                                                      oscale);
 }
 
 int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n4, const double2* P, int ldp,
                      cudaStream_t st, const int* gate, const float* vscale) {
   int n = 0;
   for (int l0 = 0; l0 < nout; l0 += 16, ++n)
-    recombine_launch<16>(nout - l0 < 16 ? nout - l0 : 16, out, V, nv, l0, n4, P, ldp, st, gate, vscale);
+    recombine_launch<16, float4>(nout - l0 < 16 ? nout - l0 : 16, out, V, nv, l0, n4, P, ldp, st, gate, vscale, 1.f);
+  return n;
+}
+
+int launch_recombine(uint2* out, const uint2* V, int nv, int nout, long long n4, const double2* P, int ldp,
+                     cudaStream_t st, const int* gate, const float* vscale, float oscale) {
+  int n = 0;
+  for (int l0 = 0; l0 < nout; l0 += 16, ++n)
+    recombine_launch<16, uint2>(nout - l0 < 16 ? nout - l0 : 16, out, V, nv, l0, n4, P, ldp, st, gate, vscale,
+                                oscale);
   return n;
 }
 
@@ -236,8 +262,8 @@ int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n
 // launch order and all but the first find them in L2.  Each loop trip handles U elements
 // per vector, (NV + 1) * U independent 16-byte loads per thread, which keeps enough bytes
 // in flight for HBM even for the short last chunk.
-template <int NV, int U>
-__global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const float4* __restrict__ V, int nv, int nch, long long n4,
+template <int NV, int U, typename VT>
+__global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const VT* __restrict__ V, int nv, int nch, long long n4,
                                                        const float4* __restrict__ w, double2* partial, int ldp,
                                                        const int* gate, int want, const float* vscale) {
   if (gate && *gate != want) return;
@@ -248,7 +274,7 @@ __global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const float4* __restrict_
 #pragma unroll
   for (int i = 0; i < NV; ++i) re[i] = im[i] = 0.f;
   const long long stride = (long long)nqb * BT;
-  const float4* Vc = V + (long long)v0 * n4;
+  const VT* Vc = V + (long long)v0 * n4;
   long long q = (long long)qb * BT + threadIdx.x;
   for (; q + (U - 1) * stride < n4; q += U * stride) {
     float4 wq[U], vq[NV][U];
@@ -258,7 +284,7 @@ __global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const float4* __restrict_
     for (int i = 0; i < NV; ++i)
       if (i < nvc)
 #pragma unroll
-        for (int u = 0; u < U; ++u) vq[i][u] = Vc[(long long)i * n4 + q + u * stride];
+        for (int u = 0; u < U; ++u) vq[i][u] = ldv(Vc, (long long)i * n4 + q + u * stride);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (self) ww += wq[u].x * wq[u].x + wq[u].y * wq[u].y + wq[u].z * wq[u].z + wq[u].w * wq[u].w;
@@ -277,7 +303,7 @@ __global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const float4* __restrict_
 #pragma unroll
     for (int i = 0; i < NV; ++i)
       if (i < nvc) {
-        cx<float> d = dot4(Vc[(long long)i * n4 + q], wq);
+        cx<float> d = dot4(ldv(Vc, (long long)i * n4 + q), wq);
         re[i] += d.re;
         im[i] += d.im;
       }
@@ -300,8 +326,16 @@ __global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const float4* __restrict_
 int launch_gs_dot(const float4* V, int nv, long long n4, const float4* w, double2* partial, const int* gate, int want,
                   cudaStream_t st, const float* vscale) {
   const int nch = nv > 0 ? (nv + 7) / 8 : 1;
-  gs_dot_kernel<8, 2><<<blas_partials_blocks() * nch, BT, 0, st>>>(V, nv, nch, n4, w, partial, nv + 1, gate, want,
-                                                                   vscale);
+  gs_dot_kernel<8, 2, float4><<<blas_partials_blocks() * nch, BT, 0, st>>>(V, nv, nch, n4, w, partial, nv + 1,
+                                                                           gate, want, vscale);
+  return 1;
+}
+
+int launch_gs_dot(const uint2* V, int nv, long long n4, const float4* w, double2* partial, const int* gate, int want,
+                  cudaStream_t st, const float* vscale) {
+  const int nch = nv > 0 ? (nv + 7) / 8 : 1;
+  gs_dot_kernel<8, 2, uint2><<<blas_partials_blocks() * nch, BT, 0, st>>>(V, nv, nch, n4, w, partial, nv + 1,
+                                                                          gate, want, vscale);
   return 1;
 }
 
@@ -332,7 +366,8 @@ void launch_gs_reduce(const double2* partial, int nv, double2* out, const int* g
 // reached ~4.9 TB/s; this form reaches the copy bandwidth).  Every element still subtracts
 // h_0 v_0, h_1 v_1, ... in that order, so the result does not depend on the unrolling.
 constexpr int GP_U = 2, GP_B = 4;
-__global__ void __launch_bounds__(BT) gs_project_kernel(float4* out, const float4* w, const float4* __restrict__ V,
+template <typename VT>
+__global__ void __launch_bounds__(BT) gs_project_kernel(float4* out, const float4* w, const VT* __restrict__ V,
                                                         int nv, long long n4, const double2* h,
                                                         double2* norm_partial, const int* gate, int want,
                                                         const float* vscale) {
@@ -362,7 +397,7 @@ __global__ void __launch_bounds__(BT) gs_project_kernel(float4* out, const float
 #pragma unroll
       for (int b = 0; b < GP_B; ++b)
 #pragma unroll
-        for (int u = 0; u < GP_U; ++u) v[b][u] = ok[u] ? V[(long long)(i + b) * n4 + q[u]] : zero;
+        for (int u = 0; u < GP_U; ++u) v[b][u] = ok[u] ? ldv(V, (long long)(i + b) * n4 + q[u]) : zero;
 #pragma unroll
       for (int b = 0; b < GP_B; ++b) {
         const float2 c = hs[i + b];
@@ -380,7 +415,7 @@ __global__ void __launch_bounds__(BT) gs_project_kernel(float4* out, const float
 #pragma unroll
       for (int u = 0; u < GP_U; ++u) {
         if (!ok[u]) continue;
-        const float4 x = V[(long long)i * n4 + q[u]];
+        const float4 x = ldv(V, (long long)i * n4 + q[u]);
         a[u].x -= c.x * x.x - c.y * x.y;
         a[u].y -= c.x * x.y + c.y * x.x;
         a[u].z -= c.x * x.z - c.y * x.w;
@@ -402,7 +437,42 @@ __global__ void __launch_bounds__(BT) gs_project_kernel(float4* out, const float
 
 void launch_gs_project(float4* out, const float4* w, const float4* V, int nv, long long n4, const double2* h,
                        double2* norm_partial, const int* gate, int want, cudaStream_t st, const float* vscale) {
-  gs_project_kernel<<<blas_partials_blocks(), BT, 0, st>>>(out, w, V, nv, n4, h, norm_partial, gate, want, vscale);
+  gs_project_kernel<float4><<<blas_partials_blocks(), BT, 0, st>>>(out, w, V, nv, n4, h, norm_partial, gate, want,
+                                                                   vscale);
+}
+void launch_gs_project(float4* out, const float4* w, const uint2* V, int nv, long long n4, const double2* h,
+                       double2* norm_partial, const int* gate, int want, cudaStream_t st, const float* vscale) {
+  gs_project_kernel<uint2><<<blas_partials_blocks(), BT, 0, st>>>(out, w, V, nv, n4, h, norm_partial, gate, want,
+                                                                  vscale);
+}
+
+// v16 = FP16 of s w / sqrt(*nu2) and v32 = w / sqrt(*nu2) (the FP32 copy the next Schwarz
+// application reads); with a gate, only when *gate == 1.
+__global__ void basis16_store_kernel(uint2* v16, float4* v32, const float4* w, long long n4, const double* nu2,
+                                     float s, const int* gate) {
+  if (gate && *gate != 1) return;
+  const float inv = (float)(1.0 / sqrt(*nu2));
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+    const float4 a = w[q];
+    const float4 v = make_float4(a.x * inv, a.y * inv, a.z * inv, a.w * inv);
+    if (v32) v32[q] = v;
+    stv(v16, q, v, s);
+  }
+}
+void launch_basis16_store(uint2* v16, float4* v32, const float4* w, long long n4, const double* nu2, float s,
+                          cudaStream_t st, const int* gate) {
+  basis16_store_kernel<<<blas_partials_blocks(), BT, 0, st>>>(v16, v32, w, n4, nu2, s, gate);
+}
+
+// v32 = FP32 of v16 * s
+__global__ void basis16_load_kernel(float4* v32, const uint2* v16, long long n4, float s) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+    const float4 a = ldv(v16, q);
+    v32[q] = make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
+  }
+}
+void launch_basis16_load(float4* v32, const uint2* v16, long long n4, float s, cudaStream_t st) {
+  basis16_load_kernel<<<blas_partials_blocks(), BT, 0, st>>>(v32, v16, n4, s);
 }
 
 // v *= 1 / sqrt(*nu2)

@@ -107,6 +107,9 @@ void launch_r64_to_v32(float4* v, const double2* r, long long n4, const double2*
 // *gate == 1.  vscale (optional, device): the stored vectors are V_i = v_i / vscale[i].
 int launch_recombine(float4* out, const float4* V, int nv, int nout, long long n4, const double2* P, int ldp,
                      cudaStream_t st, const int* gate = nullptr, const float* vscale = nullptr);
+// FP16 basis (uint2 = two complex numbers as half2): the outputs are stored times oscale
+int launch_recombine(uint2* out, const uint2* V, int nv, int nout, long long n4, const double2* P, int ldp,
+                     cudaStream_t st, const int* gate, const float* vscale, float oscale);
 
 // Classical Gram-Schmidt passes with device-gated reorthogonalisation (blas.cu).  A kernel
 // given a gate runs only when *gate == want.  vscale (optional, device): the basis holds
@@ -119,6 +122,16 @@ void launch_gs_project(float4* out, const float4* w, const float4* V, int nv, lo
                        double2* norm_partial, const int* gate, int want, cudaStream_t st,
                        const float* vscale = nullptr);
 void launch_scale_inplace(float4* v, long long n4, const double* nu2, cudaStream_t st);
+// The same passes over an FP16 basis (w and the projection's output stay FP32), and the
+// FP16 basis store / load: v16 = FP16(s w / sqrt(nu2)) with the FP32 copy w / sqrt(nu2) in
+// v32 (optional; gate as r64_to_v32); v32 = s v16.
+int launch_gs_dot(const uint2* V, int nv, long long n4, const float4* w, double2* partial, const int* gate, int want,
+                  cudaStream_t st, const float* vscale);
+void launch_gs_project(float4* out, const float4* w, const uint2* V, int nv, long long n4, const double2* h,
+                       double2* norm_partial, const int* gate, int want, cudaStream_t st, const float* vscale);
+void launch_basis16_store(uint2* v16, float4* v32, const float4* w, long long n4, const double* nu2, float s,
+                          cudaStream_t st, const int* gate = nullptr);
+void launch_basis16_load(float4* v32, const uint2* v16, long long n4, float s, cudaStream_t st);
 
 // ---- BiCGstab comparison solver (krylov.cu).  U = float4 (FP32 fields) or double2 (FP64
 // fields); sc: the recurrence's scalars on the device (see krylov.cu); partial: at least

@@ -29,7 +29,7 @@ class dd_sap_params(C.Structure):
 
 class dd_solve_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("m", C.c_int), ("k", C.c_int), ("max_iter", C.c_int),
-                ("sap", dd_sap_params)]
+                ("sap", dd_sap_params), ("basis_fp16", C.c_int)]
 
 
 class dd_bicgstab_params(C.Structure):
@@ -184,9 +184,9 @@ class Context:
         return self._check(s) if check else s
 
     def dd_solve(self, f, x, nrhs=1, where=DD_HOST, tol=1e-10, m=16, k=0, max_iter=1000, i_schwarz=16,
-                 i_domain=4, storage_prec=DD_PREC_FP16, check=True, threads_per_site=0, additive=0):
+                 i_domain=4, storage_prec=DD_PREC_FP16, check=True, threads_per_site=0, additive=0, basis_fp16=0):
         p = dd_solve_params(tol, m, k, max_iter,
-                            dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site, additive))
+                            dd_sap_params(i_schwarz, i_domain, storage_prec, threads_per_site, additive), basis_fp16)
         info = dd_solve_info()
         s = lib().dd_solve(self._h, _ptr(f), _ptr(x), nrhs, where, C.byref(p), C.byref(info))
         if check:

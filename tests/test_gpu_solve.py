@@ -30,14 +30,16 @@ def test_solve_8x4_workload(prec):
     assert rel(x, xo) <= 1e-8
 
 
-def test_solve_matches_sparse_direct_with_deflation():
+@pytest.mark.parametrize("basis16", [0, 1], ids=["fp32basis", "fp16basis"])
+def test_solve_matches_sparse_direct_with_deflation(basis16):
     dims, dom = (8, 8, 4, 4), (4, 4, 2, 2)
     U = gauge(dims, 0.5, 21, ape=2)
     f = synth.gaussian_source(dims, 22)
     kappa, csw = 0.1390, 1.5
     c = ctx_for(dims, dom, U, kappa, csw)
     x = np.zeros_like(f)
-    info = c.dd_solve(f, x, tol=1e-10, m=6, k=3, i_schwarz=2, i_domain=2, storage_prec=dd.DD_PREC_FP16)
+    info = c.dd_solve(f, x, tol=1e-10, m=6, k=3, i_schwarz=2, i_domain=2, storage_prec=dd.DD_PREC_FP16,
+                      basis_fp16=basis16)
     A = DN.assemble_A(U, kappa, csw).tocsc()
     xl = spl.spsolve(A, f.ravel()).reshape(f.shape)
     assert S.true_residual(U, x, f, kappa, csw) <= 1e-10
@@ -96,18 +98,20 @@ def bench_lattice():
     return w, c, U, W.field_strength(U), synth.make_sources(w)[0]
 
 
-@pytest.mark.parametrize("prec", [dd.DD_PREC_FP16, dd.DD_PREC_FP32], ids=["mixed", "fp32"])
-def test_benchmark_solve_true_residual_by_oracle(bench_lattice, prec):
+@pytest.mark.parametrize("prec,basis16", [(dd.DD_PREC_FP16, 0), (dd.DD_PREC_FP32, 0), (dd.DD_PREC_FP16, 1)],
+                         ids=["mixed", "fp32", "mixed_fp16basis"])
+def test_benchmark_solve_true_residual_by_oracle(bench_lattice, prec, basis16):
     """The solve the benchmark times: 32^3x64, width 0.5 + 5 APE steps, kappa 0.136,
     c_sw 1.5, 8x4x4x4 domains, (I_Schwarz, I_domain, m, k) = (2, 4, 40, 8), two threads per
     site, device-resident f and x (the benchmark's call), in the mixed form (FP16 storage
-    in the Schwarz kernel) and the plain FP32 form.  The oracle recomputes
-    |f - A x| / |f| in FP64 on the whole lattice from the returned x."""
+    in the Schwarz kernel), the plain FP32 form and the mixed form with an FP16 Krylov
+    basis.  The oracle recomputes |f - A x| / |f| in FP64 on the whole lattice from the
+    returned x."""
     w, c, U, F, f = bench_lattice
     fd = torch.view_as_real(torch.from_numpy(f)).cuda().contiguous()
     xd = torch.zeros_like(fd)
     info = c.dd_solve(fd, xd, where=dd.DD_DEVICE, tol=w.tol, m=w.m, k=w.k, max_iter=2000,
-                      i_schwarz=w.i_schwarz, i_domain=w.i_domain, storage_prec=prec)
+                      i_schwarz=w.i_schwarz, i_domain=w.i_domain, storage_prec=prec, basis_fp16=basis16)
     x = torch.view_as_complex(xd.cpu()).numpy()
     r = f - W.apply_A(U, x, w.kappa, w.csw, F)
     res = float(np.linalg.norm(r) / np.linalg.norm(f))
