@@ -331,11 +331,78 @@ int launch_gs_dot(const float4* V, int nv, long long n4, const float4* w, double
   return 1;
 }
 
+// The FP16-basis forms read the basis in 16-byte loads of two units (four complex numbers)
+// and w as the matching two float4, so each load moves as many bytes as in the FP32 forms.
+__device__ inline void unpack_pair(uint4 u, float4& lo, float4& hi) {
+  const float2 a = h2f(u.x), b = h2f(u.y), c = h2f(u.z), d = h2f(u.w);
+  lo = make_float4(a.x, a.y, b.x, b.y);
+  hi = make_float4(c.x, c.y, d.x, d.y);
+}
+
+template <int NV, int U>
+__global__ void __launch_bounds__(BT, 2) gs_dot16_kernel(const uint4* __restrict__ V, int nv, int nch, long long n8,
+                                                         const float4* __restrict__ w, double2* partial, int ldp,
+                                                         const int* gate, int want, const float* vscale) {
+  if (gate && *gate != want) return;
+  const int chunk = blockIdx.x % nch, qb = blockIdx.x / nch, nqb = gridDim.x / nch;
+  const int v0 = chunk * NV, nvc = min(NV, nv - v0);
+  const bool self = chunk == 0;
+  float re[NV], im[NV], ww = 0.f;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) re[i] = im[i] = 0.f;
+  const long long stride = (long long)nqb * BT;
+  const uint4* Vc = V + (long long)v0 * n8;
+  for (long long q = (long long)qb * BT + threadIdx.x; q < n8; q += U * stride) {
+    float4 wl[U], wh[U];
+    uint4 vq[NV][U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long e = q + u * stride;
+      ok[u] = e < n8;
+      wl[u] = ok[u] ? w[2 * e] : make_float4(0.f, 0.f, 0.f, 0.f);
+      wh[u] = ok[u] ? w[2 * e + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (i < nvc)
+#pragma unroll
+        for (int u = 0; u < U; ++u) vq[i][u] = ok[u] ? Vc[(long long)i * n8 + q + u * stride] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (self)
+        ww += wl[u].x * wl[u].x + wl[u].y * wl[u].y + wl[u].z * wl[u].z + wl[u].w * wl[u].w +
+              wh[u].x * wh[u].x + wh[u].y * wh[u].y + wh[u].z * wh[u].z + wh[u].w * wh[u].w;
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (i < nvc) {
+          float4 lo, hi;
+          unpack_pair(vq[i][u], lo, hi);
+          const cx<float> d0 = dot4(lo, wl[u]), d1 = dot4(hi, wh[u]);
+          re[i] += d0.re + d1.re;
+          im[i] += d0.im + d1.im;
+        }
+    }
+  }
+  double2 acc[NV + 1];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    const double sc = (vscale && i < nvc) ? (double)vscale[v0 + i] : 1.0;
+    acc[i] = make_double2(re[i] * sc, im[i] * sc);
+  }
+  acc[NV] = make_double2(ww, 0.0);
+  __shared__ double2 out[NV + 1];
+  block_reduce<NV + 1>(acc, out);
+  if ((int)threadIdx.x < nvc) partial[(long long)qb * ldp + v0 + threadIdx.x] = out[threadIdx.x];
+  if (self && threadIdx.x == 0) partial[(long long)qb * ldp + nv] = out[NV];
+}
+
 int launch_gs_dot(const uint2* V, int nv, long long n4, const float4* w, double2* partial, const int* gate, int want,
                   cudaStream_t st, const float* vscale) {
   const int nch = nv > 0 ? (nv + 7) / 8 : 1;
-  gs_dot_kernel<8, 2, uint2><<<blas_partials_blocks() * nch, BT, 0, st>>>(V, nv, nch, n4, w, partial, nv + 1,
-                                                                          gate, want, vscale);
+  // n4 is even (six units per site): the basis is read as n4 / 2 pairs of units
+  gs_dot16_kernel<8, 2><<<blas_partials_blocks() * nch, BT, 0, st>>>(reinterpret_cast<const uint4*>(V), nv, nch,
+                                                                     n4 / 2, w, partial, nv + 1, gate, want, vscale);
   return 1;
 }
 
@@ -440,10 +507,87 @@ void launch_gs_project(float4* out, const float4* w, const float4* V, int nv, lo
   gs_project_kernel<float4><<<blas_partials_blocks(), BT, 0, st>>>(out, w, V, nv, n4, h, norm_partial, gate, want,
                                                                    vscale);
 }
+// out = w - V h over an FP16 basis read in unit pairs (see gs_dot16_kernel); in place
+// allowed (out aliases w).
+__global__ void __launch_bounds__(BT) gs_project16_kernel(float4* out, const float4* w, const uint4* __restrict__ V,
+                                                          int nv, long long n8, const double2* h,
+                                                          double2* norm_partial, const int* gate, int want,
+                                                          const float* vscale) {
+  if (gate && *gate != want) return;
+  __shared__ float2 hs[64];
+  for (int i = threadIdx.x; i < nv; i += BT) {
+    const double sc = vscale ? (double)vscale[i] : 1.0;
+    hs[i] = make_float2((float)(h[i].x * sc), (float)(h[i].y * sc));
+  }
+  __syncthreads();
+  auto sub = [](float4& a, float2 c, float4 v) {
+    a.x -= c.x * v.x - c.y * v.y;
+    a.y -= c.x * v.y + c.y * v.x;
+    a.z -= c.x * v.z - c.y * v.w;
+    a.w -= c.x * v.w + c.y * v.z;
+  };
+  const long long stride = (long long)gridDim.x * BT;
+  float nrm = 0.f;
+  for (long long q0 = blockIdx.x * (long long)BT + threadIdx.x; q0 < n8; q0 += GP_U * stride) {
+    float4 al[GP_U], ah[GP_U];
+    long long q[GP_U];
+    bool ok[GP_U];
+#pragma unroll
+    for (int u = 0; u < GP_U; ++u) {
+      q[u] = q0 + u * stride;
+      ok[u] = q[u] < n8;
+      al[u] = ok[u] ? w[2 * q[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+      ah[u] = ok[u] ? w[2 * q[u] + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    int i = 0;
+    for (; i + GP_B <= nv; i += GP_B) {
+      uint4 v[GP_B][GP_U];
+#pragma unroll
+      for (int b = 0; b < GP_B; ++b)
+#pragma unroll
+        for (int u = 0; u < GP_U; ++u) v[b][u] = ok[u] ? V[(long long)(i + b) * n8 + q[u]] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int b = 0; b < GP_B; ++b) {
+        const float2 c = hs[i + b];
+#pragma unroll
+        for (int u = 0; u < GP_U; ++u) {
+          float4 lo, hi;
+          unpack_pair(v[b][u], lo, hi);
+          sub(al[u], c, lo);
+          sub(ah[u], c, hi);
+        }
+      }
+    }
+    for (; i < nv; ++i) {
+      const float2 c = hs[i];
+#pragma unroll
+      for (int u = 0; u < GP_U; ++u) {
+        if (!ok[u]) continue;
+        float4 lo, hi;
+        unpack_pair(V[(long long)i * n8 + q[u]], lo, hi);
+        sub(al[u], c, lo);
+        sub(ah[u], c, hi);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < GP_U; ++u)
+      if (ok[u]) {
+        out[2 * q[u]] = al[u];
+        out[2 * q[u] + 1] = ah[u];
+        nrm += al[u].x * al[u].x + al[u].y * al[u].y + al[u].z * al[u].z + al[u].w * al[u].w +
+               ah[u].x * ah[u].x + ah[u].y * ah[u].y + ah[u].z * ah[u].z + ah[u].w * ah[u].w;
+      }
+  }
+  double2 acc[1] = {make_double2(nrm, 0.0)};
+  __shared__ double2 o[1];
+  block_reduce<1>(acc, o);
+  if (threadIdx.x == 0) norm_partial[blockIdx.x] = o[0];
+}
+
 void launch_gs_project(float4* out, const float4* w, const uint2* V, int nv, long long n4, const double2* h,
                        double2* norm_partial, const int* gate, int want, cudaStream_t st, const float* vscale) {
-  gs_project_kernel<uint2><<<blas_partials_blocks(), BT, 0, st>>>(out, w, V, nv, n4, h, norm_partial, gate, want,
-                                                                  vscale);
+  gs_project16_kernel<<<blas_partials_blocks(), BT, 0, st>>>(out, w, reinterpret_cast<const uint4*>(V), nv, n4 / 2, h,
+                                                             norm_partial, gate, want, vscale);
 }
 
 // v16 = FP16 of s w / sqrt(*nu2) and v32 = w / sqrt(*nu2) (the FP32 copy the next Schwarz
