@@ -67,3 +67,19 @@ def test_profile_traffic_needs_the_current_source(bench, tmp_path, monkeypatch):
     assert bench.read_profile("k.txt", "abc123") == 1234.0
     assert bench.read_profile("k.txt", "ffffff") is None
     assert bench.read_profile("missing.txt", "abc123") is None
+
+
+def test_oracle_all_cores_sample_runs_and_fails_cleanly():
+    """The all-cores oracle baseline: one spawned process per core times the same small
+    samples concurrently and returns the slowest times; a process that fails (a lattice the
+    domain shape does not divide) releases the others and raises instead of hanging."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench as B
+    import synth
+    w = synth.WORKLOADS["32^3x64"]
+    fa = B.oracle_fields(w, (8, 8, 8, 8))
+    n, t_a, t_s = B.oracle_all_cores(w, fa, B.oracle_fields(w, (16, 8, 8, 8)))
+    assert n == (os.cpu_count() or 1) and t_a > 0 and t_s > 0
+    with pytest.raises(RuntimeError):
+        B.oracle_all_cores(w, fa, B.oracle_fields(w, (12, 8, 8, 8)))
