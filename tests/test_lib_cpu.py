@@ -124,6 +124,13 @@ def test_null_arguments_are_invalid_not_fatal(ddmod):
     assert L.dd_destroy(None) == ddmod.DD_ERR_INVALID
     assert L.dd_load_gauge(None, None, 0) == ddmod.DD_ERR_INVALID
     assert L.dd_solve(None, None, None, 1, 0, None, None) == ddmod.DD_ERR_INVALID
+    assert L.dd_mg_setup(None, None, 0, None, None) == ddmod.DD_ERR_INVALID
+    assert L.dd_mg_restrict(None, None, None) == ddmod.DD_ERR_INVALID
+    assert L.dd_mg_prolong(None, None, None) == ddmod.DD_ERR_INVALID
+    assert L.dd_mg_coarse_apply(None, None, None) == ddmod.DD_ERR_INVALID
+    assert L.dd_mg_coarse_solve(None, None, None) == ddmod.DD_ERR_INVALID
+    assert L.dd_mg_precondition(None, None, None, 0) == ddmod.DD_ERR_INVALID
+    assert L.dd_solve_mg(None, None, None, 0, None, None) == ddmod.DD_ERR_INVALID
 
 
 def test_host_deflation_rejects_bad_sizes(ddmod):
