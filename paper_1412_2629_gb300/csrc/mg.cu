@@ -362,17 +362,54 @@ __global__ void __launch_bounds__(256) mg_coarse_apply_kernel(Geom g, const floa
   y[t] = b ? make_float2(b[t].x - ar, b[t].y - ai) : make_float2(ar, ai);
 }
 
+// The same product with nine threads per coarse row, one per coupling (dir): one block per
+// domain of 9 nc threads (the row length compiled in), each summing NC terms, then the nine
+// partial sums of a row added in a fixed order through shared memory.  Nine times the
+// threads of the one-thread-per-row form keeps enough loads in flight for short rows.
+template <int NC>
+__global__ void __launch_bounds__(9 * 32) mg_coarse_apply9_kernel(Geom g, const float2* __restrict__ Dc,
+                                                                  const float2* __restrict__ x, float2* y,
+                                                                  const float2* b, const int* gate) {
+  if (gate && *gate) return;
+  __shared__ float2 part[9][NC];
+  const int d = blockIdx.x, dir = threadIdx.x / NC, i = threadIdx.x % NC;
+  int n[4];
+  domain_coords(g, d, n);
+  const int dn = dir == 0 ? d : neighbour_domain(g, d, n, (dir - 1) >> 1, ((dir - 1) & 1) ? -1 : +1);
+  const float2* D = Dc + ((long long)d * 9 + dir) * NC * NC + i;
+  const float2* xv = x + (long long)dn * NC;
+  float ar = 0.f, ai = 0.f;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const float2 a = D[(long long)j * NC], v = xv[j];
+    ar += a.x * v.x - a.y * v.y;
+    ai += a.x * v.y + a.y * v.x;
+  }
+  part[dir][i] = make_float2(ar, ai);
+  __syncthreads();
+  if (dir == 0) {
+    float sr = 0.f, si = 0.f;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      sr += part[q][i].x;
+      si += part[q][i].y;
+    }
+    const long long t = (long long)d * NC + i;
+    y[t] = b ? make_float2(b[t].x - sr, b[t].y - si) : make_float2(sr, si);
+  }
+}
+
 void launch_mg_coarse_apply(const Geom& g, const float2* Dc, int nc, const float2* x, float2* y, const float2* b,
                             const int* gate, cudaStream_t st) {
-  const long long n = (long long)g.ND * nc;
-  const unsigned nb = (unsigned)((n + 255) / 256);
   switch (nc) {
-    case 8: mg_coarse_apply_kernel<8><<<nb, 256, 0, st>>>(g, Dc, nc, x, y, b, gate); break;
-    case 16: mg_coarse_apply_kernel<16><<<nb, 256, 0, st>>>(g, Dc, nc, x, y, b, gate); break;
-    case 24: mg_coarse_apply_kernel<24><<<nb, 256, 0, st>>>(g, Dc, nc, x, y, b, gate); break;
-    case 32: mg_coarse_apply_kernel<32><<<nb, 256, 0, st>>>(g, Dc, nc, x, y, b, gate); break;
-    default: mg_coarse_apply_kernel<0><<<nb, 256, 0, st>>>(g, Dc, nc, x, y, b, gate); break;
+    case 8: mg_coarse_apply9_kernel<8><<<g.ND, 72, 0, st>>>(g, Dc, x, y, b, gate); return;
+    case 16: mg_coarse_apply9_kernel<16><<<g.ND, 144, 0, st>>>(g, Dc, x, y, b, gate); return;
+    case 24: mg_coarse_apply9_kernel<24><<<g.ND, 216, 0, st>>>(g, Dc, x, y, b, gate); return;
+    case 32: mg_coarse_apply9_kernel<32><<<g.ND, 288, 0, st>>>(g, Dc, x, y, b, gate); return;
+    default: break;
   }
+  const long long n = (long long)g.ND * nc;
+  mg_coarse_apply_kernel<0><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, Dc, nc, x, y, b, gate);
 }
 
 // ------------------------------------------------------------------ coarse-vector BLAS
