@@ -262,8 +262,8 @@ int launch_recombine(uint2* out, const uint2* V, int nv, int nout, long long n4,
 // launch order and all but the first find them in L2.  Each loop trip handles U elements
 // per vector, (NV + 1) * U independent 16-byte loads per thread, which keeps enough bytes
 // in flight for HBM even for the short last chunk.
-template <int NV, int U, typename VT>
-__global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const VT* __restrict__ V, int nv, int nch, long long n4,
+template <int NV, int U>
+__global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const float4* __restrict__ V, int nv, int nch, long long n4,
                                                        const float4* __restrict__ w, double2* partial, int ldp,
                                                        const int* gate, int want, const float* vscale) {
   if (gate && *gate != want) return;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const VT* __restrict__ V,
 #pragma unroll
   for (int i = 0; i < NV; ++i) re[i] = im[i] = 0.f;
   const long long stride = (long long)nqb * BT;
-  const VT* Vc = V + (long long)v0 * n4;
+  const float4* Vc = V + (long long)v0 * n4;
   long long q = (long long)qb * BT + threadIdx.x;
   for (; q + (U - 1) * stride < n4; q += U * stride) {
     float4 wq[U], vq[NV][U];
@@ -326,8 +326,8 @@ __global__ void __launch_bounds__(BT, 2) gs_dot_kernel(const VT* __restrict__ V,
 int launch_gs_dot(const float4* V, int nv, long long n4, const float4* w, double2* partial, const int* gate, int want,
                   cudaStream_t st, const float* vscale) {
   const int nch = nv > 0 ? (nv + 7) / 8 : 1;
-  gs_dot_kernel<8, 2, float4><<<blas_partials_blocks() * nch, BT, 0, st>>>(V, nv, nch, n4, w, partial, nv + 1,
-                                                                           gate, want, vscale);
+  gs_dot_kernel<8, 2><<<blas_partials_blocks() * nch, BT, 0, st>>>(V, nv, nch, n4, w, partial, nv + 1, gate, want,
+                                                                   vscale);
   return 1;
 }
 
@@ -433,8 +433,7 @@ void launch_gs_reduce(const double2* partial, int nv, double2* out, const int* g
 // reached ~4.9 TB/s; this form reaches the copy bandwidth).  Every element still subtracts
 // h_0 v_0, h_1 v_1, ... in that order, so the result does not depend on the unrolling.
 constexpr int GP_U = 2, GP_B = 4;
-template <typename VT>
-__global__ void __launch_bounds__(BT) gs_project_kernel(float4* out, const float4* w, const VT* __restrict__ V,
+__global__ void __launch_bounds__(BT) gs_project_kernel(float4* out, const float4* w, const float4* __restrict__ V,
                                                         int nv, long long n4, const double2* h,
                                                         double2* norm_partial, const int* gate, int want,
                                                         const float* vscale) {
@@ -504,9 +503,9 @@ __global__ void __launch_bounds__(BT) gs_project_kernel(float4* out, const float
 
 void launch_gs_project(float4* out, const float4* w, const float4* V, int nv, long long n4, const double2* h,
                        double2* norm_partial, const int* gate, int want, cudaStream_t st, const float* vscale) {
-  gs_project_kernel<float4><<<blas_partials_blocks(), BT, 0, st>>>(out, w, V, nv, n4, h, norm_partial, gate, want,
-                                                                   vscale);
+  gs_project_kernel<<<blas_partials_blocks(), BT, 0, st>>>(out, w, V, nv, n4, h, norm_partial, gate, want, vscale);
 }
+
 // out = w - V h over an FP16 basis read in unit pairs (see gs_dot16_kernel); in place
 // allowed (out aliases w).
 __global__ void __launch_bounds__(BT) gs_project16_kernel(float4* out, const float4* w, const uint4* __restrict__ V,
