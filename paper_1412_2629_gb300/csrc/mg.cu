@@ -320,45 +320,28 @@ void launch_mg_coarse_build(const Geom& g, const float2* U32, const float4* C32,
 }
 
 // ------------------------------------------------------------------ coarse operator
-// y = D_c x (b == nullptr) or y = b - D_c x; one thread per coarse row (domain, i).
-// Skipped when *gate != 0.  NC > 0: the row length is a compile-time constant, so each
-// block's loads are all in flight at once; NC = 0 reads nc at run time.
-template <int NC>
-__global__ void __launch_bounds__(256) mg_coarse_apply_kernel(Geom g, const float2* __restrict__ Dc, int nc_rt,
+// y = D_c x (b == nullptr) or y = b - D_c x; one thread per coarse row (domain, i), for row
+// lengths without a compiled nine-thread form below.  Skipped when *gate != 0.
+__global__ void __launch_bounds__(256) mg_coarse_apply_kernel(Geom g, const float2* __restrict__ Dc, int nc,
                                                               const float2* __restrict__ x, float2* y,
                                                               const float2* b, const int* gate) {
   if (gate && *gate) return;
-  const int nc = NC > 0 ? NC : nc_rt;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)g.ND * nc) return;
   const int d = (int)(t / nc), i = (int)(t % nc);
   int n[4];
   domain_coords(g, d, n);
-  float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+  float ar = 0.f, ai = 0.f;
   for (int dir = 0; dir < 9; ++dir) {
     const int dn = dir == 0 ? d : neighbour_domain(g, d, n, (dir - 1) >> 1, ((dir - 1) & 1) ? -1 : +1);
     const float2* D = Dc + ((long long)d * 9 + dir) * nc * nc + i;
     const float2* xv = x + (long long)dn * nc;
-    if constexpr (NC > 0) {
-#pragma unroll
-      for (int j = 0; j < NC; j += 2) {
-        const float2 a0 = D[(long long)j * NC], v0 = xv[j];
-        const float2 a1 = D[(long long)(j + 1) * NC], v1 = xv[j + 1];
-        ar += a0.x * v0.x - a0.y * v0.y;
-        ai += a0.x * v0.y + a0.y * v0.x;
-        br += a1.x * v1.x - a1.y * v1.y;
-        bi += a1.x * v1.y + a1.y * v1.x;
-      }
-    } else {
-      for (int j = 0; j < nc; ++j) {
-        const float2 a = D[(long long)j * nc], v = xv[j];
-        ar += a.x * v.x - a.y * v.y;
-        ai += a.x * v.y + a.y * v.x;
-      }
+    for (int j = 0; j < nc; ++j) {
+      const float2 a = D[(long long)j * nc], v = xv[j];
+      ar += a.x * v.x - a.y * v.y;
+      ai += a.x * v.y + a.y * v.x;
     }
   }
-  ar += br;
-  ai += bi;
   y[t] = b ? make_float2(b[t].x - ar, b[t].y - ai) : make_float2(ar, ai);
 }
 
@@ -409,7 +392,7 @@ void launch_mg_coarse_apply(const Geom& g, const float2* Dc, int nc, const float
     default: break;
   }
   const long long n = (long long)g.ND * nc;
-  mg_coarse_apply_kernel<0><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, Dc, nc, x, y, b, gate);
+  mg_coarse_apply_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, Dc, nc, x, y, b, gate);
 }
 
 // ------------------------------------------------------------------ coarse-vector BLAS

@@ -200,3 +200,21 @@ def test_mg_setup_rejects_bad_parameters():
     src = torch.zeros(*dims[::-1], 4, 3, 2, dtype=torch.float32, device="cuda")
     with pytest.raises(dd.DDError):
         c.dd_mg_precondition(src, torch.empty_like(src))
+
+
+def test_coarse_operator_odd_test_vector_count():
+    """Three test vectors (six coarse unknowns per domain: the row-length-at-run-time form of
+    the coarse operator) against the oracle's D_c."""
+    dims, dom, seed = CASES[1]
+    U = gauge(dims, 0.5, seed, ape=2)
+    c = ctx_for(dims, dom, U, KAPPA, CSW)
+    tv = [synth.gaussian_source(dims, seed + 200 + k) for k in range(3)]
+    c.dd_mg_setup(torch.stack([dev(v) for v in tv]).contiguous(), 3, dd.DD_DEVICE, setup_iters=0, coarse_m=16,
+                  coarse_cycles=2, i_schwarz=1, i_domain=4, storage_prec=dd.DD_PREC_FP32, threads_per_site=2)
+    agg = MG.Aggregates(dims, dom)
+    Dc = MG.coarse_matrix(U, KAPPA, CSW, MG.interpolation(tv, agg), agg)
+    rng = np.random.default_rng(seed + 3)
+    x = rng.standard_normal(Dc.shape[0]) + 1j * rng.standard_normal(Dc.shape[0])
+    y = torch.empty(Dc.shape[0], 2, dtype=torch.float32, device="cuda")
+    c.dd_mg_coarse_apply(_cvec(x), y)
+    assert rel(_chost(y), Dc @ x) <= 1e-4
