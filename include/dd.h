@@ -313,6 +313,10 @@ long long dd_launch_count(const dd_ctx* ctx);
  * limit).  2 flop per FFMA.  Uses its own stream and a 16-byte buffer; changes no device
  * setting. */
 dd_status dd_fp32_peak(int duration_ms, double* burst_tflops, double* sustained_tflops);
+/* The same for FP64 fused multiply-adds (DFMA chains): the denominator of the FP64 operator
+ * that recomputes the true residual at every restart (Sec. II-C: reliable updates), which
+ * GB300's FP64 rate bounds.  Arguments and behaviour as dd_fp32_peak. */
+dd_status dd_fp64_peak(int duration_ms, double* burst_tflops, double* sustained_tflops);
 
 /* Wave-quantisation load of the Schwarz kernel, the GPU analogue of Eq. 6-7: with
  * n = number of domains of one colour and `slots` CTAs resident at once,

@@ -95,6 +95,7 @@ def lib():
             "dd_deflate_host": (I, [I, I, P, P, P, P, P, P, P]),
             "dd_deflate_device": (I, [I, I, P, P, P, P, P, P, P, C.POINTER(D)]),
             "dd_fp32_peak": (I, [I, C.POINTER(D), C.POINTER(D)]),
+            "dd_fp64_peak": (I, [I, C.POINTER(D), C.POINTER(D)]),
             "dd_mg_setup": (I, [P, P, I, C.POINTER(dd_mg_params), C.POINTER(D)]),
             "dd_mg_restrict": (I, [P, P, P]),
             "dd_mg_prolong": (I, [P, P, P]),
@@ -285,6 +286,15 @@ def dd_fp32_peak(duration_ms=2000):
     st = lib().dd_fp32_peak(int(duration_ms), C.byref(b), C.byref(s))
     if st != DD_OK:
         raise DDError(st, "dd_fp32_peak failed")
+    return b.value, s.value
+
+
+def dd_fp64_peak(duration_ms=1000):
+    """(burst, sustained) FP64 TFLOP/s of the current device from the DFMA kernel."""
+    b, s = C.c_double(), C.c_double()
+    st = lib().dd_fp64_peak(int(duration_ms), C.byref(b), C.byref(s))
+    if st != DD_OK:
+        raise DDError(st, "dd_fp64_peak failed")
     return b.value, s.value
 
 
